@@ -1,0 +1,137 @@
+"""Pins for the imaging oracle (Section 2.2): the PSWF kernel against scipy and
+its integral eigen-relation, grid correction against the closed form, a point
+source at a pixel centre, and brute-force DFT imaging on tiny arrays."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import pro_ang1
+
+import synth
+from oracle import imaging as I
+from oracle import xengine as X
+
+
+def test_pswf_matches_scipy():
+    eta = np.linspace(-0.999, 0.999, 41)      # scipy's pro_ang1 returns nan at |eta| = 1
+    ref = np.array([pro_ang1(0, 0, I.PSWF_C, e)[0] for e in eta]) / pro_ang1(0, 0, I.PSWF_C, 0.0)[0]
+    assert np.max(np.abs(I.pswf_psi0(eta) - ref)) < 1e-10
+
+
+def _lambda0():
+    x, w = np.polynomial.legendre.leggauss(200)
+    return float(np.sum(w * I.pswf_psi0(x)))      # integral of psi_0 = lambda_0 psi_0(0)
+
+
+def test_pswf_eigen_relation():
+    # int_{-1}^{1} psi_0(x) exp(i c x eta) dx = lambda_0 psi_0(eta)
+    x, w = np.polynomial.legendre.leggauss(200)
+    psi = I.pswf_psi0(x)
+    lam = _lambda0()
+    for eta in np.linspace(-1, 1, 11):
+        lhs = np.sum(w * psi * np.exp(1j * I.PSWF_C * x * eta))
+        assert abs(lhs - lam * I.pswf_psi0(eta)) < 1e-12
+
+
+def test_kernel_table_shape_and_symmetry():
+    t = I.kernel_table()
+    assert t.size == I.SUPPORT * I.OVERSAMPLE + 1
+    assert t[t.size // 2] == 1.0 and np.allclose(t, t[::-1], atol=1e-15)
+    assert t.min() > 0 and np.all(np.diff(t[: t.size // 2 + 1]) > 0)
+
+
+@pytest.mark.parametrize("n", [64, 256, 1024])
+def test_grid_correction_closed_form(n):
+    # FT of C(x) = psi_0(x / 3.5) over [-3.5, 3.5] at frequency d / N is
+    # 3.5 lambda_0 psi_0(2 d / N); the tabulated sum matches to the Riemann-sum error
+    corr = I.grid_correction(I.kernel_table(), n)
+    d = np.arange(-n // 2, n // 2)
+    ref = 3.5 * _lambda0() * I.pswf_psi0(2 * d / n)
+    assert np.max(np.abs(corr - ref)) < 1e-6
+
+
+def test_uv_cells_closed_form():
+    # a baseline of B metres at wavelength lam spans B / lam wavelengths = (B / lam) N cell cells
+    nu = 60e6
+    lam = I.C_LIGHT / nu
+    n, cell = 256, 2.0 / 256
+    s = I.cells_per_metre(nu, n, cell)
+    assert 123.0 * s == pytest.approx(123.0 / lam * n * cell, rel=1e-14)
+
+
+def _point_source_vis(pos, nu, l0, m0):
+    """Noise-free unit point source: V_ab = exp(-2 pi i (u l0 + v m0)), XX = YY."""
+    n_ant = pos.shape[0]
+    a, b = X.baseline_pairs(n_ant)
+    lam = I.C_LIGHT / nu
+    ph = -2 * np.pi * ((pos[a, 0] - pos[b, 0]) * l0 + (pos[a, 1] - pos[b, 1]) * m0) / lam
+    v = np.exp(1j * ph)
+    vis = np.zeros((a.size, 4, 2))
+    for p in (0, 3):
+        vis[:, p, 0], vis[:, p, 1] = v.real, v.imag
+    return vis
+
+
+def _small_array(n_ant=12, radius=60.0, seed=3):
+    cfg = synth.Config("t", n_ant, 1, [8], 8, 64, seed, core_radius_m=radius)
+    return synth.antenna_positions(cfg)
+
+
+@pytest.mark.parametrize("n,cell", [(64, 0.02), (64, 2.0 / 64)])
+def test_point_source_peak_at_pixel(n, cell):
+    pos = _small_array()
+    nu = 60e6
+    r0, c0 = n // 2 + 5, n // 2 - 9
+    l0, m0 = (c0 - n // 2) * cell, (r0 - n // 2) * cell
+    vis = _point_source_vis(pos, nu, l0, m0)
+    img, ng, nd = I.dirty_images(vis[None], pos, np.array([nu]), n, cell)
+    img = img[0]
+    assert np.unravel_index(np.argmax(img), img.shape) == (r0, c0)
+    assert ng[0] > 0
+    assert abs(img[r0, c0] - 1.0) < 2e-3
+
+
+def test_gridded_matches_direct_dft():
+    # brute-force DFT imaging of the same (kept) baselines agrees with the
+    # gridded image to the kernel's aliasing level inside |l|, |m| < 0.5 of the field
+    pos = _small_array(10, 50.0, 9)
+    n, cell, nu = 64, 0.02, 60e6
+    g = np.random.default_rng(4)
+    nbl = X.n_baselines(pos.shape[0])
+    vis = g.normal(size=(nbl, 4, 2)) * 100
+    img, ng, nd = I.dirty_images(vis[None], pos, np.array([nu]), n, cell)
+    assert nd[0] == 0
+    ref = I.dft_image(vis, pos, nu, n, cell)
+    inner = slice(n // 4, 3 * n // 4)
+    err = np.max(np.abs(img[0][inner, inner] - ref[inner, inner]))
+    assert err < 1e-3 * np.max(np.abs(ref))
+
+
+def test_hermitian_grid_gives_real_image():
+    pos = _small_array()
+    n, cell, nu = 32, 0.03, 60e6
+    vis = np.random.default_rng(8).normal(size=(X.n_baselines(pos.shape[0]), 4, 2))
+    G, ng, nd = I.grid_channel(vis, pos, nu, n, cell, I.kernel_table())
+    # with the mirror at (-u, -v) the grid is Hermitian about the centre cell
+    flip = np.roll(G[::-1, ::-1], 1, axis=(0, 1))
+    assert np.allclose(G, np.conj(flip), atol=1e-12)
+    raw = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(G)))
+    assert np.max(np.abs(raw.imag)) < 1e-12 * np.max(np.abs(raw.real))
+
+
+def test_baselines_off_grid_are_dropped():
+    # an east-west pair whose footprint just fits / just does not fit
+    n, cell, nu = 32, 2.0 / 32, 60e6
+    s = I.cells_per_metre(nu, n, cell)
+    limit = (n // 2 - 4 + 0.49) / s        # centre cell n/2 - 4 from the middle: taps reach cell 1
+    for dx, kept in ((limit * 0.98, True), ((n // 2 - 2) / s, False)):
+        pos = np.array([[0.0, 0, 0], [dx, 0, 0]])
+        vis = np.ones((3, 4, 2))
+        G, ng, nd = I.grid_channel(vis, pos, nu, n, cell, I.kernel_table())
+        assert (ng == 2) == kept and (nd == 0) == kept
+
+
+def test_horizon_mask():
+    m = I.horizon_mask(64, 2.0 / 64)
+    assert m[32, 32] and not m[0, 0] and not m[32, 0]
+    assert abs(m.sum() / 64 ** 2 - math.pi / 4) < 0.02
