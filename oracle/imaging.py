@@ -12,8 +12,9 @@ are the search product).  Readings where the paper is silent:
   convolved onto the grid with a separable 7 x 7 prolate-spheroidal kernel
   C(x) = psi_0(c, x / 3.5) / psi_0(c, 0), c = 7 pi / 2, tabulated at Q = 1024
   samples per cell.  The position is rounded to the table once:
-  p = rint(u Q); centre cell c0 = floor((p + Q/2) / Q); the tap at cell
-  c0 + t takes table sample t Q - (p - c0 Q).
+  p = rint(u Q); centre cell c0 = p / Q rounded half away from zero (so a
+  visibility at -p has centre -c0 and its footprint is the exact point
+  reflection); the tap at cell c0 + t takes table sample t Q - (p - c0 Q).
 * A baseline whose footprint (or its mirror's) leaves the N x N grid is
   dropped and counted.
 * Image I(r, c) = Re sum_grid G exp(+2 pi i (u l + v m)) / (sum w * C^(r) C^(c)),
@@ -108,7 +109,7 @@ def _cross_pairs(n_ant: int):
 
 def _taps(p: np.ndarray, n: int, q: int):
     """Centre cell, table offset and in-grid flag for rounded positions p (1/Q cells)."""
-    c0 = (p + q // 2) // q
+    c0 = np.sign(p) * ((np.abs(p) + q // 2) // q)
     off = p - c0 * q
     half = SUPPORT // 2
     inside = (n // 2 + c0 - half >= 0) & (n // 2 + c0 + half <= n - 1)

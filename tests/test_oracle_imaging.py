@@ -119,6 +119,17 @@ def test_hermitian_grid_gives_real_image():
     assert np.max(np.abs(raw.imag)) < 1e-12 * np.max(np.abs(raw.real))
 
 
+def test_mirror_footprint_is_point_reflection():
+    # centre cells round half away from zero, so the tap set of -p is the reflection
+    # of the tap set of p, ties (p = Q/2 mod Q) included
+    q, n = I.OVERSAMPLE, 64
+    p = np.array([0, 1, q // 2, -q // 2, 3 * q // 2, 5 * q + q // 2, 7 * q - 3, -(9 * q + q // 2)])
+    c0, off, _ = I._taps(p, n, q)
+    c1, off1, _ = I._taps(-p, n, q)
+    assert np.array_equal(c1, -c0) and np.array_equal(off1, -off)
+    assert np.all(np.abs(off) <= q // 2)
+
+
 def test_baselines_off_grid_are_dropped():
     # an east-west pair whose footprint just fits / just does not fit
     n, cell, nu = 32, 2.0 / 32, 60e6
