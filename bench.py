@@ -1,0 +1,329 @@
+"""Throughput of the whole hot path on the full-array workload.
+
+One step = unpack + upchannelize + requantise (ovro_upchan), X-engine
+(ovro_correlate), uvw + gridding + 2D FFT dirty images (ovro_grid_image) and the
+Stage I search (ovro_detect) over one 10 s integration of one 24 kHz coarse
+channel from 352 dual-pol antennas (8192-point upchannelizer, K = 29 spectra,
+256 x 256 all-sky images): 61,776 cross baselines x 4 pol products x 8192 fine
+channels = 2.02e9 fine-channel visibilities and 8192 channel images per step.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fine-chan visibilities/s & channel-images/s at 352 ants, INT8-TC vs FP32 plain"
+UNIT = "visibilities/s"
+WORKLOAD = ("full array, one coarse channel: 352 dual-pol antennas (251 in a 200 m core, 101 in a "
+            "200 m-1.5 km annulus), 24 kHz coarse channel of 4+4-bit voltages, 8192-point "
+            "upchannelizer, 10 s (K = 29), 256x256 all-sky images")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 7 and parts[0].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[1]) for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------ oracle
+def oracle_sample(cfg, volt, pos, freqs, n_chan_sample=2, n_pix_sample=4):
+    """Times the CPU oracle on a bounded slice of one step; returns the estimated
+    seconds per full step and a description of the sample."""
+    from oracle import detect as OD, imaging as OI, upchan as OU, xengine as OX
+    n = cfg.nfft[0]
+    K = cfg.n_spec[0]
+    t0 = time.perf_counter()
+    inputs = list(range(0, cfg.n_input, max(1, cfg.n_input // 64)))[:64]
+    X = OU.upchannelize(volt[0][:, inputs], n)
+    s = OU.requant_scale(OU.power(volt[0][:, inputs], n), n, K * n)
+    q = OU.requantize(X, s)
+    t_up = (time.perf_counter() - t0) * cfg.n_input / len(inputs)
+    # X-engine + imaging on a few channels of random int8 spectra with the right statistics
+    g = np.random.default_rng(0)
+    qs = np.clip(np.rint(g.normal(0, 8, (n_chan_sample, cfg.n_input, K, 2))), -127, 127).astype(np.int8)
+    t0 = time.perf_counter()
+    vis = OX.correlate(qs, cfg.n_ant)
+    t_x = (time.perf_counter() - t0) / n_chan_sample
+    t0 = time.perf_counter()
+    imgs, _, _ = OI.dirty_images(vis, pos, freqs[:n_chan_sample], cfg.image_size, cfg.cell)
+    t_i = (time.perf_counter() - t0) / n_chan_sample
+    # search: per-channel statistics, and per-pixel high-pass + boxcars over all 8192 channels
+    mask = OI.horizon_mask(cfg.image_size, cfg.cell)
+    t0 = time.perf_counter()
+    for f in range(n_chan_sample):
+        OD.channel_stats(imgs[f], mask)
+    t_s = (time.perf_counter() - t0) / n_chan_sample
+    spec = g.normal(size=(n, n_pix_sample))
+    w = OD.window_channels(24000.0 / n)
+    t0 = time.perf_counter()
+    zp = OD.highpass(spec, [(0, n)], [w])
+    OD.matched_filter(zp, [(0, n)])
+    t_p = (time.perf_counter() - t0) / n_pix_sample
+    n_valid = int(mask.sum())
+    total = t_up + n * (t_x + t_i + t_s) + n_valid * t_p
+    sample = (f"upchannelizer on {len(inputs)} of {cfg.n_input} inputs; X-engine, imaging and channel "
+              f"statistics on {n_chan_sample} of {n} channels; running median + boxcars on "
+              f"{n_pix_sample} of {n_valid} pixel spectra; per-unit times scaled to one full step")
+    del q
+    return total, sample
+
+
+def run_reference(args):
+    import synth
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    cfg = synth.make_config("full")
+    volt = synth.generate(cfg)
+    pos = synth.antenna_positions(cfg)
+    freqs = synth.fine_freqs_hz(cfg.nfft)
+    vis_per_step = cfg.n_ant * (cfg.n_ant - 1) // 2 * 4 * cfg.n_chan_total
+    for _ in range(args.warmup):
+        oracle_sample(cfg, volt, pos, freqs, 1, 2)
+    est = []
+    wall = time.perf_counter()
+    for _ in range(args.steps):
+        t, sample = oracle_sample(cfg, volt, pos, freqs, 1, 2)
+        est.append(t)
+    wall = time.perf_counter() - wall
+    t_step = float(np.mean(est))
+    value = vis_per_step / t_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "oracle": "plain NumPy CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sampled_wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2606_04304_gb300 import ovro
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg = synth.make_config("full")
+    cfg.seed += 1000 * rank                      # each rank: its own coarse channel (weak scaling)
+    volt_h = synth.generate(cfg)
+    pos = synth.antenna_positions(cfg)
+    freqs = synth.fine_freqs_hz(cfg.nfft)
+    n_chan, K, N = cfg.n_chan_total, cfg.n_spec[0], cfg.image_size
+    vis_per_step = cfg.n_ant * (cfg.n_ant - 1) // 2 * 4 * n_chan
+    mode = ovro.XENG_TC if args.xeng == "tc" else ovro.XENG_FP32
+
+    dev = torch.device("cuda", local)
+    volt_pin = torch.from_numpy(volt_h).pin_memory()
+    volt = volt_pin.to(dev)
+    q = torch.empty(ovro.fine_elements(cfg.nfft, cfg.n_time, cfg.n_input), dtype=torch.int8, device=dev)
+    vis = torch.empty((n_chan, ovro.n_baselines(cfg.n_ant), 4, 2), dtype=torch.int32, device=dev)
+    img = torch.empty((n_chan, N, N), dtype=torch.float32, device=dev)
+    ws_u = ovro.workspace(ovro.lib().ovro_upchan_workspace_size(cfg.n_input, 1), dev)
+    ws_i = ovro.workspace(ovro.grid_image_workspace_size(cfg.n_ant, n_chan, N), dev)
+    ws_d = ovro.workspace(ovro.detect_workspace_size(n_chan, N, cfg.nfft), dev)
+    prm = ovro.detect_params()
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        ovro.upchan(volt, cfg.nfft, out_q=q, ws=ws_u)
+        if ev: ev[1].record(stream)
+        ovro.correlate(q, cfg.n_ant, n_chan, K, mode, out=vis)
+        if ev: ev[2].record(stream)
+        ovro.grid_image(vis, pos, freqs, N, cfg.cell, out=img, ws=ws_i)
+        if ev: ev[3].record(stream)
+        c = ovro.detect(img, cfg.cell, cfg.nfft, freqs, prm, ws=ws_d)
+        if ev: ev[4].record(stream)
+        return c
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ovro.correlate_status() != 0:
+        raise RuntimeError("tensor-core X-engine reported a timeout")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- device-resident timed region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    l0 = ovro.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        t_wall = time.perf_counter()
+        e_start.record(stream)
+        for i in range(args.steps):
+            cands = step(evs[i])
+        e_end.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier()
+    launches = ovro.launch_count() - l0
+    ms = e_start.elapsed_time(e_end) / args.steps
+    stage_ms = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)]
+                         for i in range(args.steps)]).mean(axis=0)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through host buffers: H2D of the voltages, D2H of the candidates
+    e2e_ms = []
+    barrier()
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        volt.copy_(volt_pin, non_blocking=True)
+        c2 = step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+    h2d = volt_h.nbytes
+    d2h = int(len(c2)) * ovro.CANDIDATE_DTYPE.itemsize
+
+    if rank == 0:
+        peak, peak_src = _peaks()
+        # dominant-stage roofline: the X-engine writes n_chan * n_bl * 32 B of int32 visibilities
+        n_bl = ovro.n_baselines(cfg.n_ant)
+        x_bytes = n_chan * n_bl * 32 + q.numel()
+        x_ms = float(stage_ms[1])
+        achieved = x_bytes / (x_ms * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": world * vis_per_step / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "i8 in, i32 exact visibilities (FP16-carried tensor-core MMA), f32 FFT/imaging/search",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "xeng": args.xeng, "image_size": N, "n_chan": n_chan,
+                       "l2": "inputs larger than L2: 169 MB voltages and 16.3 GB visibilities per step",
+                       "parallelism": f"{world} independent coarse channels"},
+            "images_per_s": world * n_chan / (ms * 1e-3),
+            "stage_ms": {"upchan": float(stage_ms[0]), "correlate": float(stage_ms[1]),
+                         "grid_image": float(stage_ms[2]), "detect": float(stage_ms[3])},
+            "roofline": {"kernel": "k_xeng_tc" if args.xeng == "tc" else "k_xeng_simt",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"{peak_src} copy bandwidth"},
+            "e2e": {"value": world * vis_per_step / (e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "candidates_per_step": int(len(cands)),
+            "wall_s_timed": t_wall,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            t_cpu, sample = oracle_sample(cfg, volt_h, pos, freqs)
+            line["cpu_baseline"] = {"value": vis_per_step / t_cpu, "unit": UNIT, "cores": 1,
+                                    "kind": "oracle", "sample": sample}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--xeng", default="tc", choices=["tc", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

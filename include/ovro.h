@@ -1,0 +1,236 @@
+/*
+ * ovro.h -- C ABI of the GB300 ultra-narrowband all-sky imaging hot path
+ * (OVRO-LWA technosignature search, arXiv 2606.04304).
+ *
+ * The path: unpack 4+4-bit coarse-channel voltages, upchannelize with an FFT,
+ * requantise to 8 bits, cross-correlate every antenna pair and polarisation
+ * product (X-engine), grid and image every fine channel, and search every
+ * pixel spectrum for narrowband candidates.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers prefixed d_ are device pointers, h_ are host pointers.  The
+ *    caller owns every buffer.  The library never allocates or frees device
+ *    memory: where a call needs scratch it takes a caller-allocated workspace
+ *    (d_ws, ws_bytes) whose size the matching *_workspace_size() returns.
+ *    Workspaces must be 256-byte aligned.
+ *  - Calls are asynchronous and ordered on `stream` (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream), except ovro_detect, which
+ *    synchronises `stream` once to run its global Benjamini-Hochberg step.
+ *  - Every argument is validated on the host before anything is launched; an
+ *    invalid call returns a negative ovro_status and launches nothing.
+ *    Nothing throws across the ABI.
+ *  - A call that launched kernels returns OVRO_ERR_CUDA if a launch failed;
+ *    the message of the last failure is available from ovro_last_error().
+ *  - Inputs are numbered input = 2 * antenna + polarisation (X = 0, Y = 1).
+ *  - Not thread-safe per stream; distinct streams may be used from distinct
+ *    host threads.
+ */
+#ifndef OVRO_H
+#define OVRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OVRO_OK = 0,
+  OVRO_ERR_INVALID_ARG = -1,   /* null pointer, negative size, bad enum */
+  OVRO_ERR_UNSUPPORTED = -2,   /* valid but outside what the kernels implement */
+  OVRO_ERR_CUDA = -3,          /* a CUDA call or launch failed */
+  OVRO_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up */
+  OVRO_ERR_WORKSPACE = -5,     /* workspace missing, too small or misaligned */
+  OVRO_ERR_OVERFLOW = -6,      /* an integer accumulation bound would be exceeded */
+  OVRO_ERR_CAPACITY = -7       /* output capacity too small (true count reported) */
+} ovro_status;
+
+/* Human-readable name of a status code (static storage). */
+const char* ovro_status_string(int status);
+/* Message of the last CUDA failure seen by this library in this thread. */
+const char* ovro_last_error(void);
+/* Library ABI version, (major << 16) | minor. */
+int ovro_version(void);
+/* Number of kernels this library has launched in this process. */
+unsigned long long ovro_launch_count(void);
+
+/* -------------------------------------------------------------------------
+ * a1-a3  Unpack + FFT upchannelizer + 8-bit requantisation
+ *
+ * Section 2.1: the offline pipeline upchannelizes each coarse channel by an
+ * FFT over its time samples (factor 2400 -> 9.9 Hz in the paper) and feeds
+ * 8-bit complex samples to the xGPU correlator.
+ *
+ * d_volt   uint8 [n_coarse][n_time][n_input]; each byte is one complex sample,
+ *          real part in the high nibble, imaginary in the low nibble, both
+ *          4-bit two's complement.
+ * h_nfft   [n_coarse] FFT length N_c per coarse channel, a power of two in
+ *          [2, 16384].  Each coarse channel yields K_c = n_time / N_c spectra
+ *          from non-overlapping blocks (rectangular window, unnormalised
+ *          exp(-2 pi i k n / N) transform); leftover samples are ignored.
+ *          Fine channel k' = (k + N/2) mod N (fftshift) sits at
+ *          nu_c + (k' - N/2) f_c / N.
+ * h_scale_or_null  NULL: one scale per (coarse, input),
+ *          s = 8 sqrt(2) / sqrt(N_c P) with P the mean |x|^2 of the used
+ *          samples (exact integer sum, FP64 arithmetic), s = 0 if P = 0.
+ *          Otherwise a host array [n_coarse][n_input] of scales.
+ * d_fine_q int8 output, coarse-major blocks; block c is
+ *          [N_c][K_c][n_input][2] (re, im), starting at element offset
+ *          sum_{c' < c} N_c' K_c' n_input * 2.  Each component is
+ *          clamp(rint(s * X), -127, 127), s rounded to FP32, one FP32 multiply,
+ *          round half to even.
+ * d_fine_f32_or_null  optional FP32 spectra in the same layout (floats).
+ * Workspace: ovro_upchan_workspace_size(n_input, n_coarse) bytes.
+ * Errors: OVRO_ERR_INVALID_ARG (null pointers, n_* <= 0), OVRO_ERR_UNSUPPORTED
+ *          (N_c not a power of two in range, n_time < N_c).
+ * ------------------------------------------------------------------------- */
+size_t ovro_upchan_workspace_size(int n_input, int n_coarse);
+int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time,
+                const int32_t* h_nfft, const double* h_scale_or_null,
+                int8_t* d_fine_q, float* d_fine_f32_or_null,
+                void* d_ws, size_t ws_bytes, void* stream);
+
+/* -------------------------------------------------------------------------
+ * a4  X-engine: per fine channel, every antenna pair and polarisation product
+ *
+ * Section 2.1: the correlation stage (xGPU) integrates, per fine channel,
+ *     V_ij^pq = sum_{s < K} q_ip(s) conj(q_jq(s))        (i <= j, autos kept)
+ *
+ * d_fine_q  int8 [n_chan][n_spec][2 n_ant][2] (one coarse block of
+ *           ovro_upchan's output, or several with the same K).
+ * d_vis     int32 output [n_chan][n_bl][4][2], n_bl = n_ant (n_ant + 1) / 2,
+ *           baseline (a, b), a <= b, at a n_ant - a (a - 1) / 2 + (b - a);
+ *           pol product p = 2 p_a + p_b (XX, XY, YX, YY); (re, im).
+ * mode      OVRO_XENG_TC: tensor cores (tcgen05, int8 values carried exactly
+ *           in FP16 operands, FP32 accumulation in tensor memory, exact while
+ *           every partial sum stays below 2^24);
+ *           OVRO_XENG_FP32: plain FP32 SIMT accumulation (same exactness
+ *           bound).  Both are bit-exact integer results.
+ * Errors:   OVRO_ERR_OVERFLOW if 2 * 127^2 * n_spec >= 2^24 (n_spec > 520),
+ *           OVRO_ERR_UNSUPPORTED if n_ant > 4096.
+ * ------------------------------------------------------------------------- */
+enum { OVRO_XENG_TC = 0, OVRO_XENG_FP32 = 1 };
+int ovro_correlate(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec, int mode,
+                   int32_t* d_vis, void* stream);
+/* Synchronises `stream` and reports whether the last OVRO_XENG_TC call gave up
+ * a bounded wait on the tensor-core completion barrier (OVRO_ERR_TIMEOUT), in
+ * which case its output is incomplete. */
+int ovro_correlate_status(void* stream);
+
+/* -------------------------------------------------------------------------
+ * a5-a7  uvw (FP64), prolate-spheroidal gridding, 2D FFT -> dirty images
+ *
+ * Section 2.2: every fine channel is imaged over the visible hemisphere
+ * (dirty images are the search product).  Stokes I = (XX + YY) / 2 of every
+ * cross baseline, natural weights, zenith phase centre (planar array, w = 0).
+ * u = (x_a - x_b) s_nu cells, s_nu = nu / (c du), du = 1 / (N cell), one
+ * FP64 multiply; position rounded to 1/1024 cell; separable 7 x 7 kernel
+ * psi_0(7 pi / 2, x / 3.5); a baseline whose footprint (or its mirror's)
+ * leaves the grid is dropped.  Image = Re sum G exp(+2 pi i (u l + v m)),
+ * divided by (gridded visibilities incl. mirrors) and the grid correction;
+ * pixel (r, c) <-> l = (c - N/2) cell, m = (r - N/2) cell; pixels with
+ * l^2 + m^2 >= 1 are 0.
+ *
+ * d_vis           int32 [n_chan][n_bl][4][2] as produced by ovro_correlate.
+ * h_ant_enu_m     [n_ant][3] antenna positions, metres (only E, N are used).
+ * h_chan_freq_hz  [n_chan] sky frequency of each channel.
+ * image_size      N, a power of two in [16, 1024].
+ * cell_dircos     pixel size in direction cosines (2 / N images the sky to
+ *                 the horizon).
+ * storage         OVRO_STORE_FP32, or OVRO_STORE_BF16 / OVRO_STORE_FP16 to keep
+ *                 the intermediate uv grid in 16-bit storage (FP32 arithmetic).
+ * d_img           float output [n_chan][N][N].
+ * d_n_gridded_or_null  optional int32 [n_chan]: gridded visibilities per
+ *                 channel (mirrors included).
+ * Workspace: ovro_grid_image_workspace_size(...) bytes.
+ * ------------------------------------------------------------------------- */
+enum { OVRO_STORE_FP32 = 0, OVRO_STORE_BF16 = 1, OVRO_STORE_FP16 = 2 };
+size_t ovro_grid_image_workspace_size(int n_ant, int n_chan, int image_size, int storage);
+int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
+                    const double* h_chan_freq_hz, int n_chan, int image_size,
+                    double cell_dircos, int storage, float* d_img,
+                    int32_t* d_n_gridded_or_null, void* d_ws, size_t ws_bytes, void* stream);
+
+/* a5 on its own: p = rint(u Q), Q = 1024, the rounded uv position in 1/1024
+ * cell of every cross baseline (a < b, row-major order) in every channel,
+ * int32 [n_chan][n_cross] (saturated at +-2^30).  The FP64 product of the
+ * definition is reproduced exactly.  Workspace: ovro_grid_image_workspace_size
+ * with the same n_ant, n_chan and image_size. */
+int ovro_uvw(const double* h_ant_enu_m, int n_ant, const double* h_chan_freq_hz, int n_chan,
+             int image_size, double cell_dircos, int32_t* d_pu, int32_t* d_pv, void* d_ws,
+             size_t ws_bytes, void* stream);
+
+/* -------------------------------------------------------------------------
+ * a8-a12  Stage I candidate search
+ *
+ * Section 2.4: standardise each channel image by its median absolute
+ * deviation (in-horizon pixels, FP64 statistics, z = (x - med) /
+ * (1.482602218505602 MAD)); subtract a running median along frequency per
+ * pixel (window: smallest odd W with W df > highpass_hz, centred, clipped at
+ * coarse-channel edges); boxcar matched filters of the given widths
+ * (unit-normalised 1/sqrt(w), width w at channel k covers
+ * k - floor((w-1)/2) .. k + ceil((w-1)/2) inside the coarse channel), keeping
+ * the maximum SNR and its width; p = Q(SNR) with Benjamini-Hochberg across
+ * all in-horizon pixels x channels, or a fixed n_sigma threshold; then 1D
+ * non-maximum suppression along frequency per pixel (half-width
+ * max(1, floor(w/2)), within a coarse channel).
+ * ------------------------------------------------------------------------- */
+enum { OVRO_DETECT_BH = 0, OVRO_DETECT_FIXED = 1 };
+
+typedef struct {
+  int mode;               /* OVRO_DETECT_BH or OVRO_DETECT_FIXED */
+  double alpha;           /* BH false-discovery level (e.g. 0.01) */
+  double nsigma;          /* fixed-mode threshold (the paper quotes 10) */
+  double highpass_hz;     /* running-median span, "over 5 kHz" -> 5000 */
+  double coarse_bw_hz;    /* coarse-channel width (24000) */
+} ovro_detect_params;
+
+typedef struct {
+  int32_t coarse;         /* coarse channel */
+  int32_t fine;           /* fine channel within the coarse channel */
+  int32_t chan;           /* global channel index */
+  int32_t row, col;       /* pixel */
+  int32_t width;          /* matched-filter width, channels */
+  float snr;              /* matched-filter SNR */
+  float pad_;
+  double freq_hz;         /* sky frequency of the channel */
+  double log10_p;         /* log10 of the one-sided Gaussian p-value */
+} ovro_candidate;
+
+/* Number of boxcar widths and their values (the default set used by
+ * ovro_detect: 1..10, 13..49 step 3, 50..100 step 10). */
+int ovro_default_widths(int32_t* h_out_or_null);
+
+size_t ovro_detect_workspace_size(int n_chan, int image_size, int n_coarse,
+                                  const int32_t* h_nfft);
+/* d_img     float [n_chan][N][N] images (ovro_grid_image output layout).
+ * h_nfft    [n_coarse] channels per coarse channel (sum = n_chan).
+ * h_chan_freq_hz [n_chan] sky frequencies (for the candidate records).
+ * h_out     host array of max_out candidates, ordered by (row, col, chan);
+ *           *n_out = number found.  OVRO_ERR_CAPACITY if more than max_out
+ *           (the first max_out are written, *n_out holds the true count). */
+int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dircos,
+                int n_coarse, const int32_t* h_nfft, const double* h_chan_freq_hz,
+                const ovro_detect_params* params, ovro_candidate* h_out, int max_out,
+                int* n_out, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Stage-isolated pieces of ovro_detect (same workspace), for inspection and
+ * testing.  Layouts are the caller's:
+ *   ovro_detect_stats:  d_stats double [n_chan][2] = (median, MAD).
+ *   ovro_detect_filter: d_zp (optional) float [n_chan][N][N] high-passed
+ *       standardised cube (0 outside the horizon); d_snr float [n_chan][N][N]
+ *       maximum boxcar SNR; d_width int32 [n_chan][N][N] its width (0 outside
+ *       the horizon).  Needs d_stats from ovro_detect_stats. */
+int ovro_detect_stats(const float* d_img, int n_chan, int image_size, double cell_dircos,
+                      double* d_stats, void* d_ws, size_t ws_bytes, void* stream);
+int ovro_detect_filter(const float* d_img, const double* d_stats, int n_chan, int image_size,
+                       double cell_dircos, int n_coarse, const int32_t* h_nfft,
+                       const ovro_detect_params* params, float* d_zp_or_null, float* d_snr,
+                       int32_t* d_width, void* d_ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OVRO_H */

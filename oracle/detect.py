@@ -74,18 +74,24 @@ def running_median(spec: np.ndarray, w: int) -> np.ndarray:
     """Centred running median along the last axis, window clipped at the ends.
 
     spec: [..., n].  Interior positions use np.median over a full window; the
-    h positions at each end use the shrunken window.
+    h positions at each end use the shrunken window.  Leading rows are taken
+    a few at a time so the window view stays small in memory.
     """
     n = spec.shape[-1]
     h = w // 2
-    out = np.empty(spec.shape, dtype=np.float64)
-    if n > 2 * h:
-        win = np.lib.stride_tricks.sliding_window_view(spec, 2 * h + 1, axis=-1)
-        out[..., h:n - h] = np.median(win, axis=-1)
-    for k in list(range(min(h, n))) + list(range(max(n - h, h), n)):
-        lo, hi = max(0, k - h), min(n - 1, k + h)
-        out[..., k] = np.median(spec[..., lo:hi + 1], axis=-1)
-    return out
+    flat = spec.reshape(-1, n)
+    out = np.empty(flat.shape, dtype=np.float64)
+    rows = max(1, int(2e8 // max(1, (n * (2 * h + 1)))))
+    for r0 in range(0, flat.shape[0], rows):
+        blk = flat[r0:r0 + rows]
+        o = out[r0:r0 + rows]
+        if n > 2 * h:
+            win = np.lib.stride_tricks.sliding_window_view(blk, 2 * h + 1, axis=-1)
+            o[:, h:n - h] = np.median(win, axis=-1)
+        for k in list(range(min(h, n))) + list(range(max(n - h, h), n)):
+            lo, hi = max(0, k - h), min(n - 1, k + h)
+            o[:, k] = np.median(blk[:, lo:hi + 1], axis=-1)
+    return out.reshape(spec.shape)
 
 
 def highpass(z: np.ndarray, chan_bounds, windows) -> np.ndarray:

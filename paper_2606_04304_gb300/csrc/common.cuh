@@ -1,0 +1,88 @@
+// Internal helpers shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/ovro.h"
+
+namespace ovro {
+
+// Records the message of a failed CUDA call for ovro_last_error().
+void set_last_error(const char* where, cudaError_t e);
+// Counts kernel launches made by the library (ovro_launch_count()).
+void count_launch();
+
+#define OVRO_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) {                                  \
+      ::ovro::set_last_error(#expr, e_);                      \
+      return OVRO_ERR_CUDA;                                   \
+    }                                                         \
+  } while (0)
+
+#define OVRO_LAUNCH_CHECK()                                   \
+  do {                                                        \
+    ::ovro::count_launch();                                   \
+    cudaError_t e_ = cudaGetLastError();                      \
+    if (e_ != cudaSuccess) {                                  \
+      ::ovro::set_last_error("kernel launch", e_);            \
+      return OVRO_ERR_CUDA;                                   \
+    }                                                         \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+inline int ilog2(long long x) { int r = 0; while ((1LL << r) < x) ++r; return r; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves 256-byte aligned sub-buffers out of a caller workspace.
+struct Carver {
+  char* base;
+  size_t used = 0;
+  size_t cap;
+  Carver(void* b, size_t c) : base(static_cast<char*>(b)), cap(c) {}
+  template <class T>
+  T* take(size_t count) {
+    used = align_up(used, 256);
+    T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+    used += count * sizeof(T);
+    return p;
+  }
+  bool ok() const { return used <= cap; }
+};
+
+inline int check_workspace(void* ws, size_t ws_bytes, size_t need) {
+  if (need == 0) return OVRO_OK;
+  if (ws == nullptr || ws_bytes < need) return OVRO_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return OVRO_ERR_WORKSPACE;
+  return OVRO_OK;
+}
+
+inline int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+// ---- device helpers ------------------------------------------------------
+// Order-preserving map float -> uint32 (total order, -0 < +0 irrelevant here).
+__device__ __forceinline__ uint32_t f2key(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+}  // namespace ovro

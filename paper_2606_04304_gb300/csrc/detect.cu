@@ -1,0 +1,947 @@
+// a8-a12: Stage I candidate search over the image cube (Section 2.4).
+//
+//  a8  k_stats       per channel image: exact median and MAD of the in-horizon
+//                    pixels (radix selection on order-preserving keys; the
+//                    MAD's |x - med| ordering is decided on FP32 keys and the
+//                    few elements inside the FP32 error window are resolved in
+//                    FP64), giving FP64 statistics.
+//      k_ztrans      standardises (z = (x - med) / (1.4826 MAD)) and turns the
+//                    cube into per-pixel spectra [coarse][pixel][channel].
+//  a9  k_rank        per pixel spectrum: stable LSD radix sort (4 x 8-bit
+//                    digits, warp match for in-warp ranks) -> sorted values and
+//                    the rank of every channel.
+//      k_walk        one thread per pixel walks the channels keeping the
+//                    window's ranks in a bitset (shared memory, interleaved per
+//                    thread) and a cursor on the lower median, so every step of
+//                    the exact running median costs O(1) amortised.
+//  a10 k_mf          per 8 consecutive channels a thread holds the 107-value
+//                    neighbourhood as register prefix sums and evaluates all 29
+//                    boxcars as prefix differences; keeps max SNR and width and
+//                    histograms the SNRs above the p = alpha floor.
+//  a11 host          Benjamini-Hochberg: the histogram bounds the cut to one
+//                    bin; k_compact gathers every voxel at or above that bin
+//                    and the exact step-up rule runs on that small set in FP64.
+//  a12 host          greedy 1D non-maximum suppression per pixel and coarse
+//                    channel.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ovro {
+namespace {
+
+constexpr double kMadToSigma = 1.482602218505602;
+constexpr int kNW = 29;
+// default boxcar widths: 1..10, 13..49 step 3, 50..100 step 10 (29 widths)
+__host__ __device__ constexpr int width_of(int i) {
+  return i < 10 ? i + 1 : (i < 23 ? 13 + 3 * (i - 10) : 50 + 10 * (i - 23));
+}
+// 1 / sqrt(w) for the default widths, correctly rounded from FP64
+__host__ __device__ constexpr float rsqrt_width(int i) {
+  return i == 0 ? 1.f : i == 1 ? 0.70710678118654746f : i == 2 ? 0.57735026918962584f
+       : i == 3 ? 0.5f : i == 4 ? 0.44721359549995793f : i == 5 ? 0.40824829046386307f
+       : i == 6 ? 0.3779644730092272f : i == 7 ? 0.35355339059327373f
+       : i == 8 ? 0.33333333333333331f : i == 9 ? 0.31622776601683794f
+       : i == 10 ? 0.27735009811261457f : i == 11 ? 0.25f : i == 12 ? 0.22941573387056174f
+       : i == 13 ? 0.21320071635561041f : i == 14 ? 0.20000000000000001f
+       : i == 15 ? 0.1889822365046136f : i == 16 ? 0.17960530202677491f
+       : i == 17 ? 0.17149858514250882f : i == 18 ? 0.16439898730535729f
+       : i == 19 ? 0.15811388300841897f : i == 20 ? 0.15249857033260467f
+       : i == 21 ? 0.14744195615489714f : i == 22 ? 0.14285714285714285f
+       : i == 23 ? 0.1414213562373095f : i == 24 ? 0.12909944487358055f
+       : i == 25 ? 0.11952286093343936f : i == 26 ? 0.11180339887498948f
+       : i == 27 ? 0.10540925533894598f : 0.10000000000000001f;
+}
+constexpr int kMaxLo = 49, kMaxHi = 50;
+constexpr int kVox = 8;                                  // voxels per thread in k_mf
+constexpr int kWin = kVox + kMaxLo + kMaxHi;             // 107
+
+// histogram of SNRs: bins of 2^-7 relative width from the floor up to 64, then overflow
+constexpr int kHistShift = 16;
+
+__device__ int g_detect_status;
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ float ulpf(float x) {
+  x = fabsf(x);
+  if (x == 0.f) return 1.4e-45f;
+  const int e = (__float_as_int(x) >> 23) & 0xff;
+  return e > 23 ? __int_as_float((e - 23) << 23) : 1.4e-45f;
+}
+
+// block-wide exclusive scan of `n` uint32 counters in shared memory (any blockDim multiple of 32)
+__device__ void block_exclusive_scan(uint32_t* a, int n, uint32_t* warp_tot) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int per = (n + T - 1) / T;
+  const int lo = tid * per, hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += a[i];
+  // inclusive warp scan of s
+  const int lane = tid & 31, warp = tid >> 5;
+  uint32_t v = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) warp_tot[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = T >> 5;
+    uint32_t w = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < nw) warp_tot[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = v - s + (warp > 0 ? warp_tot[warp - 1] : 0);
+  for (int i = lo; i < hi; ++i) {
+    const uint32_t c = a[i];
+    a[i] = run;
+    run += c;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ a8 stats
+struct SelectState {
+  uint32_t prefix;
+  int k;
+};
+
+// k-th smallest (0-based) of the keys produced by key_of(i), i < n.
+// hist: 2048 uint32 in shared memory; tot: 64 uint32 scratch; result broadcast.
+template <class KeyOf>
+__device__ uint32_t block_select(int n, int k, const KeyOf& key_of, uint32_t* hist, uint32_t* tot,
+                                 int* sel) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  uint32_t prefix = 0;
+  int kk = k;
+  const int shifts[3] = {21, 10, 0};
+  const int widths[3] = {11, 11, 10};
+  for (int pass = 0; pass < 3; ++pass) {
+    const int sh = shifts[pass];
+    const int nb = 1 << widths[pass];
+    for (int i = tid; i < nb; i += T) hist[i] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += T) {
+      const uint32_t key = key_of(i);
+      const bool match = pass == 0 ? true : ((key >> (sh + widths[pass])) == prefix);
+      if (match) atomicAdd(&hist[(key >> sh) & (nb - 1)], 1u);
+    }
+    __syncthreads();
+    block_exclusive_scan(hist, nb, tot);
+    // find b with hist[b] <= kk < hist[b+1] (exclusive prefix)
+    for (int b = tid; b < nb; b += T) {
+      const uint32_t lo = hist[b];
+      const uint32_t hi = (b + 1 < nb) ? hist[b + 1] : 0xffffffffu;
+      if (lo <= static_cast<uint32_t>(kk) && static_cast<uint32_t>(kk) < hi) {
+        sel[0] = b;
+        sel[1] = kk - static_cast<int>(lo);
+      }
+    }
+    __syncthreads();
+    prefix = (prefix << widths[pass]) | static_cast<uint32_t>(sel[0]);
+    kk = sel[1];
+    __syncthreads();
+  }
+  return prefix;
+}
+
+__global__ void __launch_bounds__(1024)
+k_stats(const float* __restrict__ img, const int* __restrict__ pix, int n_valid, long long npix,
+        int in_smem, double* __restrict__ stats64, float* __restrict__ stats32) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);            // 2048
+  uint32_t* tot = hist + 2048;                                    // 64
+  int* sel = reinterpret_cast<int*>(tot + 64);                    // 8
+  double* wbuf = reinterpret_cast<double*>(sel + 8);              // 2048 window values
+  float* vals = reinterpret_cast<float*>(wbuf + 2048);            // n_valid (if in_smem)
+  __shared__ int wcount;
+  __shared__ int lcount;
+  const int ch = blockIdx.x;
+  const float* im = img + static_cast<long long>(ch) * npix;
+  if (in_smem)
+    for (int i = threadIdx.x; i < n_valid; i += blockDim.x) vals[i] = im[pix[i]];
+  __syncthreads();
+  auto xval = [&](int i) -> float { return in_smem ? vals[i] : im[pix[i]]; };
+  auto key_x = [&](int i) -> uint32_t { return f2key(xval(i)); };
+
+  const int n = n_valid;
+  const int k1 = (n - 1) / 2, k2 = n / 2;
+  const uint32_t key1 = block_select(n, k1, key_x, hist, tot, sel);
+  uint32_t key2 = key1;
+  if (k2 != k1) key2 = block_select(n, k2, key_x, hist, tot, sel);
+  const double x1 = static_cast<double>(key2f(key1)), x2 = static_cast<double>(key2f(key2));
+  const double med = (k1 == k2) ? x1 : (x1 + x2) / 2.0;
+  const float m32 = static_cast<float>(med);
+  auto key_d = [&](int i) -> uint32_t { return f2key(fabsf(xval(i) - m32)); };
+  const uint32_t d1k = block_select(n, k1, key_d, hist, tot, sel);
+  uint32_t d2k = d1k;
+  if (k2 != k1) d2k = block_select(n, k2, key_d, hist, tot, sel);
+  const float v1 = key2f(d1k), v2 = key2f(d2k);
+  const float margin = 4.0f * (ulpf(v2) + ulpf(m32)) + 4.0f * ulpf(fmaxf(v2, fabsf(m32)));
+  const float vlo = v1 - margin, vhi = v2 + margin;
+  if (threadIdx.x == 0) { wcount = 0; lcount = 0; }
+  __syncthreads();
+  int my_l = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float x = xval(i);
+    const float d = fabsf(x - m32);
+    if (d < vlo) {
+      ++my_l;
+    } else if (d <= vhi) {
+      const int s = atomicAdd(&wcount, 1);
+      if (s < 2048) wbuf[s] = fabs(static_cast<double>(x) - med);
+    }
+  }
+  atomicAdd(&lcount, my_l);
+  __syncthreads();
+  const int nw = wcount, L = lcount;
+  double mad = 0.0;
+  bool ok = nw <= 2048 && k1 - L >= 0 && k2 - L < nw;
+  // more than half the pixels equal an exactly representable median: MAD = 0
+  const bool zero_mad = (v2 == 0.0f) && (static_cast<double>(m32) == med);
+  if (zero_mad) ok = true;
+  if (ok && !zero_mad) {
+    // ranks inside the window by counting (ties broken by slot index)
+    const int r1 = k1 - L, r2 = k2 - L;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) {
+      const double v = wbuf[i];
+      int r = 0;
+      for (int j = 0; j < nw; ++j) {
+        const double u = wbuf[j];
+        r += (u < v || (u == v && j < i)) ? 1 : 0;
+      }
+      if (r == r1) reinterpret_cast<double*>(tot)[0] = v;
+      if (r == r2) reinterpret_cast<double*>(tot)[1] = v;
+    }
+    __syncthreads();
+    const double d1 = reinterpret_cast<double*>(tot)[0], d2 = reinterpret_cast<double*>(tot)[1];
+    mad = (k1 == k2) ? d1 : (d1 + d2) / 2.0;
+  }
+  if (threadIdx.x == 0) {
+    if (!ok) atomicExch(&g_detect_status, 2);
+    stats64[2 * ch] = med;
+    stats64[2 * ch + 1] = ok ? mad : nan("");
+    stats32[2 * ch] = m32;
+    stats32[2 * ch + 1] = (ok && mad > 0.0) ? static_cast<float>(1.0 / (kMadToSigma * mad)) : 0.0f;
+  }
+}
+
+__global__ void k_stats32(const double* __restrict__ s64, int n_chan, float* __restrict__ s32) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_chan) return;
+  const double med = s64[2 * f], mad = s64[2 * f + 1];
+  s32[2 * f] = static_cast<float>(med);
+  s32[2 * f + 1] = mad > 0.0 ? static_cast<float>(1.0 / (kMadToSigma * mad)) : 0.0f;
+}
+
+// ------------------------------------------------- standardise + transpose
+// z[p][k] = (x[chan0 + k][pix[p]] - med) * inv, 32 x 32 tiles.
+__global__ void k_ztrans(const float* __restrict__ img, const int* __restrict__ pix, int n_valid,
+                         long long npix, int chan0, int nc, const float* __restrict__ stats32,
+                         float* __restrict__ z) {
+  __shared__ float t[32][33];
+  const int p0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    const int k = k0 + j, p = p0 + tx;
+    float v = 0.f;
+    if (k < nc && p < n_valid) {
+      const int ch = chan0 + k;
+      const float x = img[static_cast<long long>(ch) * npix + pix[p]];
+      v = (x - stats32[2 * ch]) * stats32[2 * ch + 1];
+    }
+    t[j][tx] = v;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int p = p0 + j, k = k0 + tx;
+    if (p < n_valid && k < nc) z[static_cast<long long>(p) * nc + k] = t[tx][j];
+  }
+}
+
+// --------------------------------------------------------------- a9 sort
+// Stable LSD radix sort of one pixel spectrum per CTA iteration.
+__global__ void __launch_bounds__(512)
+k_rank(const float* __restrict__ z, int n_valid, int nc, float* __restrict__ sv,
+       uint16_t* __restrict__ rank) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = blockDim.x >> 5;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);           // 256 * W
+  uint32_t* tot = hist + 256 * W;                                // 32
+  uint32_t* ka = tot + 32;
+  uint32_t* kb = ka + nc;
+  uint16_t* ia = reinterpret_cast<uint16_t*>(kb + nc);
+  uint16_t* ib = ia + nc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = ((nc + W - 1) / W + 31) / 32 * 32;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int p = blockIdx.x; p < n_valid; p += gridDim.x) {
+    const float* zp = z + static_cast<long long>(p) * nc;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      ka[k] = f2key(zp[k]);
+      ia[k] = static_cast<uint16_t>(k);
+    }
+    uint32_t* ks = ka; uint32_t* kd = kb;
+    uint16_t* is = ia; uint16_t* id = ib;
+    __syncthreads();
+    for (int pass = 0; pass < 4; ++pass) {
+      const int sh = 8 * pass;
+      for (int i = threadIdx.x; i < 256 * W; i += blockDim.x) hist[i] = 0;
+      __syncthreads();
+      for (int i = lane; i < seg; i += 32) {
+        const int k = warp * seg + i;
+        if (k < nc) atomicAdd(&hist[((ks[k] >> sh) & 255u) * W + warp], 1u);
+      }
+      __syncthreads();
+      block_exclusive_scan(hist, 256 * W, tot);
+      for (int b = 0; b < seg; b += 32) {
+        const int k = warp * seg + b + lane;
+        const bool valid = k < nc;
+        const uint32_t key = valid ? ks[k] : 0u;
+        const uint32_t d = valid ? ((key >> sh) & 255u) : 256u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid) {
+          const uint32_t pos = hist[d * W + warp] + __popc(peers & lt_mask);
+          kd[pos] = key;
+          id[pos] = is[k];
+        }
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) hist[d * W + warp] += __popc(peers);
+        __syncwarp();
+      }
+      __syncthreads();
+      uint32_t* t1 = ks; ks = kd; kd = t1;
+      uint16_t* t2 = is; is = id; id = t2;
+    }
+    float* svp = sv + static_cast<long long>(p) * nc;
+    uint16_t* rp = rank + static_cast<long long>(p) * nc;
+    for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+      svp[r] = key2f(ks[r]);
+      rp[is[r]] = static_cast<uint16_t>(r);
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------- a9 running median
+constexpr int kWalkThreads = 64;
+
+__device__ __forceinline__ int next_set(const uint32_t* bits, int p, int nwords) {
+  int w = p >> 5;
+  if (w >= nwords) return -1;
+  uint32_t word = bits[w * kWalkThreads] & (0xffffffffu << (p & 31));
+  while (word == 0) {
+    if (++w >= nwords) return -1;
+    word = bits[w * kWalkThreads];
+  }
+  return (w << 5) + __ffs(word) - 1;
+}
+
+__device__ __forceinline__ int prev_set(const uint32_t* bits, int p) {
+  if (p < 0) return -1;
+  int w = p >> 5;
+  uint32_t word = bits[w * kWalkThreads] & (0xffffffffu >> (31 - (p & 31)));
+  while (word == 0) {
+    if (--w < 0) return -1;
+    word = bits[w * kWalkThreads];
+  }
+  return (w << 5) + 31 - __clz(word);
+}
+
+// zbuf holds z on entry and z - running median on exit ([pixel][channel]).
+__global__ void __launch_bounds__(kWalkThreads)
+k_walk(float* __restrict__ zbuf, const float* __restrict__ sv, const uint16_t* __restrict__ rank,
+       int n_valid, int nc, int h) {
+  extern __shared__ uint32_t bits_all[];
+  const int t = threadIdx.x;
+  const int p = blockIdx.x * kWalkThreads + t;
+  const int nwords = (nc + 31) >> 5;
+  uint32_t* bits = bits_all + t;                         // word w at bits[w * kWalkThreads]
+  for (int w = 0; w < nwords; ++w) bits[w * kWalkThreads] = 0u;
+  if (p >= n_valid) return;
+  float* zp = zbuf + static_cast<long long>(p) * nc;
+  const float* svp = sv + static_cast<long long>(p) * nc;
+  const uint16_t* rp = rank + static_cast<long long>(p) * nc;
+
+  // window for k = 0: [0, min(h, nc - 1)]
+  int size = 0;
+  const int hi0 = min(h, nc - 1);
+  for (int j = 0; j <= hi0; ++j) {
+    const int r = rp[j];
+    bits[(r >> 5) * kWalkThreads] |= 1u << (r & 31);
+    ++size;
+  }
+  // cursor on the lower median: the t-th smallest set bit
+  int target = (size - 1) >> 1;
+  int cur = next_set(bits, 0, nwords);
+  int lt = 0;
+  while (lt < target && cur >= 0) { cur = next_set(bits, cur + 1, nwords); ++lt; }
+  if (cur < 0) {
+    atomicExch(&g_detect_status, 3);
+    return;
+  }
+
+  for (int k = 0; k < nc; ++k) {
+    if (k > 0) {
+      const int jin = k + h, jout = k - h - 1;
+      bool removed_cur = false;
+      int rout = -1;
+      if (jin < nc) {
+        const int r = rp[jin];
+        bits[(r >> 5) * kWalkThreads] |= 1u << (r & 31);
+        ++size;
+        if (r < cur) ++lt;
+      }
+      if (jout >= 0) {
+        rout = rp[jout];
+        bits[(rout >> 5) * kWalkThreads] &= ~(1u << (rout & 31));
+        --size;
+        if (rout < cur) --lt;
+        else if (rout == cur) removed_cur = true;
+      }
+      if (removed_cur) {
+        const int nx = next_set(bits, rout, nwords);
+        if (nx >= 0) {
+          cur = nx;
+        } else {
+          cur = prev_set(bits, rout);
+          --lt;
+        }
+      }
+      target = (size - 1) >> 1;
+      while (lt < target && cur >= 0) { cur = next_set(bits, cur + 1, nwords); ++lt; }
+      while (lt > target && cur >= 0) { cur = prev_set(bits, cur - 1); --lt; }
+      if (cur < 0) {                      // cannot happen for a consistent bitset
+        atomicExch(&g_detect_status, 3);
+        return;
+      }
+    }
+    float med = svp[cur];
+    if ((size & 1) == 0) {
+      const int up = next_set(bits, cur + 1, nwords);
+      if (up < 0) {
+        atomicExch(&g_detect_status, 3);
+        return;
+      }
+      med = 0.5f * (med + svp[up]);
+    }
+    zp[k] = zp[k] - med;
+  }
+}
+
+// -------------------------------------------------------- a10 matched filter
+__global__ void __launch_bounds__(256)
+k_mf(const float* __restrict__ zbuf, int n_valid, int nc, float* __restrict__ snr,
+     uint8_t* __restrict__ width, uint32_t hist_key0, int n_bins, unsigned long long* __restrict__ ghist) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* s = reinterpret_cast<float*>(smem);                 // [kMaxLo + nc + kMaxHi + kVox]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(s + kMaxLo + nc + kMaxHi + kVox);
+  for (int i = threadIdx.x; i < n_bins; i += blockDim.x) hist[i] = 0;
+  const float floor_snr = key2f(hist_key0 << kHistShift);
+  for (int p = blockIdx.x; p < n_valid; p += gridDim.x) {
+    const float* zp = zbuf + static_cast<long long>(p) * nc;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kMaxLo + nc + kMaxHi + kVox; i += blockDim.x) {
+      const int k = i - kMaxLo;
+      s[i] = (k >= 0 && k < nc) ? zp[k] : 0.f;
+    }
+    __syncthreads();
+    for (int k0 = threadIdx.x * kVox; k0 < nc; k0 += blockDim.x * kVox) {
+      float P[kWin + 1];
+      P[0] = 0.f;
+#pragma unroll
+      for (int i = 0; i < kWin; ++i) P[i + 1] = P[i] + s[k0 + i];     // s index k0 + i <-> channel k0 - 49 + i
+      float best[kVox];
+      int bw[kVox];
+#pragma unroll
+      for (int j = 0; j < kVox; ++j) { best[j] = -INFINITY; bw[j] = 0; }
+#pragma unroll
+      for (int wi = 0; wi < kNW; ++wi) {
+        const int w = width_of(wi);
+        const int lo = (w - 1) / 2, hi = w - 1 - lo;
+#pragma unroll
+        for (int j = 0; j < kVox; ++j) {
+          const int k = k0 + j;
+          if (k - lo >= 0 && k + hi <= nc - 1) {
+            const float S = P[j + kMaxLo + hi + 1] - P[j + kMaxLo - lo];
+            const float v = S * rsqrt_width(wi);
+            if (v > best[j]) { best[j] = v; bw[j] = w; }
+          }
+        }
+      }
+      float* so = snr + static_cast<long long>(p) * nc + k0;
+      uint8_t* wo = width + static_cast<long long>(p) * nc + k0;
+#pragma unroll
+      for (int j = 0; j < kVox; ++j) {
+        if (k0 + j < nc) {
+          so[j] = best[j];
+          wo[j] = static_cast<uint8_t>(bw[j]);
+          if (best[j] >= floor_snr) {
+            int b = static_cast<int>((f2key(best[j]) >> kHistShift) - hist_key0);
+            if (b >= n_bins) b = n_bins - 1;
+            atomicAdd(&hist[b], 1u);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_bins; i += blockDim.x)
+    if (hist[i]) atomicAdd(ghist + i, static_cast<unsigned long long>(hist[i]));
+}
+
+// ---------------------------------------------------------- a11 compaction
+struct Det {
+  int coarse, p, k, width;
+  float snr;
+};
+
+__global__ void k_compact(const float* __restrict__ snr, const uint8_t* __restrict__ width,
+                          long long n, int n_valid, int nc, int coarse, float cut, Det* __restrict__ out,
+                          int cap, int* __restrict__ count) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float v = snr[i];
+    if (v >= cut) {
+      const int slot = atomicAdd(count, 1);
+      if (slot < cap) {
+        Det d;
+        d.coarse = coarse;
+        d.p = static_cast<int>(i / nc);
+        d.k = static_cast<int>(i - static_cast<long long>(d.p) * nc);
+        d.width = width[i];
+        d.snr = v;
+        out[slot] = d;
+      }
+    }
+  }
+}
+
+// scatter [pixel][k] arrays of one coarse block into [chan][N][N] (stage isolation)
+template <class T>
+__global__ void k_scatter(const T* __restrict__ src, const int* __restrict__ pix, int n_valid, int nc,
+                          int chan0, long long npix, T* __restrict__ dst) {
+  const long long n = static_cast<long long>(n_valid) * nc;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int p = static_cast<int>(i / nc), k = static_cast<int>(i - static_cast<long long>(p) * nc);
+    dst[static_cast<long long>(chan0 + k) * npix + pix[p]] = src[i];
+  }
+}
+
+__global__ void k_u8_to_i32(const uint8_t* __restrict__ a, long long n, int32_t* __restrict__ b) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    b[i] = a[i];
+}
+
+// ------------------------------------------------------------------ host side
+double log_q(double s) {
+  // ln of the upper Gaussian tail Q(s)
+  if (s < 25.0) return std::log(0.5 * std::erfc(s / std::sqrt(2.0)));
+  const double s2 = s * s;
+  const double series = 1.0 - 1.0 / s2 + 3.0 / (s2 * s2) - 15.0 / (s2 * s2 * s2) + 105.0 / (s2 * s2 * s2 * s2);
+  return -0.5 * s2 - std::log(s * std::sqrt(2.0 * M_PI)) + std::log(series);
+}
+
+double q_inverse(double p) {
+  // upper-tail Gaussian quantile by bisection on log_q
+  double lo = -10.0, hi = 60.0;
+  const double lp = std::log(p);
+  for (int i = 0; i < 200; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    if (log_q(mid) > lp) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+int window_channels(double df, double span) {
+  int w = static_cast<int>(std::floor(span / df)) + 1;
+  while (w * df <= span) ++w;
+  if (w % 2 == 0) ++w;
+  return w;
+}
+
+struct DetectPlan {
+  int n, n_coarse, n_chan;
+  long long npix;
+  std::vector<int> pix;        // in-horizon pixel indices
+  std::vector<int> nfft, chan0, half;
+  std::vector<long long> vox0; // voxel offset of each coarse block in snr/width
+  long long n_vox = 0;
+  int max_nc = 0;
+  int n_valid = 0;
+  bool stats_in_smem = false;
+};
+
+DetectPlan make_plan(int n_chan, int n, double cell, int n_coarse, const int32_t* nfft,
+                     double coarse_bw, double span) {
+  DetectPlan p;
+  p.n = n;
+  p.n_coarse = n_coarse;
+  p.n_chan = n_chan;
+  p.npix = static_cast<long long>(n) * n;
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      const double l = static_cast<double>(c - n / 2) * cell;
+      const double m = static_cast<double>(r - n / 2) * cell;
+      if (l * l + m * m < 1.0) p.pix.push_back(r * n + c);
+    }
+  p.n_valid = static_cast<int>(p.pix.size());
+  int c0 = 0;
+  for (int c = 0; c < n_coarse; ++c) {
+    p.nfft.push_back(nfft[c]);
+    p.chan0.push_back(c0);
+    p.vox0.push_back(p.n_vox);
+    p.half.push_back(window_channels(coarse_bw / nfft[c], span) / 2);
+    p.n_vox += static_cast<long long>(p.n_valid) * nfft[c];
+    p.max_nc = std::max(p.max_nc, static_cast<int>(nfft[c]));
+    c0 += nfft[c];
+  }
+  p.stats_in_smem = (static_cast<size_t>(p.n_valid) * 4 + 8192 + 256 + 32 + 16384) <= 231000;
+  return p;
+}
+
+constexpr int kMaxBins = 2048;
+constexpr int kDetCap = 1 << 22;
+
+struct DetectWs {
+  int* pix;
+  double* stats64;
+  float* stats32;
+  float* zbuf;
+  float* sv;
+  uint16_t* rank;
+  float* snr;
+  uint8_t* width;
+  unsigned long long* hist;
+  Det* dets;
+  int* count;
+};
+
+DetectWs carve_detect(void* ws, size_t bytes, const DetectPlan& p, size_t* need) {
+  Carver c(ws, bytes);
+  DetectWs w;
+  const size_t blk = static_cast<size_t>(p.n_valid) * p.max_nc;
+  w.pix = c.take<int>(p.n_valid > 0 ? p.n_valid : 1);
+  w.stats64 = c.take<double>(2 * static_cast<size_t>(p.n_chan));
+  w.stats32 = c.take<float>(2 * static_cast<size_t>(p.n_chan));
+  w.zbuf = c.take<float>(blk);
+  w.sv = c.take<float>(blk);
+  w.rank = c.take<uint16_t>(blk);
+  w.snr = c.take<float>(static_cast<size_t>(p.n_vox));
+  w.width = c.take<uint8_t>(static_cast<size_t>(p.n_vox));
+  w.hist = c.take<unsigned long long>(kMaxBins);
+  w.dets = c.take<Det>(kDetCap);
+  w.count = c.take<int>(4);
+  *need = c.used;
+  return w;
+}
+
+int validate(int n_chan, int n, double cell, int n_coarse, const int32_t* nfft) {
+  if (n_chan <= 0 || n_coarse <= 0 || !nfft || !(cell > 0.0)) return OVRO_ERR_INVALID_ARG;
+  if (!is_pow2(n) || n < 16 || n > 1024) return OVRO_ERR_UNSUPPORTED;
+  long long tot = 0;
+  for (int c = 0; c < n_coarse; ++c) {
+    if (nfft[c] <= 0) return OVRO_ERR_INVALID_ARG;
+    if (nfft[c] > 16384) return OVRO_ERR_UNSUPPORTED;
+    tot += nfft[c];
+  }
+  if (tot != n_chan) return OVRO_ERR_INVALID_ARG;
+  return OVRO_OK;
+}
+
+int run_stats(const float* d_img, const DetectPlan& p, const DetectWs& w, cudaStream_t st) {
+  const size_t base = 2048 * 4 + 64 * 4 + 8 * 4 + 2048 * 8;
+  const size_t sm = base + (p.stats_in_smem ? static_cast<size_t>(p.n_valid) * 4 : 0);
+  OVRO_CUDA_TRY(cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  k_stats<<<p.n_chan, 1024, sm, st>>>(d_img, w.pix, p.n_valid, p.npix, p.stats_in_smem ? 1 : 0,
+                                      w.stats64, w.stats32);
+  OVRO_LAUNCH_CHECK();
+  return OVRO_OK;
+}
+
+// a9 + a10 for every coarse block: snr/width [coarse][pixel][k] in the workspace.
+int run_filter(const float* d_img, const DetectPlan& p, const DetectWs& w, uint32_t hist_key0,
+               int n_bins, float* d_zp_out, cudaStream_t st) {
+  const int nsm = num_sms();
+  for (int c = 0; c < p.n_coarse; ++c) {
+    const int nc = p.nfft[c];
+    {
+      dim3 g((p.n_valid + 31) / 32, (nc + 31) / 32);
+      k_ztrans<<<g, 256, 0, st>>>(d_img, w.pix, p.n_valid, p.npix, p.chan0[c], nc, w.stats32, w.zbuf);
+      OVRO_LAUNCH_CHECK();
+    }
+    {
+      const int threads = 512, W = threads / 32;
+      const size_t sm = (256 * W + 32) * 4 + static_cast<size_t>(nc) * 12;
+      OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+      const int blocks = std::min(p.n_valid, 2 * nsm * 8);
+      k_rank<<<blocks, threads, sm, st>>>(w.zbuf, p.n_valid, nc, w.sv, w.rank);
+      OVRO_LAUNCH_CHECK();
+    }
+    {
+      const size_t sm = static_cast<size_t>((nc + 31) / 32) * kWalkThreads * 4;
+      OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+      k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(
+          w.zbuf, w.sv, w.rank, p.n_valid, nc, p.half[c]);
+      OVRO_LAUNCH_CHECK();
+    }
+    if (d_zp_out) {
+      k_scatter<float><<<4 * nsm, 256, 0, st>>>(w.zbuf, w.pix, p.n_valid, nc, p.chan0[c], p.npix, d_zp_out);
+      OVRO_LAUNCH_CHECK();
+    }
+    {
+      const size_t sm = static_cast<size_t>(kMaxLo + nc + kMaxHi + kVox) * 4 + static_cast<size_t>(n_bins) * 4;
+      OVRO_CUDA_TRY(cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+      const int blocks = std::min(p.n_valid, 4 * nsm * 4);
+      k_mf<<<blocks, 256, sm, st>>>(w.zbuf, p.n_valid, nc, w.snr + p.vox0[c], w.width + p.vox0[c],
+                                    hist_key0, n_bins, w.hist);
+      OVRO_LAUNCH_CHECK();
+    }
+  }
+  return OVRO_OK;
+}
+
+uint32_t host_f2key(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+float host_key2f(uint32_t k) {
+  const uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// histogram floor and bin count for a mode
+void hist_range(const ovro_detect_params& prm, uint32_t* key0, int* n_bins) {
+  double floor_snr;
+  if (prm.mode == OVRO_DETECT_FIXED) floor_snr = prm.nsigma;
+  else floor_snr = q_inverse(prm.alpha) - 0.01;
+  if (floor_snr < 0.25) floor_snr = 0.25;
+  // round the floor down to a bin edge
+  *key0 = host_f2key(static_cast<float>(floor_snr)) >> kHistShift;
+  const uint32_t top = (host_f2key(64.0f) >> kHistShift);
+  int nb = static_cast<int>(top > *key0 ? top - *key0 : 0) + 1;   // + overflow bin
+  if (nb > kMaxBins) nb = kMaxBins;
+  *n_bins = nb;
+}
+
+}  // namespace
+}  // namespace ovro
+
+extern "C" {
+
+int ovro_default_widths(int32_t* h_out_or_null) {
+  if (h_out_or_null)
+    for (int i = 0; i < ovro::kNW; ++i) h_out_or_null[i] = ovro::width_of(i);
+  return ovro::kNW;
+}
+
+size_t ovro_detect_workspace_size(int n_chan, int image_size, int n_coarse, const int32_t* h_nfft) {
+  using namespace ovro;
+  // the in-horizon pixel count depends on the cell; size for the largest (all pixels)
+  if (validate(n_chan, image_size, 1.0, n_coarse, h_nfft) != OVRO_OK) return 0;
+  DetectPlan p = make_plan(n_chan, image_size, 1e-9, n_coarse, h_nfft, 24000.0, 5000.0);
+  size_t need = 0;
+  carve_detect(nullptr, 0, p, &need);
+  return need;
+}
+
+int ovro_detect_stats(const float* d_img, int n_chan, int image_size, double cell_dircos, double* d_stats,
+                      void* d_ws, size_t ws_bytes, void* stream) {
+  using namespace ovro;
+  if (!d_img || !d_stats) return OVRO_ERR_INVALID_ARG;
+  const int32_t one[1] = {n_chan};
+  if (int e = validate(n_chan, image_size, cell_dircos, 1, one)) return e;
+  DetectPlan p = make_plan(n_chan, image_size, cell_dircos, 1, one, 24000.0, 5000.0);
+  if (p.n_valid == 0) return OVRO_ERR_INVALID_ARG;
+  size_t need = 0;
+  DetectWs w = carve_detect(d_ws, ws_bytes, p, &need);
+  if (int e = check_workspace(d_ws, ws_bytes, need)) return e;
+  cudaStream_t st = as_stream(stream);
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.pix, p.pix.data(), p.pix.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (int e = run_stats(d_img, p, w, st)) return e;
+  OVRO_CUDA_TRY(cudaMemcpyAsync(d_stats, w.stats64, 2 * sizeof(double) * n_chan, cudaMemcpyDeviceToDevice, st));
+  return OVRO_OK;
+}
+
+int ovro_detect_filter(const float* d_img, const double* d_stats, int n_chan, int image_size,
+                       double cell_dircos, int n_coarse, const int32_t* h_nfft,
+                       const ovro_detect_params* params, float* d_zp_or_null, float* d_snr,
+                       int32_t* d_width, void* d_ws, size_t ws_bytes, void* stream) {
+  using namespace ovro;
+  if (!d_img || !d_stats || !params || !d_snr || !d_width) return OVRO_ERR_INVALID_ARG;
+  if (int e = validate(n_chan, image_size, cell_dircos, n_coarse, h_nfft)) return e;
+  DetectPlan p = make_plan(n_chan, image_size, cell_dircos, n_coarse, h_nfft, params->coarse_bw_hz,
+                           params->highpass_hz);
+  if (p.n_valid == 0) return OVRO_ERR_INVALID_ARG;
+  size_t need = 0;
+  DetectWs w = carve_detect(d_ws, ws_bytes, p, &need);
+  if (int e = check_workspace(d_ws, ws_bytes, need)) return e;
+  cudaStream_t st = as_stream(stream);
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.pix, p.pix.data(), p.pix.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  k_stats32<<<(n_chan + 255) / 256, 256, 0, st>>>(d_stats, n_chan, w.stats32);
+  OVRO_LAUNCH_CHECK();
+  uint32_t key0;
+  int nb;
+  hist_range(*params, &key0, &nb);
+  OVRO_CUDA_TRY(cudaMemsetAsync(w.hist, 0, kMaxBins * sizeof(unsigned long long), st));
+  if (d_zp_or_null) OVRO_CUDA_TRY(cudaMemsetAsync(d_zp_or_null, 0, sizeof(float) * n_chan * p.npix, st));
+  OVRO_CUDA_TRY(cudaMemsetAsync(d_snr, 0, sizeof(float) * n_chan * p.npix, st));
+  OVRO_CUDA_TRY(cudaMemsetAsync(d_width, 0, sizeof(int32_t) * n_chan * p.npix, st));
+  if (int e = run_filter(d_img, p, w, key0, nb, d_zp_or_null, st)) return e;
+  const int nsm = num_sms();
+  for (int c = 0; c < p.n_coarse; ++c) {
+    k_scatter<float><<<4 * nsm, 256, 0, st>>>(w.snr + p.vox0[c], w.pix, p.n_valid, p.nfft[c], p.chan0[c],
+                                               p.npix, d_snr);
+    OVRO_LAUNCH_CHECK();
+    // widths: widen to int32 in the zbuf scratch, then scatter
+    const long long nv = static_cast<long long>(p.n_valid) * p.nfft[c];
+    int32_t* tmp = reinterpret_cast<int32_t*>(w.zbuf);
+    k_u8_to_i32<<<4 * nsm, 256, 0, st>>>(w.width + p.vox0[c], nv, tmp);
+    OVRO_LAUNCH_CHECK();
+    k_scatter<int32_t><<<4 * nsm, 256, 0, st>>>(tmp, w.pix, p.n_valid, p.nfft[c], p.chan0[c], p.npix, d_width);
+    OVRO_LAUNCH_CHECK();
+  }
+  return OVRO_OK;
+}
+
+int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dircos, int n_coarse,
+                const int32_t* h_nfft, const double* h_chan_freq_hz, const ovro_detect_params* params,
+                ovro_candidate* h_out, int max_out, int* n_out, void* d_ws, size_t ws_bytes,
+                void* stream) {
+  using namespace ovro;
+  if (!d_img || !params || !n_out || (max_out > 0 && !h_out) || max_out < 0 || !h_chan_freq_hz)
+    return OVRO_ERR_INVALID_ARG;
+  if (params->mode != OVRO_DETECT_BH && params->mode != OVRO_DETECT_FIXED) return OVRO_ERR_INVALID_ARG;
+  if (params->mode == OVRO_DETECT_BH && !(params->alpha > 0.0 && params->alpha <= 0.4))
+    return OVRO_ERR_INVALID_ARG;
+  if (!(params->highpass_hz > 0.0) || !(params->coarse_bw_hz > 0.0)) return OVRO_ERR_INVALID_ARG;
+  if (int e = validate(n_chan, image_size, cell_dircos, n_coarse, h_nfft)) return e;
+  DetectPlan p = make_plan(n_chan, image_size, cell_dircos, n_coarse, h_nfft, params->coarse_bw_hz,
+                           params->highpass_hz);
+  *n_out = 0;
+  if (p.n_valid == 0) return OVRO_OK;
+  size_t need = 0;
+  DetectWs w = carve_detect(d_ws, ws_bytes, p, &need);
+  if (int e = check_workspace(d_ws, ws_bytes, need)) return e;
+  cudaStream_t st = as_stream(stream);
+  int zero = 0;
+  OVRO_CUDA_TRY(cudaMemcpyToSymbolAsync(g_detect_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.pix, p.pix.data(), p.pix.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (int e = run_stats(d_img, p, w, st)) return e;
+  uint32_t key0;
+  int nb;
+  hist_range(*params, &key0, &nb);
+  OVRO_CUDA_TRY(cudaMemsetAsync(w.hist, 0, kMaxBins * sizeof(unsigned long long), st));
+  if (int e = run_filter(d_img, p, w, key0, nb, nullptr, st)) return e;
+
+  // ---- a11: threshold
+  std::vector<unsigned long long> hist(nb);
+  OVRO_CUDA_TRY(cudaMemcpyAsync(hist.data(), w.hist, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  int status = 0;
+  OVRO_CUDA_TRY(cudaMemcpyFromSymbolAsync(&status, g_detect_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (status) return OVRO_ERR_CAPACITY;
+  const double m = static_cast<double>(p.n_valid) * n_chan;
+  float cut;
+  if (params->mode == OVRO_DETECT_FIXED) {
+    cut = static_cast<float>(params->nsigma);
+  } else {
+    // lowest bin where a rejection is possible: Q(upper edge) <= alpha * count(>= lower edge) / m
+    unsigned long long above = 0;      // count(SNR >= lower edge of bin b)
+    int lowest = -1;
+    for (int b = nb - 1; b >= 0; --b) {
+      above += hist[b];
+      const double up = (b == nb - 1) ? 1e30 : static_cast<double>(host_key2f((key0 + b + 1) << kHistShift));
+      const double lq_up = up >= 1e29 ? -1e300 : log_q(up);
+      if (above > 0 && lq_up <= std::log(params->alpha * static_cast<double>(above) / m)) lowest = b;
+    }
+    if (lowest < 0) return OVRO_OK;    // nothing can be rejected
+    cut = host_key2f((key0 + lowest) << kHistShift);
+  }
+  // ---- gather everything at or above the cut
+  OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, sizeof(int), st));
+  const int nsm = num_sms();
+  for (int c = 0; c < p.n_coarse; ++c) {
+    const long long nv = static_cast<long long>(p.n_valid) * p.nfft[c];
+    k_compact<<<8 * nsm, 256, 0, st>>>(w.snr + p.vox0[c], w.width + p.vox0[c], nv, p.n_valid, p.nfft[c], c,
+                                       cut, w.dets, kDetCap, w.count);
+    OVRO_LAUNCH_CHECK();
+  }
+  int nd = 0;
+  OVRO_CUDA_TRY(cudaMemcpyAsync(&nd, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (nd > kDetCap) return OVRO_ERR_CAPACITY;
+  std::vector<Det> dets(nd);
+  if (nd) OVRO_CUDA_TRY(cudaMemcpy(dets.data(), w.dets, nd * sizeof(Det), cudaMemcpyDeviceToHost));
+  if (params->mode == OVRO_DETECT_BH) {
+    // exact step-up rule on the gathered set (all voxels with SNR >= cut are present)
+    std::vector<float> s(nd);
+    for (int i = 0; i < nd; ++i) s[i] = dets[i].snr;
+    std::sort(s.begin(), s.end(), std::greater<float>());
+    int kmax = 0;
+    for (int i = 1; i <= nd; ++i)
+      if (log_q(s[i - 1]) <= std::log(static_cast<double>(i) * params->alpha / m)) kmax = i;
+    if (kmax == 0) return OVRO_OK;
+    const float thr = s[kmax - 1];
+    dets.erase(std::remove_if(dets.begin(), dets.end(), [&](const Det& d) { return d.snr < thr; }), dets.end());
+  }
+  // ---- a12: greedy NMS per (pixel, coarse channel)
+  std::sort(dets.begin(), dets.end(), [](const Det& a, const Det& b) {
+    if (a.p != b.p) return a.p < b.p;
+    if (a.coarse != b.coarse) return a.coarse < b.coarse;
+    if (a.snr != b.snr) return a.snr > b.snr;
+    return a.k < b.k;
+  });
+  std::vector<Det> keep;
+  size_t i = 0;
+  while (i < dets.size()) {
+    size_t j = i;
+    while (j < dets.size() && dets[j].p == dets[i].p && dets[j].coarse == dets[i].coarse) ++j;
+    std::vector<Det> acc;
+    for (size_t q = i; q < j; ++q) {
+      bool sup = false;
+      for (const Det& a : acc)
+        if (std::abs(dets[q].k - a.k) <= std::max(1, a.width / 2)) { sup = true; break; }
+      if (!sup) acc.push_back(dets[q]);
+    }
+    std::sort(acc.begin(), acc.end(), [](const Det& a, const Det& b) { return a.k < b.k; });
+    keep.insert(keep.end(), acc.begin(), acc.end());
+    i = j;
+  }
+  const int total = static_cast<int>(keep.size());
+  *n_out = total;
+  const int nw = std::min(total, max_out);
+  for (int q = 0; q < nw; ++q) {
+    const Det& d = keep[q];
+    ovro_candidate& o = h_out[q];
+    const int pixel = p.pix[d.p];
+    o.coarse = d.coarse;
+    o.fine = d.k;
+    o.chan = p.chan0[d.coarse] + d.k;
+    o.row = pixel / image_size;
+    o.col = pixel % image_size;
+    o.width = d.width;
+    o.snr = d.snr;
+    o.pad_ = 0.f;
+    o.freq_hz = h_chan_freq_hz[o.chan];
+    o.log10_p = log_q(d.snr) / std::log(10.0);
+  }
+  return total > max_out ? OVRO_ERR_CAPACITY : OVRO_OK;
+}
+
+}  // extern "C"

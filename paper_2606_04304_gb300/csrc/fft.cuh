@@ -1,0 +1,143 @@
+// In-register radix-R DFTs and a shared-memory Stockham FFT used by the
+// upchannelizer and the imaging kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace ovro {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <int R>
+struct BitRev {
+  static __device__ __forceinline__ constexpr int of(int x) {
+    int r = 0;
+    for (int b = 1, m = R >> 1; b < R; b <<= 1, m >>= 1)
+      if (x & b) r |= m;
+    return r;
+  }
+};
+
+// V[k] = sum_r v[r] exp(-2 pi i r k / R), natural order in and out.
+template <int R>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+  float2 t[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) t[i] = v[BitRev<R>::of(i)];
+#pragma unroll
+  for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+    for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+      for (int j = 0; j < h; ++j) {
+        float2 x = t[b + j + h];
+        if (j != 0) {
+          // w = exp(-2 pi i j / (2h)) = exp(-2 pi i (j * 8 / h) / 16)
+          const int q = j * (8 / h);
+          float cw, sw;
+          switch (q) {
+            case 1: cw = 0.92387953251128674f; sw = -0.38268343236508977f; break;
+            case 2: cw = 0.70710678118654752f; sw = -0.70710678118654752f; break;
+            case 3: cw = 0.38268343236508977f; sw = -0.92387953251128674f; break;
+            case 4: cw = 0.0f; sw = -1.0f; break;
+            case 5: cw = -0.38268343236508977f; sw = -0.92387953251128674f; break;
+            case 6: cw = -0.70710678118654752f; sw = -0.70710678118654752f; break;
+            default: cw = -0.92387953251128674f; sw = -0.38268343236508977f; break;
+          }
+          if (q == 4) {
+            x = make_float2(x.y, -x.x);           // multiply by -i
+          } else {
+            x = cmul(x, make_float2(cw, sw));
+          }
+        }
+        const float2 a = t[b + j];
+        t[b + j] = make_float2(a.x + x.x, a.y + x.y);
+        t[b + j + h] = make_float2(a.x - x.x, a.y - x.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+
+// Forward FFTs (exp(-2 pi i k n / N)) of `count` rows of length N = 2^LOG2N
+// stored in `a` with row stride `ld` >= N; `b` is a scratch buffer of the same
+// shape.  Stockham auto-sort: radix-16 passes, then one radix-2/4/8 pass.
+// All threads of the block take part; returns the buffer holding the result.
+// tw: omega_{N * tw_stride}^k table.
+template <int LOG2N>
+__device__ float2* fft_rows_pingpong(float2* a, float2* b, int count, int ld,
+                                     const float2* __restrict__ tw, int tw_stride) {
+  constexpr int N = 1 << LOG2N;
+  constexpr int n16 = LOG2N / 4;
+  constexpr int rem = LOG2N % 4;
+  constexpr int n_pass = n16 + (rem ? 1 : 0);
+  int Ns = 1;
+  float2* src = a;
+  float2* dst = b;
+#pragma unroll 1
+  for (int p = 0; p < n_pass; ++p) {
+    const int R = (p < n16) ? 16 : (1 << rem);
+    const int per = N / R;
+    const int total = count * per;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int f = t / per, j = t - f * per;
+      const int k = j & (Ns - 1);
+      const float2* s = src + f * ld;
+      float2* d = dst + f * ld;
+      const int o = (j / Ns) * Ns * R + k;
+      const int base = k * (N / (Ns * R));
+      if (R == 16) {
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = s[j + r * per];
+        if (Ns > 1) {
+#pragma unroll
+          for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], __ldg(tw + (r * base) * tw_stride));
+        }
+        dft_reg<16>(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) d[o + r * Ns] = v[r];
+      } else if (R == 8) {
+        float2 v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = s[j + r * per];
+        if (Ns > 1) {
+#pragma unroll
+          for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], __ldg(tw + (r * base) * tw_stride));
+        }
+        dft_reg<8>(v);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) d[o + r * Ns] = v[r];
+      } else if (R == 4) {
+        float2 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = s[j + r * per];
+        if (Ns > 1) {
+#pragma unroll
+          for (int r = 1; r < 4; ++r) v[r] = cmul(v[r], __ldg(tw + (r * base) * tw_stride));
+        }
+        dft_reg<4>(v);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) d[o + r * Ns] = v[r];
+      } else {
+        float2 v[2];
+        v[0] = s[j];
+        v[1] = s[j + per];
+        if (Ns > 1) v[1] = cmul(v[1], __ldg(tw + base * tw_stride));
+        dft_reg<2>(v);
+        d[o] = v[0];
+        d[o + Ns] = v[1];
+      }
+    }
+    __syncthreads();
+    float2* t = src; src = dst; dst = t;
+    Ns *= R;
+  }
+  return src;
+}
+
+}  // namespace ovro

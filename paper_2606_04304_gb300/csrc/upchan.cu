@@ -1,0 +1,531 @@
+// a1-a3: unpack 4+4-bit voltages, FFT upchannelizer, 8-bit requantisation.
+//
+// Section 2.1 of the paper: each ~24 kHz coarse channel is upchannelized by an
+// FFT over its time samples, and the fine-channel voltages are correlated by an
+// 8-bit X-engine.  One CTA handles one spectrum (N consecutive samples) of a
+// group of G adjacent inputs: it stages the G-byte-wide rows of packed samples
+// in shared memory, runs F FFTs at a time (Stockham auto-sort, radix-16 passes
+// through a shared exchange buffer, 16 complex values per thread in registers),
+// requantises in the last pass and writes the int8 spectra for all G inputs
+// with row-contiguous stores, so the output for fine channel k' is one
+// 2G-byte run in [k'][spectrum][input] order -- the layout the X-engine reads.
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace ovro {
+namespace {
+
+constexpr int kMaxLog2N = 14;
+constexpr int kMaxN = 1 << kMaxLog2N;
+
+// ---------------------------------------------------------------- power pass
+// Exact sum over the used samples of re^2 + im^2 per (coarse, input).
+__device__ __forceinline__ uint32_t sample_power(uint32_t b) {
+  int re = static_cast<int>(static_cast<int8_t>(b)) >> 4;
+  int im = static_cast<int>(static_cast<int8_t>(b << 4)) >> 4;
+  return static_cast<uint32_t>(re * re + im * im);
+}
+
+template <int VW>
+__global__ void k_power(const uint8_t* __restrict__ volt, int n_input, long long n_used,
+                        unsigned long long* __restrict__ power) {
+  // thread = one VW-byte column of the row; blocks stride over rows
+  const int nvec = (n_input + VW - 1) / VW;
+  const int v = blockIdx.y * blockDim.x + threadIdx.x;
+  if (v >= nvec) return;
+  uint32_t acc[VW];
+#pragma unroll
+  for (int j = 0; j < VW; ++j) acc[j] = 0;
+  const bool full = (v + 1) * VW <= n_input;
+#pragma unroll 4
+  for (long long r = blockIdx.x; r < n_used; r += gridDim.x) {
+    const uint8_t* p = volt + r * n_input + static_cast<long long>(v) * VW;
+    if (VW == 16) {
+      const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
+      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[q * 4 + b] += sample_power((ws[q] >> (8 * b)) & 0xffu);
+    } else if (VW == 4) {
+      const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(p));
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[b] += sample_power((w >> (8 * b)) & 0xffu);
+    } else {
+#pragma unroll
+      for (int b = 0; b < VW; ++b)
+        if (full || v * VW + b < n_input) acc[b] += sample_power(p[b]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < VW; ++j)
+    if (v * VW + j < n_input && acc[j]) atomicAdd(power + v * VW + j, static_cast<unsigned long long>(acc[j]));
+}
+
+// s = 8 sqrt(2) / sqrt(N P), P = power / n_used, in FP64; rounded to FP32.
+__global__ void k_scale(const unsigned long long* __restrict__ power, const double* __restrict__ user,
+                        int n, int nfft, long long n_used, float* __restrict__ scale) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s;
+  if (user) {
+    s = user[i];
+  } else {
+    double pbar = static_cast<double>(power[i]) / static_cast<double>(n_used);
+    s = pbar > 0.0 ? (8.0 * sqrt(2.0)) / sqrt(static_cast<double>(nfft) * pbar) : 0.0;
+  }
+  scale[i] = static_cast<float>(s);
+}
+
+// omega_N^k = exp(-2 pi i k / N) for the largest N in the call, FP64 -> FP32.
+__global__ void k_twiddle(float2* tw, int n) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double s, c;
+  sincospi(-2.0 * static_cast<double>(k) / static_cast<double>(n), &s, &c);
+  tw[k] = make_float2(static_cast<float>(c), static_cast<float>(s));
+}
+
+// --------------------------------------------------------- FFT + requantise
+struct UpchanArgs {
+  const uint8_t* volt;      // this coarse channel, [n_time][n_input]
+  const float2* tw;         // omega_{tw_n}^k
+  const float* scale;       // [n_input] for this coarse channel
+  int8_t* out_q;            // this coarse block, [N][K][n_input][2]
+  float* out_f;             // same layout, floats (optional)
+  int n_input;
+  int n_spec;
+  int tw_n;
+  int group;                // G inputs per CTA
+};
+
+// Radix schedule for N = 2^LOG2N: passes of 16, then one of 2^(LOG2N % 4).
+template <int LOG2N>
+struct Plan {
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int R0 = LOG2N < 4 ? N : 16;                 // radix of the first pass
+  static constexpr int n16 = LOG2N / 4;
+  static constexpr int rem = LOG2N % 4;
+  static constexpr int n_pass = LOG2N < 4 ? 1 : n16 + (rem ? 1 : 0);
+  static constexpr int VPT = R0;                                // values per thread per pass
+  static constexpr int F = (LOG2N >= 13) ? 1 : (LOG2N < 4 ? 256 : (8192 >> LOG2N));  // FFTs in flight
+  static constexpr int THREADS = F * N / VPT;
+};
+
+template <int R, int VPT>
+__device__ __forceinline__ void radix_pass_compute(float2 (&val)[VPT], int N, int Ns, int j0,
+                                                   int jstep, const float2* __restrict__ tw,
+                                                   int tw_stride) {
+  // val holds VPT / R butterflies, butterfly b at val[b*R .. b*R+R)
+#pragma unroll
+  for (int b = 0; b < VPT / R; ++b) {
+    const int j = j0 + b * jstep;
+    const int k = j & (Ns - 1);
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = val[b * R + r];
+    if (Ns > 1) {
+      const int base = k * (N / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + static_cast<long long>(r * base) * tw_stride));
+    }
+    dft_reg<R>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) val[b * R + r] = v[r];
+  }
+}
+
+template <int LOG2N>
+__global__ void __launch_bounds__(Plan<LOG2N>::THREADS)
+k_upchan(UpchanArgs a) {
+  using P = Plan<LOG2N>;
+  constexpr int N = P::N;
+  constexpr int VPT = P::VPT;
+  constexpr int F = P::F;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int G = a.group;
+  float2* buf = reinterpret_cast<float2*>(smem);                       // [F][N]
+  uint8_t* raw = smem + static_cast<size_t>(F) * N * sizeof(float2);   // [N][G]
+  int8_t* stg = reinterpret_cast<int8_t*>(raw + static_cast<size_t>(N) * G);  // [N][G][2]
+  float* sc = reinterpret_cast<float*>(
+      stg + ((static_cast<size_t>(N) * G * 2 + 15) & ~static_cast<size_t>(15)));  // [G]
+
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
+  const int s = blockIdx.y;
+  const int i0 = blockIdx.x * G;
+  const int gv = min(G, a.n_input - i0);        // valid inputs in this group
+  const long long row0 = static_cast<long long>(s) * N;
+
+  // stage the packed rows
+  {
+    const uint8_t* src = a.volt + row0 * a.n_input + i0;
+    if (gv == G && (G % 4) == 0 && (a.n_input % 4) == 0) {
+      const int wpr = G / 4;
+      for (int idx = tid; idx < N * wpr; idx += T) {
+        const int n = idx / wpr, w = idx - n * wpr;
+        reinterpret_cast<uint32_t*>(raw)[idx] =
+            *reinterpret_cast<const uint32_t*>(src + static_cast<long long>(n) * a.n_input + 4 * w);
+      }
+    } else {
+      for (int idx = tid; idx < N * G; idx += T) {
+        const int n = idx / G, g = idx - n * G;
+        raw[idx] = g < gv ? src[static_cast<long long>(n) * a.n_input + g] : 0;
+      }
+    }
+    for (int g = tid; g < G; g += T) sc[g] = g < gv ? a.scale[i0 + g] : 0.0f;
+  }
+  __syncthreads();
+
+  const int tw_stride = a.tw_n / N;
+  constexpr int BPT = VPT / P::R0;                      // butterflies per thread (first pass)
+  for (int f0 = 0; f0 < G; f0 += F) {
+    // ---- pass 0: from the packed samples
+    float2 val[VPT];
+    int Ns = 1;
+    {
+      constexpr int R = P::R0;
+      // thread -> (fft f, butterfly j); F*N/R butterflies, BPT per thread
+      const int per_fft = N / R;
+#pragma unroll
+      for (int b = 0; b < BPT; ++b) {
+        const int gb = tid + b * T;
+        const int f = gb / per_fft, j = gb - f * per_fft;
+        const int g = f0 + f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float2 x = make_float2(0.f, 0.f);
+          if (f < F && g < G) {
+            const uint32_t byte = raw[(j + r * per_fft) * G + g];
+            x.x = static_cast<float>(static_cast<int>(static_cast<int8_t>(byte)) >> 4);
+            x.y = static_cast<float>(static_cast<int>(static_cast<int8_t>(byte << 4)) >> 4);
+          }
+          val[b * R + r] = x;
+        }
+      }
+      // all butterflies in this thread share the same j layout rule
+#pragma unroll
+      for (int b = 0; b < BPT; ++b) {
+        const int gb = tid + b * T;
+        const int j = gb % (N / R);
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = val[b * R + r];
+        dft_reg<R>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) val[b * R + r] = v[r];
+        (void)j;
+      }
+    }
+
+    // ---- write pass-0 results (or finish if single pass), then middle passes
+    auto store_pass = [&](int R, int Ns_cur) {
+      const int per_fft = N / R;
+      const int nb = VPT / R;
+      for (int b = 0; b < nb; ++b) {
+        const int gb = tid + b * T;
+        const int f = gb / per_fft, j = gb - f * per_fft;
+        if (f >= F) continue;
+        const int k = j & (Ns_cur - 1);
+        const int dst = (j / Ns_cur) * Ns_cur * R + k;
+        for (int r = 0; r < R; ++r) buf[f * N + dst + r * Ns_cur] = val[b * R + r];
+      }
+    };
+    auto load_pass = [&](int R) {
+      const int per_fft = N / R;
+      const int nb = VPT / R;
+      for (int b = 0; b < nb; ++b) {
+        const int gb = tid + b * T;
+        const int f = gb / per_fft, j = gb - f * per_fft;
+        for (int r = 0; r < R; ++r)
+          val[b * R + r] = f < F ? buf[f * N + j + r * per_fft] : make_float2(0.f, 0.f);
+      }
+    };
+
+    // requantise + stage: butterfly outputs at natural bins, fftshifted
+    auto emit = [&](int R, int Ns_cur) {
+      const int per_fft = N / R;
+      const int nb = VPT / R;
+      for (int b = 0; b < nb; ++b) {
+        const int gb = tid + b * T;
+        const int f = gb / per_fft, j = gb - f * per_fft;
+        const int g = f0 + f;
+        if (f >= F || g >= gv) continue;
+        const float s_g = sc[g];
+        const int k = j & (Ns_cur - 1);
+        const int q0 = (j / Ns_cur) * Ns_cur * R + k;
+        for (int r = 0; r < R; ++r) {
+          const int kp = (q0 + r * Ns_cur + N / 2) & (N - 1);
+          const float2 X = val[b * R + r];
+          float qr = rintf(__fmul_rn(s_g, X.x));
+          float qi = rintf(__fmul_rn(s_g, X.y));
+          qr = fminf(fmaxf(qr, -127.f), 127.f);
+          qi = fminf(fmaxf(qi, -127.f), 127.f);
+          char2 q2;
+          q2.x = static_cast<signed char>(qr);
+          q2.y = static_cast<signed char>(qi);
+          reinterpret_cast<char2*>(stg)[kp * G + g] = q2;
+          if (a.out_f) {
+            const long long o = ((static_cast<long long>(kp) * a.n_spec + s) * a.n_input + i0 + g);
+            reinterpret_cast<float2*>(a.out_f)[o] = X;
+          }
+        }
+      }
+    };
+
+    if (P::n_pass == 1) {
+      emit(P::R0, 1);
+    } else {
+      store_pass(P::R0, 1);
+      Ns = P::R0;
+      __syncthreads();
+      for (int p = 1; p < P::n_pass; ++p) {
+        const bool last = (p == P::n_pass - 1);
+        const int R = (p < P::n16) ? 16 : (1 << P::rem);
+        load_pass(R);
+        __syncthreads();
+        const int per_fft = N / R;
+        switch (R) {
+          case 16: {
+            float2 v16[VPT];
+#pragma unroll
+            for (int i = 0; i < VPT; ++i) v16[i] = val[i];
+            const int gb0 = tid;
+            radix_pass_compute<16, VPT>(v16, N, Ns, gb0 % per_fft, T, a.tw, tw_stride);
+#pragma unroll
+            for (int i = 0; i < VPT; ++i) val[i] = v16[i];
+            break;
+          }
+          case 8: {
+            for (int b = 0; b < VPT / 8; ++b) {
+              const int j = (tid + b * T) % per_fft;
+              float2 v[8];
+#pragma unroll
+              for (int r = 0; r < 8; ++r) v[r] = val[b * 8 + r];
+              float2 vv[8];
+#pragma unroll
+              for (int r = 0; r < 8; ++r) vv[r] = v[r];
+              radix_pass_compute<8, 8>(vv, N, Ns, j, 0, a.tw, tw_stride);
+#pragma unroll
+              for (int r = 0; r < 8; ++r) val[b * 8 + r] = vv[r];
+            }
+            break;
+          }
+          case 4: {
+            for (int b = 0; b < VPT / 4; ++b) {
+              const int j = (tid + b * T) % per_fft;
+              float2 vv[4];
+#pragma unroll
+              for (int r = 0; r < 4; ++r) vv[r] = val[b * 4 + r];
+              radix_pass_compute<4, 4>(vv, N, Ns, j, 0, a.tw, tw_stride);
+#pragma unroll
+              for (int r = 0; r < 4; ++r) val[b * 4 + r] = vv[r];
+            }
+            break;
+          }
+          default: {
+            for (int b = 0; b < VPT / 2; ++b) {
+              const int j = (tid + b * T) % per_fft;
+              float2 vv[2];
+              vv[0] = val[b * 2];
+              vv[1] = val[b * 2 + 1];
+              radix_pass_compute<2, 2>(vv, N, Ns, j, 0, a.tw, tw_stride);
+              val[b * 2] = vv[0];
+              val[b * 2 + 1] = vv[1];
+            }
+            break;
+          }
+        }
+        if (last) {
+          emit(R, Ns);
+        } else {
+          store_pass(R, Ns);
+          __syncthreads();
+        }
+        Ns *= R;
+      }
+    }
+    __syncthreads();   // buf reused by the next group of F inputs
+  }
+
+  // ---- write the staged int8 spectra: row k' is 2*gv contiguous bytes
+  {
+    int8_t* dst0 = a.out_q + (static_cast<long long>(s) * a.n_input + i0) * 2;
+    const long long row_stride = static_cast<long long>(a.n_spec) * a.n_input * 2;
+    if (gv == G && (G % 2) == 0) {
+      const int wpr = G / 2;           // 4-byte words per row
+      for (int idx = tid; idx < N * wpr; idx += T) {
+        const int kp = idx / wpr, w = idx - kp * wpr;
+        *reinterpret_cast<uint32_t*>(dst0 + kp * row_stride + 4 * w) =
+            reinterpret_cast<const uint32_t*>(stg)[idx];
+      }
+    } else {
+      for (int idx = tid; idx < N * gv; idx += T) {
+        const int kp = idx / gv, g = idx - kp * gv;
+        *reinterpret_cast<char2*>(dst0 + kp * row_stride + 2 * g) =
+            reinterpret_cast<const char2*>(stg)[kp * G + g];
+      }
+    }
+  }
+}
+
+int group_for(int log2n, int n_input) {
+  // G inputs per CTA so that raw (G N) + staging (2 G N) + exchange (8 F N) fit.
+  const int N = 1 << log2n;
+  const int F = log2n >= 13 ? 1 : (log2n < 4 ? 256 : (8192 >> log2n));
+  const size_t budget = 200 * 1024;
+  const size_t xbuf = static_cast<size_t>(F) * N * 8;
+  int G = 1;
+  while (G < 64 && (xbuf + 3ull * (2 * G) * N + 4 * 2 * G) <= budget) G *= 2;
+  if (G < F) G = F;
+  int np2 = 1;
+  while (np2 < n_input) np2 *= 2;
+  if (G > np2) G = np2;
+  return G;
+}
+
+size_t smem_for(int log2n, int G) {
+  const int N = 1 << log2n;
+  const int F = log2n >= 13 ? 1 : (log2n < 4 ? 256 : (8192 >> log2n));
+  return static_cast<size_t>(F) * N * 8 + static_cast<size_t>(N) * G +
+         ((static_cast<size_t>(N) * G * 2 + 15) & ~static_cast<size_t>(15)) + 4 * G + 16;
+}
+
+template <int L>
+int launch_upchan_t(const UpchanArgs& a, cudaStream_t st) {
+  using P = Plan<L>;
+  const size_t sm = smem_for(L, a.group);
+  auto kern = k_upchan<L>;
+  OVRO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(sm)));
+  dim3 grid((a.n_input + a.group - 1) / a.group, a.n_spec);
+  kern<<<grid, P::THREADS, sm, st>>>(a);
+  OVRO_LAUNCH_CHECK();
+  return OVRO_OK;
+}
+
+int launch_upchan(int log2n, const UpchanArgs& a, cudaStream_t st) {
+  switch (log2n) {
+    case 1: return launch_upchan_t<1>(a, st);
+    case 2: return launch_upchan_t<2>(a, st);
+    case 3: return launch_upchan_t<3>(a, st);
+    case 4: return launch_upchan_t<4>(a, st);
+    case 5: return launch_upchan_t<5>(a, st);
+    case 6: return launch_upchan_t<6>(a, st);
+    case 7: return launch_upchan_t<7>(a, st);
+    case 8: return launch_upchan_t<8>(a, st);
+    case 9: return launch_upchan_t<9>(a, st);
+    case 10: return launch_upchan_t<10>(a, st);
+    case 11: return launch_upchan_t<11>(a, st);
+    case 12: return launch_upchan_t<12>(a, st);
+    case 13: return launch_upchan_t<13>(a, st);
+    case 14: return launch_upchan_t<14>(a, st);
+    default: return OVRO_ERR_UNSUPPORTED;
+  }
+}
+
+struct UpchanWs {
+  unsigned long long* power;
+  float* scale;
+  double* user;
+  float2* tw;
+};
+
+UpchanWs carve_upchan(void* ws, size_t bytes, int n_input, int n_coarse, size_t* need) {
+  Carver c(ws, bytes);
+  UpchanWs w;
+  w.power = c.take<unsigned long long>(static_cast<size_t>(n_input) * n_coarse);
+  w.scale = c.take<float>(static_cast<size_t>(n_input) * n_coarse);
+  w.user = c.take<double>(static_cast<size_t>(n_input) * n_coarse);
+  w.tw = c.take<float2>(kMaxN);
+  *need = c.used;
+  return w;
+}
+
+}  // namespace
+}  // namespace ovro
+
+extern "C" {
+
+size_t ovro_upchan_workspace_size(int n_input, int n_coarse) {
+  if (n_input <= 0 || n_coarse <= 0) return 0;
+  size_t need = 0;
+  ovro::carve_upchan(nullptr, 0, n_input, n_coarse, &need);
+  return need;
+}
+
+int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time,
+                const int32_t* h_nfft, const double* h_scale_or_null, int8_t* d_fine_q,
+                float* d_fine_f32_or_null, void* d_ws, size_t ws_bytes, void* stream) {
+  using namespace ovro;
+  if (!d_volt || !h_nfft || !d_fine_q || n_input <= 0 || n_coarse <= 0 || n_time <= 0)
+    return OVRO_ERR_INVALID_ARG;
+  int max_n = 2;
+  for (int c = 0; c < n_coarse; ++c) {
+    const int n = h_nfft[c];
+    if (n <= 0) return OVRO_ERR_INVALID_ARG;
+    if (!is_pow2(n) || n < 2 || n > kMaxN || n_time < n) return OVRO_ERR_UNSUPPORTED;
+    if (n > max_n) max_n = n;
+  }
+  size_t need = 0;
+  UpchanWs w = carve_upchan(d_ws, ws_bytes, n_input, n_coarse, &need);
+  if (int e = check_workspace(d_ws, ws_bytes, need)) return e;
+  cudaStream_t st = as_stream(stream);
+
+  k_twiddle<<<(max_n + 255) / 256, 256, 0, st>>>(w.tw, max_n);
+  OVRO_LAUNCH_CHECK();
+  const size_t nsc = static_cast<size_t>(n_input) * n_coarse;
+  if (h_scale_or_null) {
+    OVRO_CUDA_TRY(cudaMemcpyAsync(w.user, h_scale_or_null, nsc * sizeof(double),
+                                  cudaMemcpyHostToDevice, st));
+  } else {
+    OVRO_CUDA_TRY(cudaMemsetAsync(w.power, 0, nsc * sizeof(unsigned long long), st));
+  }
+  long long q_off = 0;
+  for (int c = 0; c < n_coarse; ++c) {
+    const int n = h_nfft[c];
+    const long long k = n_time / n;
+    const long long n_used = k * n;
+    if (!h_scale_or_null) {
+      const int vw = (n_input % 16 == 0) ? 16 : ((n_input % 4 == 0) ? 4 : 1);
+      const int nvec = (n_input + vw - 1) / vw;
+      const int threads = nvec >= 256 ? 256 : ((nvec + 31) / 32) * 32;
+      const long long rows = n_used < 8LL * num_sms() ? n_used : 8LL * num_sms();
+      dim3 grid(static_cast<unsigned>(rows), (nvec + threads - 1) / threads);
+      const uint8_t* vc = d_volt + static_cast<long long>(c) * n_time * n_input;
+      unsigned long long* pc = w.power + static_cast<size_t>(c) * n_input;
+      if (vw == 16)
+        k_power<16><<<grid, threads, 0, st>>>(vc, n_input, n_used, pc);
+      else if (vw == 4)
+        k_power<4><<<grid, threads, 0, st>>>(vc, n_input, n_used, pc);
+      else
+        k_power<1><<<grid, threads, 0, st>>>(vc, n_input, n_used, pc);
+      OVRO_LAUNCH_CHECK();
+    }
+    k_scale<<<(n_input + 255) / 256, 256, 0, st>>>(
+        w.power + static_cast<size_t>(c) * n_input,
+        h_scale_or_null ? w.user + static_cast<size_t>(c) * n_input : nullptr, n_input, n,
+        n_used, w.scale + static_cast<size_t>(c) * n_input);
+    OVRO_LAUNCH_CHECK();
+
+    UpchanArgs a;
+    a.volt = d_volt + static_cast<long long>(c) * n_time * n_input;
+    a.tw = w.tw;
+    a.scale = w.scale + static_cast<size_t>(c) * n_input;
+    a.out_q = d_fine_q + q_off;
+    a.out_f = d_fine_f32_or_null ? d_fine_f32_or_null + q_off : nullptr;
+    a.n_input = n_input;
+    a.n_spec = static_cast<int>(k);
+    a.tw_n = max_n;
+    const int l = ilog2(n);
+    a.group = group_for(l, n_input);
+    if (int e = launch_upchan(l, a, st)) return e;
+    q_off += static_cast<long long>(n) * k * n_input * 2;
+  }
+  return OVRO_OK;
+}
+
+}  // extern "C"

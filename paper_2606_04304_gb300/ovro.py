@@ -1,0 +1,268 @@
+"""Thin Python binding of the C ABI in include/ovro.h (argument marshalling only).
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+computation runs in libovro.so.  Importing this module loads the library and
+raises immediately if it has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libovro.so")
+
+OVRO_OK = 0
+XENG_TC, XENG_FP32 = 0, 1
+STORE_FP32, STORE_BF16, STORE_FP16 = 0, 1, 2
+DETECT_BH, DETECT_FIXED = 0, 1
+
+
+class OvroError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        msg = _lib.ovro_status_string(status).decode()
+        last = _lib.ovro_last_error().decode()
+        super().__init__(f"{fn} -> {msg}" + (f" ({last})" if last else ""))
+
+
+class DetectParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("alpha", ctypes.c_double), ("nsigma", ctypes.c_double),
+                ("highpass_hz", ctypes.c_double), ("coarse_bw_hz", ctypes.c_double)]
+
+
+class Candidate(ctypes.Structure):
+    _fields_ = [("coarse", ctypes.c_int32), ("fine", ctypes.c_int32), ("chan", ctypes.c_int32),
+                ("row", ctypes.c_int32), ("col", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("snr", ctypes.c_float), ("pad_", ctypes.c_float), ("freq_hz", ctypes.c_double),
+                ("log10_p", ctypes.c_double)]
+
+
+CANDIDATE_DTYPE = np.dtype([("coarse", "<i4"), ("fine", "<i4"), ("chan", "<i4"), ("row", "<i4"),
+                            ("col", "<i4"), ("width", "<i4"), ("snr", "<f4"), ("pad_", "<f4"),
+                            ("freq_hz", "<f8"), ("log10_p", "<f8")])
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(the library has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, L, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "ovro_status_string": (ctypes.c_char_p, [I]),
+        "ovro_last_error": (ctypes.c_char_p, []),
+        "ovro_version": (I, []),
+        "ovro_launch_count": (ctypes.c_ulonglong, []),
+        "ovro_upchan_workspace_size": (S, [I, I]),
+        "ovro_upchan": (I, [P, I, I, L, P, P, P, P, P, S, P]),
+        "ovro_correlate": (I, [P, I, I, I, I, P, P]),
+        "ovro_correlate_status": (I, [P]),
+        "ovro_grid_image_workspace_size": (S, [I, I, I, I]),
+        "ovro_grid_image": (I, [P, I, P, P, I, I, D, I, P, P, P, S, P]),
+        "ovro_uvw": (I, [P, I, P, I, I, D, P, P, P, S, P]),
+        "ovro_default_widths": (I, [P]),
+        "ovro_detect_workspace_size": (S, [I, I, I, P]),
+        "ovro_detect": (I, [P, I, I, D, I, P, P, P, P, I, P, P, S, P]),
+        "ovro_detect_stats": (I, [P, I, I, D, P, P, S, P]),
+        "ovro_detect_filter": (I, [P, P, I, I, D, I, P, P, P, P, P, P, S, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def launch_count() -> int:
+    return int(_lib.ovro_launch_count())
+
+
+def _check(fn: str, status: int) -> int:
+    if status != OVRO_OK:
+        raise OvroError(fn, status)
+    return status
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream: Optional[torch.cuda.Stream] = None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _host(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _cuda(t: torch.Tensor, dtype: torch.dtype, name: str):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
+
+
+def fine_elements(nfft: Sequence[int], n_time: int, n_input: int) -> int:
+    return int(sum(n * (n_time // n) * n_input * 2 for n in nfft))
+
+
+# ---------------------------------------------------------------------- a1-a3
+def upchan(volt: torch.Tensor, nfft: Sequence[int], scales=None, want_f32: bool = False,
+           out_q: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None):
+    """volt: uint8 [n_coarse][n_time][n_input] on the GPU.  Returns (q int8, f32 or None),
+    both flat in the coarse-major [N][K][n_input][2] block layout of ovro_upchan."""
+    _cuda(volt, torch.uint8, "volt")
+    n_coarse, n_time, n_input = volt.shape
+    nf = _host(nfft, np.int32)
+    total = fine_elements(nf, n_time, n_input)
+    q = out_q if out_q is not None else torch.empty(total, dtype=torch.int8, device=volt.device)
+    f = torch.empty(total, dtype=torch.float32, device=volt.device) if want_f32 else None
+    need = _lib.ovro_upchan_workspace_size(n_input, n_coarse)
+    ws = ws if ws is not None and ws.numel() >= need else workspace(need, volt.device)
+    sc = None if scales is None else _host(scales, np.float64)
+    _check("ovro_upchan", _lib.ovro_upchan(
+        _ptr(volt), n_input, n_coarse, n_time, nf.ctypes.data_as(ctypes.c_void_p),
+        None if sc is None else sc.ctypes.data_as(ctypes.c_void_p), _ptr(q), _ptr(f), _ptr(ws),
+        ws.numel(), _stream(stream)))
+    return q, f
+
+
+# ------------------------------------------------------------------------- a4
+def n_baselines(n_ant: int) -> int:
+    return n_ant * (n_ant + 1) // 2
+
+
+def correlate(q: torch.Tensor, n_ant: int, n_chan: int, n_spec: int, mode: int = XENG_TC,
+              out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """q: int8 [n_chan][n_spec][2 n_ant][2] (flat ok).  Returns int32 [n_chan][n_bl][4][2]."""
+    _cuda(q, torch.int8, "q")
+    vis = out if out is not None else torch.empty((n_chan, n_baselines(n_ant), 4, 2), dtype=torch.int32,
+                                                  device=q.device)
+    _check("ovro_correlate", _lib.ovro_correlate(_ptr(q), n_ant, n_chan, n_spec, mode, _ptr(vis),
+                                                 _stream(stream)))
+    return vis
+
+
+def correlate_status(stream=None) -> int:
+    return _lib.ovro_correlate_status(_stream(stream))
+
+
+# ---------------------------------------------------------------------- a5-a7
+def grid_image_workspace_size(n_ant: int, n_chan: int, image_size: int, storage: int = STORE_FP32) -> int:
+    return _lib.ovro_grid_image_workspace_size(n_ant, n_chan, image_size, storage)
+
+
+def grid_image(vis: torch.Tensor, ant_enu_m, freqs_hz, image_size: int, cell: float,
+               storage: int = STORE_FP32, out: Optional[torch.Tensor] = None,
+               ws: Optional[torch.Tensor] = None, want_counts: bool = False, stream=None):
+    """vis: int32 [n_chan][n_bl][4][2].  Returns float images [n_chan][N][N] (and counts)."""
+    _cuda(vis, torch.int32, "vis")
+    pos = _host(ant_enu_m, np.float64)
+    fr = _host(freqs_hz, np.float64)
+    n_ant, n_chan = pos.shape[0], fr.shape[0]
+    img = out if out is not None else torch.empty((n_chan, image_size, image_size), dtype=torch.float32,
+                                                  device=vis.device)
+    cnt = torch.empty(n_chan, dtype=torch.int32, device=vis.device) if want_counts else None
+    need = grid_image_workspace_size(n_ant, n_chan, image_size, storage)
+    ws = ws if ws is not None and ws.numel() >= need else workspace(need, vis.device)
+    _check("ovro_grid_image", _lib.ovro_grid_image(
+        _ptr(vis), n_ant, pos.ctypes.data_as(ctypes.c_void_p), fr.ctypes.data_as(ctypes.c_void_p), n_chan,
+        image_size, float(cell), storage, _ptr(img), _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)))
+    return (img, cnt) if want_counts else img
+
+
+def uvw(ant_enu_m, freqs_hz, image_size: int, cell: float, stream=None):
+    """a5 alone: int32 (p_u, p_v) [n_chan][n_cross], positions in 1/1024 cell."""
+    pos = _host(ant_enu_m, np.float64)
+    fr = _host(freqs_hz, np.float64)
+    n_ant, n_chan = pos.shape[0], fr.shape[0]
+    n_cross = n_ant * (n_ant - 1) // 2
+    pu = torch.empty((n_chan, n_cross), dtype=torch.int32, device="cuda")
+    pv = torch.empty_like(pu)
+    need = grid_image_workspace_size(n_ant, n_chan, image_size)
+    ws = workspace(need)
+    _check("ovro_uvw", _lib.ovro_uvw(pos.ctypes.data_as(ctypes.c_void_p), n_ant,
+                                     fr.ctypes.data_as(ctypes.c_void_p), n_chan, image_size, float(cell),
+                                     _ptr(pu), _ptr(pv), _ptr(ws), ws.numel(), _stream(stream)))
+    return pu, pv
+
+
+# --------------------------------------------------------------------- a8-a12
+def default_widths() -> np.ndarray:
+    n = _lib.ovro_default_widths(None)
+    out = np.zeros(n, np.int32)
+    _lib.ovro_default_widths(out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def detect_params(mode: int = DETECT_BH, alpha: float = 0.01, nsigma: float = 10.0,
+                  highpass_hz: float = 5000.0, coarse_bw_hz: float = 24000.0) -> DetectParams:
+    return DetectParams(mode, alpha, nsigma, highpass_hz, coarse_bw_hz)
+
+
+def detect_workspace_size(n_chan: int, image_size: int, nfft: Sequence[int]) -> int:
+    nf = _host(nfft, np.int32)
+    return _lib.ovro_detect_workspace_size(n_chan, image_size, len(nf), nf.ctypes.data_as(ctypes.c_void_p))
+
+
+def detect(img: torch.Tensor, cell: float, nfft: Sequence[int], freqs_hz, params: Optional[DetectParams] = None,
+           max_out: int = 1 << 20, ws: Optional[torch.Tensor] = None, stream=None) -> np.ndarray:
+    """Stage I search; returns a structured array of candidates (CANDIDATE_DTYPE)."""
+    _cuda(img, torch.float32, "img")
+    n_chan, n, _ = img.shape
+    nf = _host(nfft, np.int32)
+    fr = _host(freqs_hz, np.float64)
+    prm = params or detect_params()
+    need = detect_workspace_size(n_chan, n, nf)
+    ws = ws if ws is not None and ws.numel() >= need else workspace(need, img.device)
+    out = np.zeros(max_out, CANDIDATE_DTYPE)
+    n_out = ctypes.c_int(0)
+    st = _lib.ovro_detect(_ptr(img), n_chan, n, float(cell), len(nf), nf.ctypes.data_as(ctypes.c_void_p),
+                          fr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm),
+                          out.ctypes.data_as(ctypes.c_void_p), max_out, ctypes.byref(n_out), _ptr(ws),
+                          ws.numel(), _stream(stream))
+    _check("ovro_detect", st)
+    return out[: n_out.value]
+
+
+def detect_stats(img: torch.Tensor, cell: float, stream=None) -> torch.Tensor:
+    _cuda(img, torch.float32, "img")
+    n_chan, n, _ = img.shape
+    stats = torch.empty((n_chan, 2), dtype=torch.float64, device=img.device)
+    ws = workspace(detect_workspace_size(n_chan, n, [n_chan]), img.device)
+    _check("ovro_detect_stats", _lib.ovro_detect_stats(_ptr(img), n_chan, n, float(cell), _ptr(stats), _ptr(ws),
+                                                       ws.numel(), _stream(stream)))
+    return stats
+
+
+def detect_filter(img: torch.Tensor, stats: torch.Tensor, cell: float, nfft: Sequence[int],
+                  params: Optional[DetectParams] = None, want_zp: bool = False, stream=None):
+    """Returns (zp or None, snr, width), each [n_chan][N][N]."""
+    _cuda(img, torch.float32, "img")
+    _cuda(stats, torch.float64, "stats")
+    n_chan, n, _ = img.shape
+    nf = _host(nfft, np.int32)
+    prm = params or detect_params()
+    zp = torch.empty_like(img) if want_zp else None
+    snr = torch.empty_like(img)
+    wid = torch.empty(img.shape, dtype=torch.int32, device=img.device)
+    ws = workspace(detect_workspace_size(n_chan, n, nf), img.device)
+    _check("ovro_detect_filter", _lib.ovro_detect_filter(
+        _ptr(img), _ptr(stats), n_chan, n, float(cell), len(nf), nf.ctypes.data_as(ctypes.c_void_p),
+        ctypes.byref(prm), _ptr(zp), _ptr(snr), _ptr(wid), _ptr(ws), ws.numel(), _stream(stream)))
+    return zp, snr, wid

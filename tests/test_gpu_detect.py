@@ -1,0 +1,117 @@
+"""GPU parity: MAD statistics (exact), running-median high-pass, boxcar bank,
+Benjamini-Hochberg and NMS against the oracle, stage by stage."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import detect as OD, imaging as OI
+
+pytestmark = pytest.mark.gpu
+
+
+def _cube(g, n_chan, n, tones=()):
+    x = g.normal(0.3, 2.0, (n_chan, n, n)).astype(np.float32)
+    for (f, r, c, a) in tones:
+        x[f, r, c] += a
+    return x
+
+
+@pytest.mark.parametrize("n,cell", [(64, 2.0 / 64), (32, 0.01), (128, 2.0 / 128)])
+def test_stats_exact(lib, n, cell):
+    g = np.random.default_rng(n)
+    cube = _cube(g, 7, n)
+    cube[3] = 0.0                      # MAD = 0 channel
+    cube[4, :, : n // 2] = 1.5         # many ties at the median
+    mask = OI.horizon_mask(n, cell)
+    st = lib.detect_stats(torch.from_numpy(cube).cuda(), cell).cpu().numpy()
+    for f in range(7):
+        med, mad = OD.channel_stats(cube[f], mask)
+        assert st[f, 0] == med and st[f, 1] == mad, (f, st[f], med, mad)
+
+
+def _filter_vs_oracle(lib, cube, cell, nfft, tol_snr=2e-4):
+    n = cube.shape[1]
+    mask = OI.horizon_mask(n, cell)
+    d = torch.from_numpy(cube).cuda()
+    st = lib.detect_stats(d, cell)
+    zp, snr, wid = lib.detect_filter(d, st, cell, nfft, want_zp=True)
+    zp, snr, wid = zp.cpu().numpy(), snr.cpu().numpy(), wid.cpu().numpy()
+    # the oracle from the same standardised cube (stage isolation for a9-a10)
+    stats = st.cpu().numpy()
+    z = np.zeros(cube.shape)
+    for f in range(cube.shape[0]):
+        if stats[f, 1] > 0:
+            z[f][mask] = (cube[f][mask].astype(np.float64) - stats[f, 0]) / (OD.MAD_TO_SIGMA * stats[f, 1])
+    bounds = OD.chan_bounds_of(nfft)
+    wins = [OD.window_channels(24000.0 / k) for k in nfft]
+    zpo = OD.highpass(z, bounds, wins)
+    zpo[:, ~mask] = 0
+    assert np.abs(zp - zpo).max() < 1e-5 * max(1.0, np.abs(zpo).max())
+    so, wo = OD.matched_filter(zpo, bounds)
+    so[:, ~mask] = 0
+    wo[:, ~mask] = 0
+    assert np.abs(snr - so).max() < tol_snr
+    # widths agree except where two widths tie within the tolerance
+    diff = wid != wo
+    if diff.any():
+        f, r, c = np.nonzero(diff)
+        for ff, rr, cc in zip(f[:50], r[:50], c[:50]):
+            assert abs(snr[ff, rr, cc] - so[ff, rr, cc]) < tol_snr
+    return snr, so, mask
+
+
+@pytest.mark.parametrize("nfft", [[256, 256], [64, 128, 64], [16, 8, 200 - 24]])
+def test_filter_small(lib, nfft):
+    g = np.random.default_rng(sum(nfft))
+    n, cell = 32, 0.02
+    cube = _cube(g, sum(nfft), n, tones=[(10, 16, 16, 30.0), (sum(nfft) - 1, 3, 20, 20.0)])
+    _filter_vs_oracle(lib, cube, cell, nfft)
+
+
+def test_filter_long_window_c2_shape(lib):
+    # 8192-channel coarse channel (window 1707) on a small pixel grid
+    g = np.random.default_rng(11)
+    n, cell = 16, 0.3                  # 37 pixels above the horizon
+    cube = _cube(g, 8192, n, tones=[(4000, 8, 8, 12.0)])
+    _filter_vs_oracle(lib, cube, cell, [8192])
+
+
+def test_detect_bh_and_fixed(lib):
+    g = np.random.default_rng(5)
+    nfft = [256, 256]
+    n, cell = 32, 0.02
+    tones = [(40, 10, 12, 25.0), (300, 20, 5, 15.0), (301, 20, 5, 14.0), (450, 7, 7, 9.0)]
+    cube = _cube(g, sum(nfft), n, tones=tones)
+    mask = OI.horizon_mask(n, cell)
+    freqs = synth.fine_freqs_hz(nfft)
+    d = torch.from_numpy(cube).cuda()
+    for mode, kw in ((lib.DETECT_BH, dict(alpha=0.01)), (lib.DETECT_FIXED, dict(nsigma=6.0))):
+        prm = lib.detect_params(mode=mode, **kw)
+        got = lib.detect(d, cell, nfft, freqs, prm)
+        ref = OD.detect(cube.astype(np.float64), mask, nfft, mode="bh" if mode == lib.DETECT_BH else "fixed",
+                        **({"alpha": 0.01} if mode == lib.DETECT_BH else {"nsigma": 6.0}))
+        gs = {(int(c["chan"]), int(c["row"]), int(c["col"]), int(c["width"])) for c in got}
+        rs = {(c.chan, c.row, c.col, c.width) for c in ref}
+        assert gs == rs, (sorted(gs ^ rs)[:10])
+        assert len(gs) >= 3
+        for c in got:
+            assert c["freq_hz"] == freqs[c["chan"]]
+
+
+def test_tiny_pipeline_end_to_end(lib):
+    cfg = synth.make_config("tiny", cell_dircos=0.005)
+    volt = synth.generate(cfg)
+    pos = synth.antenna_positions(cfg)
+    freqs = synth.fine_freqs_hz(cfg.nfft)
+    q, _ = lib.upchan(torch.from_numpy(volt).cuda(), cfg.nfft)
+    vis = lib.correlate(q, cfg.n_ant, cfg.n_chan_total, cfg.n_spec[0])
+    img = lib.grid_image(vis, pos, freqs, cfg.image_size, cfg.cell)
+    got = lib.detect(img, cfg.cell, cfg.nfft, freqs)
+    mask = OI.horizon_mask(cfg.image_size, cfg.cell)
+    ref = OD.detect(img.cpu().numpy().astype(np.float64), mask, cfg.nfft)
+    gs = {(int(c["chan"]), int(c["row"]), int(c["col"])) for c in got}
+    rs = {(c.chan, c.row, c.col) for c in ref}
+    assert gs == rs
+    t = cfg.tones[0]
+    assert (sum(cfg.nfft[: t.coarse]) + t.fine, t.row, t.col) in gs
