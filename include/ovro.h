@@ -125,13 +125,14 @@ int ovro_correlate_status(void* stream);
  * Section 2.2: every fine channel is imaged over the visible hemisphere
  * (dirty images are the search product).  Stokes I = (XX + YY) / 2 of every
  * cross baseline, natural weights, zenith phase centre (planar array, w = 0).
- * u = (x_a - x_b) s_nu cells, s_nu = nu / (c du), du = 1 / (N cell), one
- * FP64 multiply; position rounded to 1/1024 cell; separable 7 x 7 kernel
- * psi_0(7 pi / 2, x / 3.5); a baseline whose footprint (or its mirror's)
- * leaves the grid is dropped.  Image = Re sum G exp(+2 pi i (u l + v m)),
- * divided by (gridded visibilities incl. mirrors) and the grid correction;
- * pixel (r, c) <-> l = (c - N/2) cell, m = (r - N/2) cell; pixels with
- * l^2 + m^2 >= 1 are 0.
+ * The uv grid is padded by 2 (G = 2N cells a side) and the image is the
+ * central N x N of its transform.  u = (x_a - x_b) s_nu cells,
+ * s_nu = nu / (c du), du = 1 / (G cell), one FP64 multiply; position rounded
+ * to 1/1024 cell; separable 7 x 7 kernel psi_0(7 pi / 2, x / 3.5); a baseline
+ * whose footprint (or its mirror's) leaves the grid is dropped.
+ * Image = Re sum G exp(+2 pi i (u l + v m)), divided by (gridded visibilities
+ * incl. mirrors) and the grid correction; pixel (r, c) <-> l = (c - N/2) cell,
+ * m = (r - N/2) cell; pixels with l^2 + m^2 >= 1 are 0.
  *
  * d_vis           int32 [n_chan][n_bl][4][2] as produced by ovro_correlate.
  * h_ant_enu_m     [n_ant][3] antenna positions, metres (only E, N are used).
@@ -154,7 +155,7 @@ int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
                     int32_t* d_n_gridded_or_null, void* d_ws, size_t ws_bytes, void* stream);
 
 /* a5 on its own: p = rint(u Q), Q = 1024, the rounded uv position in 1/1024
- * cell of every cross baseline (a < b, row-major order) in every channel,
+ * cell of the padded (2 image_size) grid of every cross baseline (a < b, row-major order) in every channel,
  * int32 [n_chan][n_cross] (saturated at +-2^30).  The FP64 product of the
  * definition is reproduced exactly.  Workspace: ovro_grid_image_workspace_size
  * with the same n_ant, n_chan and image_size. */

@@ -5,9 +5,14 @@ The paper images every fine channel over the visible hemisphere on a
 are the search product).  Readings where the paper is silent:
 
 * Stokes I = (XX + YY) / 2, autocorrelations excluded, natural weights.
-* uv in grid cells: u = (x_a - x_b) * s_nu with s_nu = nu / (c * du),
-  du = 1 / (N * cell); one FP64 multiply per coordinate.  Zenith phase centre
-  with a planar array, so w = 0.
+* The uv grid is padded by 2, as imagers such as WSClean pad theirs: it has
+  G = 2N cells a side, du = 1 / (G * cell), and the image is the central
+  N x N of the G x G transform.  Without padding the horizon of an all-sky
+  image sits where the kernel's transform has fallen to ~2e-4, and dividing
+  by it amplifies round-off and aliasing there by ~5000.
+* uv in grid cells: u = (x_a - x_b) * s_nu with s_nu = nu / (c * du); one
+  FP64 multiply per coordinate.  Zenith phase centre with a planar array, so
+  w = 0.
 * Each visibility V at (u, v) and its mirror conj(V) at (-u, -v) is
   convolved onto the grid with a separable 7 x 7 prolate-spheroidal kernel
   C(x) = psi_0(c, x / 3.5) / psi_0(c, 0), c = 7 pi / 2, tabulated at Q = 1024
@@ -15,11 +20,11 @@ are the search product).  Readings where the paper is silent:
   p = rint(u Q); centre cell c0 = p / Q rounded half away from zero (so a
   visibility at -p has centre -c0 and its footprint is the exact point
   reflection); the tap at cell c0 + t takes table sample t Q - (p - c0 Q).
-* A baseline whose footprint (or its mirror's) leaves the N x N grid is
+* A baseline whose footprint (or its mirror's) leaves the G x G grid is
   dropped and counted.
 * Image I(r, c) = Re sum_grid G exp(+2 pi i (u l + v m)) / (sum w * C^(r) C^(c)),
   with pixel (r, c) <-> l = (c - N/2) cell, m = (r - N/2) cell and grid
-  correction C^(d) = (1/Q) sum_m C(m/Q) cos(2 pi m d / (Q N)), the Fourier
+  correction C^(d) = (1/Q) sum_m C(m/Q) cos(2 pi m d / (Q G)), the Fourier
   transform of the tabulated kernel.  sum w counts gridded visibilities,
   mirrors included.  Pixels with l^2 + m^2 >= 1 (below the horizon) are 0.
 """
@@ -31,6 +36,7 @@ import numpy as np
 from numpy.polynomial import legendre as npleg
 
 C_LIGHT = 299_792_458.0
+PAD = 2
 SUPPORT = 7
 OVERSAMPLE = 1024
 PSWF_C = math.pi * SUPPORT / 2.0
@@ -76,20 +82,21 @@ def kernel_table(support: int = SUPPORT, q: int = OVERSAMPLE, c: float = PSWF_C)
     return pswf_psi0(m / q / (support / 2.0), c)
 
 
-def grid_correction(table: np.ndarray, n: int, q: int = OVERSAMPLE) -> np.ndarray:
-    """C^(d) for pixel offsets d = -N/2 .. N/2 - 1 (Fourier transform of the table)."""
+def grid_correction(table: np.ndarray, n: int, q: int = OVERSAMPLE, g: int = 0) -> np.ndarray:
+    """C^(d) for pixel offsets d = -N/2 .. N/2 - 1 on a G-cell grid (default G = PAD N)."""
+    g = g or PAD * n
     half = (table.size - 1) // 2
     m = np.arange(-half, half + 1, dtype=np.float64)
     d = np.arange(-n // 2, n // 2, dtype=np.float64)
-    return (table[None, :] * np.cos(2 * np.pi * np.outer(d, m) / (q * n))).sum(axis=1) / q
+    return (table[None, :] * np.cos(2 * np.pi * np.outer(d, m) / (q * g))).sum(axis=1) / q
 
 
 # --------------------------------------------------------------------------------------
 # uvw and gridding
 # --------------------------------------------------------------------------------------
-def cells_per_metre(nu_hz, n: int, cell: float):
-    """s_nu = nu / (c * du), du = 1 / (N cell): grid cells per metre of baseline."""
-    du = 1.0 / (n * cell)
+def cells_per_metre(nu_hz, g: int, cell: float):
+    """s_nu = nu / (c * du), du = 1 / (G cell): grid cells per metre of baseline."""
+    du = 1.0 / (g * cell)
     return np.asarray(nu_hz, dtype=np.float64) / (C_LIGHT * du)
 
 
@@ -117,8 +124,8 @@ def _taps(p: np.ndarray, n: int, q: int):
 
 
 def grid_channel(vis_chan, pos, nu_hz, n, cell, table, q=OVERSAMPLE):
-    """FP64 uv grid G[kv][ku] of one channel, plus the number of gridded
-    visibilities (mirrors included) and of dropped baselines."""
+    """FP64 uv grid G[kv][ku] (n = G cells a side) of one channel, plus the number
+    of gridded visibilities (mirrors included) and of dropped baselines."""
     n_ant = pos.shape[0]
     a, b, idx = _cross_pairs(n_ant)
     vi = stokes_i(vis_chan)[idx]
@@ -158,9 +165,12 @@ def horizon_mask(n: int, cell: float) -> np.ndarray:
 
 
 def image_from_grid(G, n_grid, n, cell, corr):
-    """Dirty image from an FP64 grid: exp(+) transform with centred axes."""
-    raw = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(G))) * (n * n)
-    img = raw.real / (max(n_grid, 1) * np.outer(corr, corr))
+    """Dirty N x N image from an FP64 G x G grid: exp(+) transform with centred
+    axes, central N x N kept."""
+    g = G.shape[0]
+    raw = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(G))) * (g * g)
+    o = g // 2 - n // 2
+    img = raw[o:o + n, o:o + n].real / (max(n_grid, 1) * np.outer(corr, corr))
     img[~horizon_mask(n, cell)] = 0.0
     return img
 
@@ -172,7 +182,7 @@ def dirty_images(vis, pos, freqs_hz, n, cell, channels=None):
     chans = range(vis.shape[0]) if channels is None else channels
     imgs, ngrid, ndrop = [], [], []
     for c in chans:
-        G, ng, nd = grid_channel(vis[c], pos, freqs_hz[c], n, cell, table)
+        G, ng, nd = grid_channel(vis[c], pos, freqs_hz[c], PAD * n, cell, table)
         imgs.append(image_from_grid(G, ng, n, cell, corr))
         ngrid.append(ng)
         ndrop.append(nd)

@@ -15,8 +15,12 @@
 //      reflection), with a separable 7 x 7 prolate-spheroidal kernel.  k_bin
 //      sorts visibilities into row bands of the grid; k_grid accumulates one
 //      band per CTA in shared memory with shared-memory atomics.
-//  a7  The grid is transformed by row FFTs (k_fft_rows) and column FFTs
-//      (k_fft_cols); the centring shifts become a (-1)^(ku+kv) sign at
+//  a7  The uv grid is padded by 2 (G = 2N cells a side, du = 1 / (G cell)) and
+//      the image is the central N x N of its transform, as padded imagers do:
+//      the horizon then sits where the kernel's transform is still > 0.25, so
+//      the grid correction does not amplify FP32 round-off.  The grid is
+//      transformed by row FFTs (k_fft_rows) and column FFTs of the N central
+//      columns (k_fft_cols); the centring shifts become a (-1)^(ku+kv) sign at
 //      gridding time and (-1)^(r+c) at output, the exp(+) transform becomes a
 //      forward transform of the conjugated grid, and the column pass applies
 //      normalisation, the grid correction and the horizon mask while writing
@@ -35,6 +39,7 @@ constexpr int kQ = kOversample;
 constexpr int kHalfTab = kSupport * kOversample / 2;
 constexpr int kTabLen = 2 * kHalfTab + 1;
 constexpr int kHalfSup = kSupport / 2;
+constexpr int kPad = 2;              // uv grid cells per image pixel, per axis
 
 struct Baseline {
   double dx, dy;
@@ -234,39 +239,40 @@ k_fft_rows(float2* __restrict__ grids, int rows_per_cta, const float2* __restric
     reinterpret_cast<float4*>(g)[i] = reinterpret_cast<const float4*>(res)[i];
 }
 
-template <int LOG2N>
+template <int LOG2G>
 __global__ void __launch_bounds__(512)
-k_fft_cols(const float2* __restrict__ grids, int cols_per_cta, int ch0, const float2* __restrict__ tw,
-           const float* __restrict__ inv_corr, const uint8_t* __restrict__ mask,
-           const int* __restrict__ kept, float* __restrict__ img) {
-  constexpr int N = 1 << LOG2N;
-  constexpr int LD = N + 1;
+k_fft_cols(const float2* __restrict__ grids, int n_img, int cols_per_cta, int ch0,
+           const float2* __restrict__ tw, const float* __restrict__ inv_corr,
+           const uint8_t* __restrict__ mask, const int* __restrict__ kept, float* __restrict__ img) {
+  constexpr int G = 1 << LOG2G;
+  constexpr int LD = G + 1;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* A = reinterpret_cast<float2*>(smem);
   float2* B = A + cols_per_cta * LD;
   const int C = cols_per_cta;
   const int cb = blockIdx.y;
-  const int c0 = blockIdx.x * C;
-  const float2* g = grids + static_cast<long long>(cb) * N * N;
-  for (int i = threadIdx.x; i < N * C; i += blockDim.x) {
+  const int off = G / 2 - n_img / 2;                  // first central grid row/column
+  const int c0 = blockIdx.x * C;                      // image column of this strip
+  const float2* g = grids + static_cast<long long>(cb) * G * G;
+  for (int i = threadIdx.x; i < G * C; i += blockDim.x) {
     const int r = i / C, c = i - r * C;
-    A[c * LD + r] = g[static_cast<long long>(r) * N + c0 + c];
+    A[c * LD + r] = g[static_cast<long long>(r) * G + off + c0 + c];
   }
   __syncthreads();
-  const float2* res = fft_rows_pingpong<LOG2N>(A, B, C, LD, tw, 1);
+  const float2* res = fft_rows_pingpong<LOG2G>(A, B, C, LD, tw, 1);
   const long long chan = ch0 + cb;
   const int k = kept[chan];
   const float norm = k > 0 ? 1.0f / static_cast<float>(k) : 0.0f;
-  float* out = img + chan * N * N;
-  for (int i = threadIdx.x; i < N * C; i += blockDim.x) {
+  float* out = img + chan * n_img * n_img;
+  for (int i = threadIdx.x; i < n_img * C; i += blockDim.x) {
     const int r = i / C, c = i - r * C;
     const int col = c0 + c;
     float v = 0.0f;
-    if (mask[r * N + col]) {
-      v = res[c * LD + r].x * norm * inv_corr[r] * inv_corr[col];
+    if (mask[r * n_img + col]) {
+      v = res[c * LD + off + r].x * norm * inv_corr[r] * inv_corr[col];
       if ((r + col) & 1) v = -v;
     }
-    out[static_cast<long long>(r) * N + col] = v;
+    out[static_cast<long long>(r) * n_img + col] = v;
   }
 }
 
@@ -294,27 +300,33 @@ __global__ void k_counts_out(const int* __restrict__ kept, int n_chan, int32_t* 
 
 // ---------------------------------------------------------------- planning
 struct ImgPlan {
-  int n, log2n, band_h, n_bands, batch, rows_per_cta, cols_per_cta;
+  int n, g, log2g, band_h, n_bands, batch, rows_per_cta, cols_per_cta;
   long long n_cross, cap;
 };
 
 ImgPlan make_plan(int n_ant, int n_chan, int n) {
   ImgPlan p;
   p.n = n;
-  p.log2n = ilog2(n);
-  p.band_h = 16384 / n < n ? 16384 / n : n;          // band of <= 128 KB FP32 complex
-  p.n_bands = n / p.band_h;
-  const long long grid_bytes = 8LL * n * n;
+  p.g = kPad * n;
+  p.log2g = ilog2(p.g);
+  p.band_h = 16384 / p.g < p.g ? 16384 / p.g : p.g;   // band of <= 128 KB FP32 complex
+  p.n_bands = p.g / p.band_h;
+  p.n_cross = static_cast<long long>(n_ant) * (n_ant - 1) / 2;
+  p.cap = p.n_cross > 0 ? p.n_cross : 1;
+  const long long grid_bytes = 8LL * p.g * p.g;
+  const long long list_bytes = 16LL * p.n_bands * p.cap;
   long long b = (64LL << 20) / grid_bytes;
+  const long long bl = (512LL << 20) / list_bytes;
+  if (bl < b) b = bl;
   if (b < 1) b = 1;
   if (b > 64) b = 64;
   if (b > n_chan) b = n_chan;
   p.batch = static_cast<int>(b);
-  p.rows_per_cta = 8192 / n < n ? 8192 / n : n;
-  p.cols_per_cta = 8192 / n < n ? 8192 / n : n;
-  if (p.cols_per_cta > 32) p.cols_per_cta = 32;
-  p.n_cross = static_cast<long long>(n_ant) * (n_ant - 1) / 2;
-  p.cap = p.n_cross > 0 ? p.n_cross : 1;
+  p.rows_per_cta = 8192 / p.g < p.g ? 8192 / p.g : p.g;
+  int c = 8192 / p.g;
+  if (c > n) c = n;
+  if (c > 32) c = 32;
+  p.cols_per_cta = c;
   return p;
 }
 
@@ -338,7 +350,7 @@ ImgWs carve_img(void* ws, size_t bytes, const ImgPlan& p, int n_ant, int n_chan,
   ImgWs w;
   w.tab = c.take<float>(kTabLen);
   w.inv_corr = c.take<float>(p.n);
-  w.tw = c.take<float2>(p.n);
+  w.tw = c.take<float2>(p.g);
   w.mask = c.take<uint8_t>(static_cast<size_t>(p.n) * p.n);
   w.ant = c.take<double>(static_cast<size_t>(n_ant) * 3);
   w.freq = c.take<double>(n_chan);
@@ -347,28 +359,28 @@ ImgWs carve_img(void* ws, size_t bytes, const ImgPlan& p, int n_ant, int n_chan,
   w.kept = c.take<int>(n_chan);
   w.list_cnt = c.take<int>(static_cast<size_t>(p.batch) * p.n_bands);
   w.lists = c.take<int4>(static_cast<size_t>(p.batch) * p.n_bands * p.cap);
-  w.grids = c.take<float2>(static_cast<size_t>(p.batch) * p.n * p.n);
+  w.grids = c.take<float2>(static_cast<size_t>(p.batch) * p.g * p.g);
   *need = c.used;
   return w;
 }
 
 template <int L>
 int launch_ffts(const ImgPlan& p, const ImgWs& w, int ch0, int nb, float* img, cudaStream_t st) {
-  constexpr int N = 1 << L;
+  constexpr int G = 1 << L;
   {
-    const size_t sm = 2ull * p.rows_per_cta * N * sizeof(float2);
+    const size_t sm = 2ull * p.rows_per_cta * G * sizeof(float2);
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm)));
-    dim3 grid(N / p.rows_per_cta, nb);
+    dim3 grid(G / p.rows_per_cta, nb);
     k_fft_rows<L><<<grid, 512, sm, st>>>(w.grids, p.rows_per_cta, w.tw);
     OVRO_LAUNCH_CHECK();
   }
   {
-    const size_t sm = 2ull * p.cols_per_cta * (N + 1) * sizeof(float2);
+    const size_t sm = 2ull * p.cols_per_cta * (G + 1) * sizeof(float2);
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm)));
-    dim3 grid(N / p.cols_per_cta, nb);
-    k_fft_cols<L><<<grid, 512, sm, st>>>(w.grids, p.cols_per_cta, ch0, w.tw, w.inv_corr, w.mask,
+    dim3 grid(p.n / p.cols_per_cta, nb);
+    k_fft_cols<L><<<grid, 512, sm, st>>>(w.grids, p.n, p.cols_per_cta, ch0, w.tw, w.inv_corr, w.mask,
                                          w.kept, img);
     OVRO_LAUNCH_CHECK();
   }
@@ -376,14 +388,14 @@ int launch_ffts(const ImgPlan& p, const ImgWs& w, int ch0, int nb, float* img, c
 }
 
 int run_ffts(const ImgPlan& p, const ImgWs& w, int ch0, int nb, float* img, cudaStream_t st) {
-  switch (p.log2n) {
-    case 4: return launch_ffts<4>(p, w, ch0, nb, img, st);
+  switch (p.log2g) {
     case 5: return launch_ffts<5>(p, w, ch0, nb, img, st);
     case 6: return launch_ffts<6>(p, w, ch0, nb, img, st);
     case 7: return launch_ffts<7>(p, w, ch0, nb, img, st);
     case 8: return launch_ffts<8>(p, w, ch0, nb, img, st);
     case 9: return launch_ffts<9>(p, w, ch0, nb, img, st);
     case 10: return launch_ffts<10>(p, w, ch0, nb, img, st);
+    case 11: return launch_ffts<11>(p, w, ch0, nb, img, st);
     default: return OVRO_ERR_UNSUPPORTED;
   }
 }
@@ -392,7 +404,7 @@ int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_a
                   const double* h_freq, int n_chan, double cell, cudaStream_t st) {
   const KernelTables& kt = kernel_tables();
   std::vector<double> corr;
-  grid_correction(p.n, corr);
+  grid_correction(p.n, p.g, corr);
   std::vector<float> inv(p.n);
   for (int i = 0; i < p.n; ++i) inv[i] = static_cast<float>(1.0 / corr[i]);
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.tab, kt.table32.data(), kTabLen * sizeof(float),
@@ -404,7 +416,7 @@ int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_a
                                 cudaMemcpyHostToDevice, st));
   // host->device copies from pageable memory are staged before cudaMemcpyAsync
   // returns, so the temporaries above may go out of scope
-  k_twiddle_img<<<(p.n + 255) / 256, 256, 0, st>>>(w.tw, p.n);
+  k_twiddle_img<<<(p.g + 255) / 256, 256, 0, st>>>(w.tw, p.g);
   OVRO_LAUNCH_CHECK();
   k_mask<<<(p.n * p.n + 255) / 256, 256, 0, st>>>(p.n, cell, w.mask);
   OVRO_LAUNCH_CHECK();
@@ -413,7 +425,7 @@ int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_a
     k_baselines<<<g, 128, 0, st>>>(w.ant, n_ant, w.base);
     OVRO_LAUNCH_CHECK();
   }
-  k_chan_scale<<<(n_chan + 255) / 256, 256, 0, st>>>(w.freq, n_chan, p.n, cell, w.cs);
+  k_chan_scale<<<(n_chan + 255) / 256, 256, 0, st>>>(w.freq, n_chan, p.g, cell, w.cs);
   OVRO_LAUNCH_CHECK();
   return OVRO_OK;
 }
@@ -461,7 +473,7 @@ int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
   if (int e = upload_common(p, w, n_ant, h_ant_enu_m, h_chan_freq_hz, n_chan, cell_dircos, st)) return e;
   OVRO_CUDA_TRY(cudaMemsetAsync(w.kept, 0, n_chan * sizeof(int), st));
   const long long n_bl = static_cast<long long>(n_ant) * (n_ant + 1) / 2;
-  const size_t grid_smem = static_cast<size_t>(p.band_h) * p.n * sizeof(float2) + kTabLen * sizeof(float);
+  const size_t grid_smem = static_cast<size_t>(p.band_h) * p.g * sizeof(float2) + kTabLen * sizeof(float);
   OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(grid_smem)));
   for (int ch0 = 0; ch0 < n_chan; ch0 += p.batch) {
@@ -469,13 +481,13 @@ int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
     OVRO_CUDA_TRY(cudaMemsetAsync(w.list_cnt, 0, static_cast<size_t>(p.batch) * p.n_bands * sizeof(int), st));
     if (p.n_cross > 0) {
       dim3 gb(static_cast<unsigned>((p.n_cross + 255) / 256), nb);
-      k_bin<<<gb, 256, 0, st>>>(w.base, static_cast<int>(p.n_cross), w.cs, ch0, p.n, p.band_h,
+      k_bin<<<gb, 256, 0, st>>>(w.base, static_cast<int>(p.n_cross), w.cs, ch0, p.g, p.band_h,
                                 p.n_bands, p.cap, w.lists, w.list_cnt, w.kept);
       OVRO_LAUNCH_CHECK();
     }
     dim3 gg(p.n_bands, nb);
     k_grid<<<gg, 512, grid_smem, st>>>(w.lists, w.list_cnt, p.n_bands, p.cap, d_vis, n_bl, w.base,
-                                       w.tab, ch0, p.n, p.band_h, w.grids);
+                                       w.tab, ch0, p.g, p.band_h, w.grids);
     OVRO_LAUNCH_CHECK();
     if (int e = run_ffts(p, w, ch0, nb, d_img, st)) return e;
   }

@@ -142,8 +142,8 @@ const KernelTables& kernel_tables() {
   return t;
 }
 
-void grid_correction(int n, std::vector<double>& out) {
-  // C^(d) = (1/Q) sum_m C(m / Q) cos(2 pi m d / (Q N)), d = -N/2 .. N/2 - 1
+void grid_correction(int n, int g, std::vector<double>& out) {
+  // C^(d) = (1/Q) sum_m C(m / Q) cos(2 pi m d / (Q G)), d = -N/2 .. N/2 - 1
   const KernelTables& t = kernel_tables();
   const int half = kSupport * kOversample / 2;
   out.assign(n, 0.0);
@@ -151,7 +151,7 @@ void grid_correction(int n, std::vector<double>& out) {
     const double d = i - n / 2;
     double acc = 0.0;
     for (int m = -half; m <= half; ++m)
-      acc += t.table64[m + half] * std::cos(2.0 * M_PI * m * d / (static_cast<double>(kOversample) * n));
+      acc += t.table64[m + half] * std::cos(2.0 * M_PI * m * d / (static_cast<double>(kOversample) * g));
     out[i] = acc / kOversample;
   }
 }

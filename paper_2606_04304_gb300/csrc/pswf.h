@@ -15,7 +15,8 @@ struct KernelTables {
 
 // psi_0(7 pi / 2, x / 3.5) normalised to 1 at x = 0, tabulated (computed once).
 const KernelTables& kernel_tables();
-// Grid correction C^(d), d = -N/2 .. N/2 - 1: Fourier transform of the table.
-void grid_correction(int n, std::vector<double>& out);
+// Grid correction C^(d), d = -N/2 .. N/2 - 1 of an image whose uv grid has G
+// cells a side: Fourier transform of the table at frequency d / G.
+void grid_correction(int n, int g, std::vector<double>& out);
 
 }  // namespace ovro

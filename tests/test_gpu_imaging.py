@@ -24,7 +24,7 @@ def test_uvw_bit_exact(lib, name, n):
     pos = synth.antenna_positions(cfg)
     freqs = synth.fine_freqs_hz(cfg.nfft)[::7]
     pu, pv = lib.uvw(pos, freqs, n, 2.0 / n)
-    ru, rv = _oracle_p(pos, freqs, n, 2.0 / n)
+    ru, rv = _oracle_p(pos, freqs, OI.PAD * n, 2.0 / n)
     assert np.array_equal(pu.cpu().numpy(), ru) and np.array_equal(pv.cpu().numpy(), rv)
 
 
