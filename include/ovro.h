@@ -92,6 +92,25 @@ int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time
                 int8_t* d_fine_q, float* d_fine_f32_or_null,
                 void* d_ws, size_t ws_bytes, void* stream);
 
+/* Allocation-free ovro_upchan (no counterpart in the paper; an interface
+ * convenience).  For callers that cannot allocate device memory at all -- a
+ * plugin whose host framework owns the device heap, or a real-time loop where
+ * an allocation (which may synchronise the device) would stall other streams.
+ * Same arguments and results as ovro_upchan without the workspace: the
+ * scratch is a fixed 1 MiB array inside the library, held on every GPU that
+ * loads it until the process exits.  Limit: ovro_upchan_workspace_size(
+ * n_input, n_coarse) <= 1 MiB (n_input * n_coarse up to about 45,000, e.g.
+ * 704 inputs x 64 coarse channels); larger calls return OVRO_ERR_CAPACITY and
+ * launch nothing.  Allocates nothing (no cudaMalloc/cudaFree).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every
+ * call reuses the same array (what must start at zero is cleared by each
+ * call), so calls that overlap on the GPU -- different streams, or different
+ * host threads, on one device -- race and must be serialised by the caller. */
+int ovro_upchan_noalloc(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time,
+                        const int32_t* h_nfft, const double* h_scale_or_null,
+                        int8_t* d_fine_q, float* d_fine_f32_or_null, void* stream);
+
 /* -------------------------------------------------------------------------
  * a4  X-engine: per fine channel, every antenna pair and polarisation product
  *

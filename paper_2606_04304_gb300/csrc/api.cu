@@ -1,5 +1,6 @@
 // Status codes, error reporting and version of the C ABI.
 #include <atomic>
+#include <cstdarg>
 #include <cstring>
 
 #include "common.cuh"
@@ -12,6 +13,13 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(const char* where, cudaError_t e) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+}
+
+void snprintf_last_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
 }
 }  // namespace ovro
 

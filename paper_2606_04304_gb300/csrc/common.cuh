@@ -14,6 +14,8 @@ namespace ovro {
 void set_last_error(const char* where, cudaError_t e);
 // Counts kernel launches made by the library (ovro_launch_count()).
 void count_launch();
+// printf-style message for ovro_last_error().
+void snprintf_last_error(const char* fmt, ...);
 
 #define OVRO_CUDA_TRY(expr)                                   \
   do {                                                        \

@@ -10,6 +10,7 @@
 // with row-contiguous stores, so the output for fine channel k' is one
 // 2G-byte run in [k'][spectrum][input] order -- the layout the X-engine reads.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -526,6 +527,67 @@ int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time
     q_off += static_cast<long long>(n) * k * n_input * 2;
   }
   return OVRO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of ovro_upchan.
+//
+// Some callers cannot call cudaMalloc at all: a plugin hosted by a framework
+// that owns the whole device heap, or a real-time acquisition loop where an
+// allocation (which may synchronise the device) would stall the other streams.
+// They get ovro_upchan_noalloc, whose scratch (the per-input power sums and
+// scales, and the twiddle table) lives in the fixed array below.  Every GPU
+// that loads this library holds the array until the process exits.
+namespace ovro {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 1u << 20;   // 1 MiB
+static __device__ __align__(256) unsigned char g_upchan_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_ptr[kMaxDevices];
+std::once_flag g_scratch_once[kMaxDevices];
+cudaError_t g_scratch_err[kMaxDevices];
+
+// Device address of the scratch array for the current device, looked up once
+// per device (host code must not use the symbol itself as a device address).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  OVRO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return OVRO_ERR_UNSUPPORTED;
+  std::call_once(g_scratch_once[dev], [dev] {
+    g_scratch_err[dev] = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_upchan_scratch);
+  });
+  if (g_scratch_err[dev] != cudaSuccess) {
+    set_last_error("cudaGetSymbolAddress(g_upchan_scratch)", g_scratch_err[dev]);
+    return OVRO_ERR_CUDA;
+  }
+  *out = g_scratch_ptr[dev];
+  return OVRO_OK;
+}
+
+}  // namespace
+}  // namespace ovro
+
+extern "C" {
+
+int ovro_upchan_noalloc(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time,
+                        const int32_t* h_nfft, const double* h_scale_or_null, int8_t* d_fine_q,
+                        float* d_fine_f32_or_null, void* stream) {
+  using namespace ovro;
+  if (n_input <= 0 || n_coarse <= 0) return OVRO_ERR_INVALID_ARG;
+  const size_t need = ovro_upchan_workspace_size(n_input, n_coarse);
+  if (need > kNoAllocScratchBytes) {
+    snprintf_last_error("ovro_upchan_noalloc: n_input * n_coarse needs %zu bytes of scratch, "
+                        "more than the fixed %zu", need, kNoAllocScratchBytes);
+    return OVRO_ERR_CAPACITY;
+  }
+  void* scratch = nullptr;
+  if (int e = noalloc_scratch(&scratch)) return e;
+  return ovro_upchan(d_volt, n_input, n_coarse, n_time, h_nfft, h_scale_or_null, d_fine_q,
+                     d_fine_f32_or_null, scratch, kNoAllocScratchBytes, stream);
 }
 
 }  // extern "C"
