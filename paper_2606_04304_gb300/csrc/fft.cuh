@@ -141,3 +141,68 @@ __device__ float2* fft_rows_pingpong(float2* a, float2* b, int count, int ld,
 }
 
 }  // namespace ovro
+
+namespace ovro {
+
+// Shared-memory index with one pad slot per 16 elements: Stockham writes at
+// stride 16 become conflict-free.
+__device__ __forceinline__ int pad16(int x) { return x + (x >> 4); }
+
+template <int R>
+__device__ __forceinline__ void inplace_pass(float2* a, int ldp, int G, int Ns,
+                                             const float2* __restrict__ tw) {
+  // every thread holds exactly 16 values: 16 / R butterflies of radix R
+  constexpr int NB = 16 / R;
+  const int per = G / R;
+  const int T = blockDim.x;
+  float2 v[16];
+  int fj[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int gb = threadIdx.x + b * T;
+    const int f = gb / per, j = gb - f * per;
+    fj[b] = gb;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b * R + r] = a[f * ldp + pad16(j + r * per)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int f = fj[b] / per, j = fj[b] - f * per;
+    const int k = j & (Ns - 1);
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[b * R + r];
+    if (Ns > 1) {
+      const int base = k * (G / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw[r * base]);
+    }
+    dft_reg<R>(x);
+    const int o = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[f * ldp + pad16(o + r * Ns)] = x[r];
+  }
+  __syncthreads();
+}
+
+// In-place forward FFTs of the rows of `a` (row f at a[f * ldp], element x at
+// pad16(x)), G = 2^LOG2G >= 32, with blockDim.x * 16 == rows * G.
+// tw: omega_G^k, k < G (shared memory).
+template <int LOG2G>
+__device__ void fft_rows_inplace(float2* a, int ldp, const float2* tw) {
+  constexpr int G = 1 << LOG2G;
+  constexpr int n16 = LOG2G / 4;
+  constexpr int rem = LOG2G % 4;
+  int Ns = 1;
+#pragma unroll
+  for (int p = 0; p < n16; ++p) {
+    inplace_pass<16>(a, ldp, G, Ns, tw);
+    Ns *= 16;
+  }
+  if (rem == 1) inplace_pass<2>(a, ldp, G, Ns, tw);
+  if (rem == 2) inplace_pass<4>(a, ldp, G, Ns, tw);
+  if (rem == 3) inplace_pass<8>(a, ldp, G, Ns, tw);
+}
+
+}  // namespace ovro

@@ -5,26 +5,32 @@
 //
 //  a5  u = (x_a - x_b) s_nu in grid cells with s_nu = nu / (c du): one
 //      correctly rounded FP64 multiply per coordinate, then rounded to 1/Q
-//      cell.  GB300's FP64 pipe is narrow, so k_bin evaluates the product as a
+//      cell.  GB300's FP64 pipe is narrow, so the kernels evaluate it as a
 //      float-float product and only falls back to a real FP64 multiply when
 //      the float-float bound cannot decide rint(u Q) (|frac - 1/2| within the
 //      error bound) -- the integer result equals the FP64 definition exactly.
 //  a6  Stokes I = (XX + YY)/2 of each kept cross baseline is gridded once (the
 //      mirror conj(V) at (-u, -v) is accounted for by taking 2 Re of the
 //      transform, which is exact because the mirror's footprint is the point
-//      reflection), with a separable 7 x 7 prolate-spheroidal kernel.  k_bin
-//      sorts visibilities into row bands of the grid; k_grid accumulates one
-//      band per CTA in shared memory with shared-memory atomics.
+//      reflection), with a separable 7 x 7 prolate-spheroidal kernel.  The uv
+//      position of a baseline moves by a fraction of a cell across a call's
+//      channels, so the host lists, once per call, the baselines that can
+//      touch each band of grid rows; k_grid_rows then works on one
+//      (channel, band): exact uv, keep test, shared-memory atomics into the
+//      band, and the band's row FFTs in place.
 //  a7  The uv grid is padded by 2 (G = 2N cells a side, du = 1 / (G cell)) and
 //      the image is the central N x N of its transform, as padded imagers do:
 //      the horizon then sits where the kernel's transform is still > 0.25, so
-//      the grid correction does not amplify FP32 round-off.  The grid is
-//      transformed by row FFTs (k_fft_rows) and column FFTs of the N central
-//      columns (k_fft_cols); the centring shifts become a (-1)^(ku+kv) sign at
-//      gridding time and (-1)^(r+c) at output, the exp(+) transform becomes a
-//      forward transform of the conjugated grid, and the column pass applies
-//      normalisation, the grid correction and the horizon mask while writing
-//      the image.  Channel batches keep the intermediate grids L2-sized.
+//      the grid correction does not amplify FP32 round-off.  k_grid_rows keeps
+//      only the N central columns of its row transforms; k_fft_cols
+//      transforms those columns, keeps the N central rows, and applies the
+//      (-1)^(r+c) centring sign, normalisation, grid correction and horizon
+//      mask while writing the image.  The (-1)^(ku+kv) centring sign is
+//      applied at gridding time, and the exp(+) transform is a forward
+//      transform of the conjugated grid.  Channel batches keep the
+//      intermediate half-transformed grids L2-sized.
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
@@ -85,21 +91,28 @@ __global__ void k_chan_scale(const double* __restrict__ freq, int n_chan, int n,
   out[f] = c;
 }
 
-// rint(fl64(x * s)) for the FP64 product, decided in FP32 whenever possible.
-__device__ __forceinline__ long long exact_rint_prod(double x, float xh, float xl, const ChanScale& s) {
+// rint(fl64(x * s)) decided in FP32: a float-float product, exact unless the
+// fractional part is within the error bound (1.2e-7) of 1/2 or |x s| >= 2^21;
+// returns false in those (rare) cases, where the FP64 product must be taken.
+__device__ __forceinline__ bool fast_rint_prod(float xh, float xl, const ChanScale& s, long long* p) {
   const float hi = __fmul_rn(xh, s.sh);
-  if (!(fabsf(hi) < 2097152.0f))                       // |P| >= 2^21: take the FP64 path
-    return __double2ll_rn(__dmul_rn(x, s.s));
+  if (!(fabsf(hi) < 2097152.0f)) return false;
   const float e = __fmaf_rn(xh, s.sh, -hi);           // exact error of hi
   const float t = __fmaf_rn(xh, s.sl, __fmaf_rn(xl, s.sh, e));
   const float n = rintf(hi);
-  const float f = __fadd_rn(hi - n, t);              // P - n, |error| < 1.2e-7
-  const float margin = 2.5e-7f;
-  long long p = static_cast<long long>(n);
-  if (fabsf(fabsf(f) - 0.5f) <= margin) return __double2ll_rn(__dmul_rn(x, s.s));
-  if (f > 0.5f) p += 1;
-  else if (f < -0.5f) p -= 1;
-  return p;
+  const float f = __fadd_rn(hi - n, t);              // x s - n, |error| < 1.2e-7
+  if (fabsf(fabsf(f) - 0.5f) <= 2.5e-7f) return false;
+  long long q = static_cast<long long>(n);
+  if (f > 0.5f) ++q;
+  else if (f < -0.5f) --q;
+  *p = q;
+  return true;
+}
+
+__device__ __forceinline__ long long exact_rint_prod(double x, float xh, float xl, const ChanScale& s) {
+  long long p;
+  if (fast_rint_prod(xh, xl, s, &p)) return p;
+  return __double2ll_rn(__dmul_rn(x, s.s));
 }
 
 __device__ __forceinline__ void centre_cell(long long p, int& c0, int& off) {
@@ -126,150 +139,135 @@ __global__ void k_uvw(const Baseline* __restrict__ base, int n_cross, const Chan
   pv[o] = static_cast<int32_t>(v > lim ? lim : (v < -lim ? -lim : v));
 }
 
-// Keep test + band binning of every (channel, cross baseline) in the batch.
-__global__ void k_bin(const Baseline* __restrict__ base, int n_cross, const ChanScale* __restrict__ cs,
-                      int ch0, int n, int band_h, int n_bands, long long cap,
-                      int4* __restrict__ lists, int* __restrict__ list_cnt, int* __restrict__ kept) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int cb = blockIdx.y;
-  bool keep = false;
-  int c0u = 0, offu = 0, c0v = 0, offv = 0;
-  long long pu = 0, pv = 0;
-  if (i < n_cross) {
-    const Baseline B = base[i];
-    const ChanScale s = cs[ch0 + cb];
-    pu = exact_rint_prod(B.dx, B.dxh, B.dxl, s);
-    pv = exact_rint_prod(B.dy, B.dyh, B.dyl, s);
-    const long long lim = static_cast<long long>(n / 2 - kHalfSup - 1) * kQ + kQ;  // loose pre-check
-    if (pu > -lim && pu < lim && pv > -lim && pv < lim) {
-      centre_cell(pu, c0u, offu);
-      centre_cell(pv, c0v, offv);
-      const int cmax = n / 2 - kHalfSup - 1;
-      keep = (c0u <= cmax && c0u >= -cmax && c0v <= cmax && c0v >= -cmax);
-    }
-  }
-  const unsigned m = __ballot_sync(0xffffffffu, keep);
-  if ((threadIdx.x & 31) == 0 && m) atomicAdd(kept + ch0 + cb, __popc(m));
-  if (!keep) return;
-  const int kv_lo = n / 2 + c0v - kHalfSup;
-  const int b0 = kv_lo / band_h, b1 = (kv_lo + kSupport - 1) / band_h;
-  for (int b = b0; b <= b1; ++b) {
-    const int slot = cb * n_bands + b;
-    const int pos = atomicAdd(list_cnt + slot, 1);
-    lists[static_cast<long long>(slot) * cap + pos] =
-        make_int4(i, static_cast<int>(pu), static_cast<int>(pv), 0);
-  }
-}
+struct GridEntry {
+  int bl;            // baseline index in the visibility record
+  int cross;         // cross-baseline index (for the FP64 fallback)
+  int pad0, pad1;
+  float dxh, dxl, dyh, dyl;
+};
 
-// One row band of one channel's grid, accumulated in shared memory.
+// One band of grid rows of one channel: grid in shared memory, row FFTs in
+// place, central N columns written to h ([batch][G][N]).
+template <int LOG2G>
 __global__ void __launch_bounds__(512)
-k_grid(const int4* __restrict__ lists, const int* __restrict__ list_cnt, int n_bands, long long cap,
-       const int32_t* __restrict__ vis, long long n_bl, const Baseline* __restrict__ base,
-       const float* __restrict__ tab, int ch0, int n, int band_h, float2* __restrict__ grids) {
+k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_off,
+            const int32_t* __restrict__ vis, long long n_bl, const Baseline* __restrict__ base,
+            const ChanScale* __restrict__ cs, const float* __restrict__ tab,
+            const float2* __restrict__ tw_g, int ch0, int n_img, int band_h,
+            int* __restrict__ kept, float2* __restrict__ h) {
+  constexpr int G = 1 << LOG2G;
+  constexpr int LDP = G + G / 16 + 1;
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* band = reinterpret_cast<float2*>(smem);
-  float* stab = reinterpret_cast<float*>(smem + static_cast<size_t>(band_h) * n * sizeof(float2));
+  float2* band = reinterpret_cast<float2*>(smem);                     // [band_h][LDP]
+  float2* tw = band + band_h * LDP;                                   // [G]
+  float* stab = reinterpret_cast<float*>(tw + G);                     // [kTabLen]
+  __shared__ int n_home;
   const int b = blockIdx.x, cb = blockIdx.y;
-  const int ncell = band_h * n;
-  for (int i = threadIdx.x; i < ncell; i += blockDim.x) band[i] = make_float2(0.f, 0.f);
-  for (int i = threadIdx.x; i < kTabLen; i += blockDim.x) stab[i] = tab[i];
-  __syncthreads();
-  const int slot = cb * n_bands + b;
-  const int cnt = list_cnt[slot];
-  const int4* L = lists + static_cast<long long>(slot) * cap;
-  const int row0 = b * band_h;
   const long long chan = ch0 + cb;
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const int4 en = L[e];
-    const long long bl = base[en.x].bl;
-    const int4* v = reinterpret_cast<const int4*>(vis + (chan * n_bl + bl) * 8);
+  for (int i = threadIdx.x; i < band_h * LDP; i += blockDim.x) band[i] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < kTabLen; i += blockDim.x) stab[i] = tab[i];
+  for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
+  if (threadIdx.x == 0) n_home = 0;
+  __syncthreads();
+  const ChanScale s = cs[chan];
+  const int row0 = b * band_h;
+  const int cmax = G / 2 - kHalfSup - 1;
+  int my_home = 0;
+  const int e0 = band_off[b], e1 = band_off[b + 1];
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const GridEntry en = entries[e];
+    long long pu = 0, pv = 0;
+    const bool fast = fast_rint_prod(en.dxh, en.dxl, s, &pu) & fast_rint_prod(en.dyh, en.dyl, s, &pv);
+    if (!fast) {                                       // FP64 product of the definition
+      const Baseline B = base[en.cross];
+      pu = __double2ll_rn(__dmul_rn(B.dx, s.s));
+      pv = __double2ll_rn(__dmul_rn(B.dy, s.s));
+    }
+    const long long lim = static_cast<long long>(cmax + 1) * kQ;
+    if (pu <= -lim || pu >= lim || pv <= -lim || pv >= lim) continue;
+    int c0u, offu, c0v, offv;
+    centre_cell(pu, c0u, offu);
+    centre_cell(pv, c0v, offv);
+    if (c0u > cmax || c0u < -cmax || c0v > cmax || c0v < -cmax) continue;
+    const int kv_home = G / 2 + c0v;
+    if (kv_home >= row0 && kv_home < row0 + band_h) ++my_home;
+    const int kv_lo = kv_home - kHalfSup;
+    if (kv_lo + kSupport <= row0 || kv_lo >= row0 + band_h) continue;
+    const int4* v = reinterpret_cast<const int4*>(vis + (chan * n_bl + en.bl) * 8);
     const int4 xx_xy = __ldg(v);
     const int4 yx_yy = __ldg(v + 1);
     // conj of Stokes I: the exp(+) image transform is done as a forward FFT of conj(G)
     const float vr = 0.5f * static_cast<float>(xx_xy.x + yx_yy.z);
     const float vi = -0.5f * static_cast<float>(xx_xy.y + yx_yy.w);
-    int c0u, offu, c0v, offv;
-    centre_cell(en.y, c0u, offu);
-    centre_cell(en.z, c0v, offv);
     float wu[kSupport];
+    const int ku0 = G / 2 + c0u - kHalfSup;
 #pragma unroll
     for (int t = 0; t < kSupport; ++t) {
-      const int ku = n / 2 + c0u + t - kHalfSup;
       const float w = stab[kHalfTab + (t - kHalfSup) * kQ - offu];
-      wu[t] = (ku & 1) ? -w : w;
+      wu[t] = ((ku0 + t) & 1) ? -w : w;
     }
-    const int ku0 = n / 2 + c0u - kHalfSup;
 #pragma unroll
     for (int tv = 0; tv < kSupport; ++tv) {
-      const int kv = n / 2 + c0v + tv - kHalfSup;
-      const int row = kv - row0;
+      const int row = kv_lo + tv - row0;
       if (row < 0 || row >= band_h) continue;
       float wv = stab[kHalfTab + (tv - kHalfSup) * kQ - offv];
-      if (kv & 1) wv = -wv;
-      float2* dst = band + row * n + ku0;
+      if ((kv_lo + tv) & 1) wv = -wv;
+      float2* dst = band + row * LDP;
 #pragma unroll
       for (int tu = 0; tu < kSupport; ++tu) {
         const float w = wv * wu[tu];
-        atomicAdd(&dst[tu].x, w * vr);
-        atomicAdd(&dst[tu].y, w * vi);
+        float2* cell = dst + pad16(ku0 + tu);
+        atomicAdd(&cell->x, w * vr);
+        atomicAdd(&cell->y, w * vi);
       }
     }
   }
+  if (my_home) atomicAdd(&n_home, my_home);
   __syncthreads();
-  float4* g = reinterpret_cast<float4*>(grids + (static_cast<long long>(cb) * n + row0) * n);
-  const float4* s4 = reinterpret_cast<const float4*>(band);
-  for (int i = threadIdx.x; i < ncell / 2; i += blockDim.x) g[i] = s4[i];
+  if (threadIdx.x == 0 && n_home) atomicAdd(kept + chan, n_home);
+  fft_rows_inplace<LOG2G>(band, LDP, tw);
+  // central N columns of each transformed row
+  const int off = G / 2 - n_img / 2;
+  float2* hb = h + (static_cast<long long>(cb) * G + row0) * n_img;
+  for (int i = threadIdx.x; i < band_h * n_img; i += blockDim.x) {
+    const int r = i / n_img, c = i - r * n_img;
+    hb[static_cast<long long>(r) * n_img + c] = band[r * LDP + pad16(off + c)];
+  }
 }
 
-template <int LOG2N>
-__global__ void __launch_bounds__(512)
-k_fft_rows(float2* __restrict__ grids, int rows_per_cta, const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOG2N;
-  extern __shared__ __align__(16) unsigned char smem[];
-  float2* A = reinterpret_cast<float2*>(smem);
-  float2* B = A + rows_per_cta * N;
-  const int cb = blockIdx.y;
-  float2* g = grids + (static_cast<long long>(cb) * N + blockIdx.x * rows_per_cta) * N;
-  const int n4 = rows_per_cta * N / 2;
-  for (int i = threadIdx.x; i < n4; i += blockDim.x)
-    reinterpret_cast<float4*>(A)[i] = reinterpret_cast<const float4*>(g)[i];
-  __syncthreads();
-  const float2* res = fft_rows_pingpong<LOG2N>(A, B, rows_per_cta, N, tw, 1);
-  for (int i = threadIdx.x; i < n4; i += blockDim.x)
-    reinterpret_cast<float4*>(g)[i] = reinterpret_cast<const float4*>(res)[i];
-}
-
+// Column transforms of the N central columns and the image itself.
 template <int LOG2G>
 __global__ void __launch_bounds__(512)
-k_fft_cols(const float2* __restrict__ grids, int n_img, int cols_per_cta, int ch0,
-           const float2* __restrict__ tw, const float* __restrict__ inv_corr,
+k_fft_cols(const float2* __restrict__ h, int n_img, int cols_per_cta, int ch0,
+           const float2* __restrict__ tw_g, const float* __restrict__ inv_corr,
            const uint8_t* __restrict__ mask, const int* __restrict__ kept, float* __restrict__ img) {
   constexpr int G = 1 << LOG2G;
-  constexpr int LD = G + 1;
+  constexpr int LDP = G + G / 16 + 1;
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* A = reinterpret_cast<float2*>(smem);
-  float2* B = A + cols_per_cta * LD;
+  float2* A = reinterpret_cast<float2*>(smem);        // [C][LDP]
+  float2* tw = A + cols_per_cta * LDP;
   const int C = cols_per_cta;
   const int cb = blockIdx.y;
-  const int off = G / 2 - n_img / 2;                  // first central grid row/column
-  const int c0 = blockIdx.x * C;                      // image column of this strip
-  const float2* g = grids + static_cast<long long>(cb) * G * G;
+  const int c0 = blockIdx.x * C;
+  const float2* hc = h + static_cast<long long>(cb) * G * n_img;
+  for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
   for (int i = threadIdx.x; i < G * C; i += blockDim.x) {
     const int r = i / C, c = i - r * C;
-    A[c * LD + r] = g[static_cast<long long>(r) * G + off + c0 + c];
+    A[c * LDP + pad16(r)] = hc[static_cast<long long>(r) * n_img + c0 + c];
   }
   __syncthreads();
-  const float2* res = fft_rows_pingpong<LOG2G>(A, B, C, LD, tw, 1);
+  fft_rows_inplace<LOG2G>(A, LDP, tw);
   const long long chan = ch0 + cb;
   const int k = kept[chan];
   const float norm = k > 0 ? 1.0f / static_cast<float>(k) : 0.0f;
+  const int off = G / 2 - n_img / 2;
   float* out = img + chan * n_img * n_img;
   for (int i = threadIdx.x; i < n_img * C; i += blockDim.x) {
     const int r = i / C, c = i - r * C;
     const int col = c0 + c;
     float v = 0.0f;
     if (mask[r * n_img + col]) {
-      v = res[c * LD + off + r].x * norm * inv_corr[r] * inv_corr[col];
+      v = A[c * LDP + pad16(off + r)].x * norm * inv_corr[r] * inv_corr[col];
       if ((r + col) & 1) v = -v;
     }
     out[static_cast<long long>(r) * n_img + col] = v;
@@ -300,8 +298,8 @@ __global__ void k_counts_out(const int* __restrict__ kept, int n_chan, int32_t* 
 
 // ---------------------------------------------------------------- planning
 struct ImgPlan {
-  int n, g, log2g, band_h, n_bands, batch, rows_per_cta, cols_per_cta;
-  long long n_cross, cap;
+  int n, g, log2g, band_h, n_bands, batch, cols_per_cta;
+  long long n_cross;
 };
 
 ImgPlan make_plan(int n_ant, int n_chan, int n) {
@@ -309,23 +307,17 @@ ImgPlan make_plan(int n_ant, int n_chan, int n) {
   p.n = n;
   p.g = kPad * n;
   p.log2g = ilog2(p.g);
-  p.band_h = 16384 / p.g < p.g ? 16384 / p.g : p.g;   // band of <= 128 KB FP32 complex
+  p.band_h = 8192 / p.g < p.g ? 8192 / p.g : p.g;    // 8192 complex values per band
   p.n_bands = p.g / p.band_h;
   p.n_cross = static_cast<long long>(n_ant) * (n_ant - 1) / 2;
-  p.cap = p.n_cross > 0 ? p.n_cross : 1;
-  const long long grid_bytes = 8LL * p.g * p.g;
-  const long long list_bytes = 16LL * p.n_bands * p.cap;
-  long long b = (64LL << 20) / grid_bytes;
-  const long long bl = (512LL << 20) / list_bytes;
-  if (bl < b) b = bl;
+  const long long h_bytes = 8LL * p.g * n;           // half-transformed grid of one channel
+  long long b = (64LL << 20) / h_bytes;
   if (b < 1) b = 1;
   if (b > 64) b = 64;
   if (b > n_chan) b = n_chan;
   p.batch = static_cast<int>(b);
-  p.rows_per_cta = 8192 / p.g < p.g ? 8192 / p.g : p.g;
   int c = 8192 / p.g;
   if (c > n) c = n;
-  if (c > 32) c = 32;
   p.cols_per_cta = c;
   return p;
 }
@@ -340,10 +332,17 @@ struct ImgWs {
   Baseline* base;
   ChanScale* cs;
   int* kept;
-  int* list_cnt;
-  int4* lists;
-  float2* grids;
+  int* band_off;
+  GridEntry* entries;
+  float2* h;
 };
+
+// Candidate entries: each cross baseline once per band it can touch (at most
+// 2 for 7-row footprints in >= 4-row bands... bounded by n_bands in general).
+long long entry_capacity(const ImgPlan& p) {
+  const long long per = std::min<long long>(p.n_bands, kSupport + 2);
+  return std::max<long long>(1, p.n_cross * per);
+}
 
 ImgWs carve_img(void* ws, size_t bytes, const ImgPlan& p, int n_ant, int n_chan, size_t* need) {
   Carver c(ws, bytes);
@@ -357,45 +356,96 @@ ImgWs carve_img(void* ws, size_t bytes, const ImgPlan& p, int n_ant, int n_chan,
   w.base = c.take<Baseline>(p.n_cross > 0 ? p.n_cross : 1);
   w.cs = c.take<ChanScale>(n_chan);
   w.kept = c.take<int>(n_chan);
-  w.list_cnt = c.take<int>(static_cast<size_t>(p.batch) * p.n_bands);
-  w.lists = c.take<int4>(static_cast<size_t>(p.batch) * p.n_bands * p.cap);
-  w.grids = c.take<float2>(static_cast<size_t>(p.batch) * p.g * p.g);
+  w.band_off = c.take<int>(p.n_bands + 1);
+  w.entries = c.take<GridEntry>(entry_capacity(p));
+  w.h = c.take<float2>(static_cast<size_t>(p.batch) * p.g * p.n);
   *need = c.used;
   return w;
 }
 
+// Host: which baselines can touch which band of grid rows for any channel of
+// the call (u, v scale linearly with frequency; one cell of margin).
+void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double* freq, int n_chan,
+                   double cell, std::vector<GridEntry>& out, std::vector<int>& off) {
+  const double du = 1.0 / (static_cast<double>(p.g) * cell);
+  double fmin = freq[0], fmax = freq[0];
+  for (int f = 1; f < n_chan; ++f) {
+    fmin = std::min(fmin, freq[f]);
+    fmax = std::max(fmax, freq[f]);
+  }
+  const double s_lo = fmin / (kCLight * du), s_hi = fmax / (kCLight * du);   // cells per metre
+  const int cmax = p.g / 2 - kHalfSup - 1;
+  std::vector<std::vector<GridEntry>> bands(p.n_bands);
+  long long cross = 0;
+  for (int a = 0; a < n_ant; ++a)
+    for (int b = a + 1; b < n_ant; ++b, ++cross) {
+      const double dx = ant[3 * a] - ant[3 * b], dy = ant[3 * a + 1] - ant[3 * b + 1];
+      const double u0 = std::min(dx * s_lo, dx * s_hi), u1 = std::max(dx * s_lo, dx * s_hi);
+      const double v0 = std::min(dy * s_lo, dy * s_hi), v1 = std::max(dy * s_lo, dy * s_hi);
+      // can the centre cell ever satisfy |c0| <= cmax?
+      if (u0 > cmax + 1.5 || u1 < -cmax - 1.5 || v0 > cmax + 1.5 || v1 < -cmax - 1.5) continue;
+      int r_lo = p.g / 2 + static_cast<int>(std::floor(v0)) - 1 - kHalfSup;
+      int r_hi = p.g / 2 + static_cast<int>(std::ceil(v1)) + 1 + kHalfSup;
+      r_lo = std::max(r_lo, 0);
+      r_hi = std::min(r_hi, p.g - 1);
+      GridEntry e;
+      e.bl = static_cast<int>(a * static_cast<long long>(n_ant) - static_cast<long long>(a) * (a - 1) / 2 + (b - a));
+      e.cross = static_cast<int>(cross);
+      e.pad0 = e.pad1 = 0;
+      e.dxh = static_cast<float>(dx);
+      e.dxl = static_cast<float>(dx - static_cast<double>(e.dxh));
+      e.dyh = static_cast<float>(dy);
+      e.dyl = static_cast<float>(dy - static_cast<double>(e.dyh));
+      for (int bd = r_lo / p.band_h; bd <= r_hi / p.band_h; ++bd) bands[bd].push_back(e);
+    }
+  out.clear();
+  off.assign(p.n_bands + 1, 0);
+  for (int bd = 0; bd < p.n_bands; ++bd) {
+    off[bd] = static_cast<int>(out.size());
+    out.insert(out.end(), bands[bd].begin(), bands[bd].end());
+  }
+  off[p.n_bands] = static_cast<int>(out.size());
+}
+
 template <int L>
-int launch_ffts(const ImgPlan& p, const ImgWs& w, int ch0, int nb, float* img, cudaStream_t st) {
+int launch_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long n_bl, int ch0, int nb,
+                 float* img, cudaStream_t st) {
   constexpr int G = 1 << L;
+  constexpr int LDP = G + G / 16 + 1;
   {
-    const size_t sm = 2ull * p.rows_per_cta * G * sizeof(float2);
-    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t sm = static_cast<size_t>(p.band_h) * LDP * sizeof(float2) + G * sizeof(float2) +
+                      kTabLen * sizeof(float);
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid_rows<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm)));
-    dim3 grid(G / p.rows_per_cta, nb);
-    k_fft_rows<L><<<grid, 512, sm, st>>>(w.grids, p.rows_per_cta, w.tw);
+    const int threads = p.band_h * G / 16;
+    dim3 grid(p.n_bands, nb);
+    k_grid_rows<L><<<grid, threads, sm, st>>>(w.entries, w.band_off, vis, n_bl, w.base, w.cs, w.tab, w.tw, ch0,
+                                              p.n, p.band_h, w.kept, w.h);
     OVRO_LAUNCH_CHECK();
   }
   {
-    const size_t sm = 2ull * p.cols_per_cta * (G + 1) * sizeof(float2);
+    const size_t sm = static_cast<size_t>(p.cols_per_cta) * LDP * sizeof(float2) + G * sizeof(float2);
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm)));
+    const int threads = p.cols_per_cta * G / 16;
     dim3 grid(p.n / p.cols_per_cta, nb);
-    k_fft_cols<L><<<grid, 512, sm, st>>>(w.grids, p.n, p.cols_per_cta, ch0, w.tw, w.inv_corr, w.mask,
-                                         w.kept, img);
+    k_fft_cols<L><<<grid, threads, sm, st>>>(w.h, p.n, p.cols_per_cta, ch0, w.tw, w.inv_corr, w.mask, w.kept,
+                                             img);
     OVRO_LAUNCH_CHECK();
   }
   return OVRO_OK;
 }
 
-int run_ffts(const ImgPlan& p, const ImgWs& w, int ch0, int nb, float* img, cudaStream_t st) {
+int run_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long n_bl, int ch0, int nb, float* img,
+              cudaStream_t st) {
   switch (p.log2g) {
-    case 5: return launch_ffts<5>(p, w, ch0, nb, img, st);
-    case 6: return launch_ffts<6>(p, w, ch0, nb, img, st);
-    case 7: return launch_ffts<7>(p, w, ch0, nb, img, st);
-    case 8: return launch_ffts<8>(p, w, ch0, nb, img, st);
-    case 9: return launch_ffts<9>(p, w, ch0, nb, img, st);
-    case 10: return launch_ffts<10>(p, w, ch0, nb, img, st);
-    case 11: return launch_ffts<11>(p, w, ch0, nb, img, st);
+    case 5: return launch_bands<5>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 6: return launch_bands<6>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 7: return launch_bands<7>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 8: return launch_bands<8>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 9: return launch_bands<9>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 10: return launch_bands<10>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 11: return launch_bands<11>(p, w, vis, n_bl, ch0, nb, img, st);
     default: return OVRO_ERR_UNSUPPORTED;
   }
 }
@@ -407,6 +457,10 @@ int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_a
   grid_correction(p.n, p.g, corr);
   std::vector<float> inv(p.n);
   for (int i = 0; i < p.n; ++i) inv[i] = static_cast<float>(1.0 / corr[i]);
+  std::vector<GridEntry> entries;
+  std::vector<int> off;
+  build_entries(p, n_ant, h_ant, h_freq, n_chan, cell, entries, off);
+  if (static_cast<long long>(entries.size()) > entry_capacity(p)) return OVRO_ERR_CAPACITY;
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.tab, kt.table32.data(), kTabLen * sizeof(float),
                                 cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.inv_corr, inv.data(), p.n * sizeof(float), cudaMemcpyHostToDevice, st));
@@ -414,6 +468,10 @@ int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_a
                                 cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.freq, h_freq, static_cast<size_t>(n_chan) * sizeof(double),
                                 cudaMemcpyHostToDevice, st));
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.band_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!entries.empty())
+    OVRO_CUDA_TRY(cudaMemcpyAsync(w.entries, entries.data(), entries.size() * sizeof(GridEntry),
+                                  cudaMemcpyHostToDevice, st));
   // host->device copies from pageable memory are staged before cudaMemcpyAsync
   // returns, so the temporaries above may go out of scope
   k_twiddle_img<<<(p.g + 255) / 256, 256, 0, st>>>(w.tw, p.g);
@@ -473,23 +531,9 @@ int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
   if (int e = upload_common(p, w, n_ant, h_ant_enu_m, h_chan_freq_hz, n_chan, cell_dircos, st)) return e;
   OVRO_CUDA_TRY(cudaMemsetAsync(w.kept, 0, n_chan * sizeof(int), st));
   const long long n_bl = static_cast<long long>(n_ant) * (n_ant + 1) / 2;
-  const size_t grid_smem = static_cast<size_t>(p.band_h) * p.g * sizeof(float2) + kTabLen * sizeof(float);
-  OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(grid_smem)));
   for (int ch0 = 0; ch0 < n_chan; ch0 += p.batch) {
     const int nb = n_chan - ch0 < p.batch ? n_chan - ch0 : p.batch;
-    OVRO_CUDA_TRY(cudaMemsetAsync(w.list_cnt, 0, static_cast<size_t>(p.batch) * p.n_bands * sizeof(int), st));
-    if (p.n_cross > 0) {
-      dim3 gb(static_cast<unsigned>((p.n_cross + 255) / 256), nb);
-      k_bin<<<gb, 256, 0, st>>>(w.base, static_cast<int>(p.n_cross), w.cs, ch0, p.g, p.band_h,
-                                p.n_bands, p.cap, w.lists, w.list_cnt, w.kept);
-      OVRO_LAUNCH_CHECK();
-    }
-    dim3 gg(p.n_bands, nb);
-    k_grid<<<gg, 512, grid_smem, st>>>(w.lists, w.list_cnt, p.n_bands, p.cap, d_vis, n_bl, w.base,
-                                       w.tab, ch0, p.g, p.band_h, w.grids);
-    OVRO_LAUNCH_CHECK();
-    if (int e = run_ffts(p, w, ch0, nb, d_img, st)) return e;
+    if (int e = run_bands(p, w, d_vis, n_bl, ch0, nb, d_img, st)) return e;
   }
   if (d_n_gridded_or_null) {
     k_counts_out<<<(n_chan + 255) / 256, 256, 0, st>>>(w.kept, n_chan, d_n_gridded_or_null);
