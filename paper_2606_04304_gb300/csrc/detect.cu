@@ -270,10 +270,14 @@ __global__ void k_ztrans(const float* __restrict__ img, const int* __restrict__ 
 }
 
 // --------------------------------------------------------------- a9 sort
+// words per pixel of the running-median step stream
+__host__ __device__ __forceinline__ int walk_stride(int nc, int h) {
+  return (nc + ((h + 3) & ~3) + 3) & ~3;
+}
 // Stable LSD radix sort of one pixel spectrum per CTA iteration.
 __global__ void __launch_bounds__(512)
-k_rank(const float* __restrict__ z, int n_valid, int nc, float* __restrict__ sv,
-       uint16_t* __restrict__ rank) {
+k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restrict__ sv,
+       uint32_t* __restrict__ steps) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = blockDim.x >> 5;
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem);           // 256 * W
@@ -323,11 +327,22 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, float* __restrict__ sv,
       uint32_t* t1 = ks; ks = kd; kd = t1;
       uint16_t* t2 = is; is = id; id = t2;
     }
+    // running-median walk stream: step k inserts channel k + h and removes
+    // channel k - h - 1, stored at index k + H (H = h rounded up to 4) as
+    // (insert rank, remove rank), 0xffff = none; indices below H hold the
+    // insert-only steps that build the first window
+    const int H = (h + 3) & ~3;
+    const int S = walk_stride(nc, h);
     float* svp = sv + static_cast<long long>(p) * nc;
-    uint16_t* rp = rank + static_cast<long long>(p) * nc;
+    uint32_t* sp = steps + static_cast<long long>(p) * S;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) sp[k] = 0xffffffffu;
+    __syncthreads();
+    uint16_t* sp16 = reinterpret_cast<uint16_t*>(sp);
     for (int r = threadIdx.x; r < nc; r += blockDim.x) {
       svp[r] = key2f(ks[r]);
-      rp[is[r]] = static_cast<uint16_t>(r);
+      const int j = is[r];
+      sp16[2 * (j - h + H)] = static_cast<uint16_t>(r);
+      if (j + h + 1 < nc) sp16[2 * (j + h + 1 + H) + 1] = static_cast<uint16_t>(r);
     }
     __syncthreads();
   }
@@ -358,9 +373,38 @@ __device__ __forceinline__ int prev_set(const uint32_t* bits, int p) {
   return (w << 5) + 31 - __clz(word);
 }
 
+__device__ __forceinline__ bool walk_step(uint32_t* bits, int nwords, uint32_t word, int& size, int& cur,
+                                          int& lt) {
+  const int rin = static_cast<int>(word & 0xffffu);
+  const int rout = static_cast<int>(word >> 16);
+  if (rin != 0xffff) {
+    bits[(rin >> 5) * kWalkThreads] |= 1u << (rin & 31);
+    ++size;
+    if (cur < 0) { cur = rin; lt = 0; }
+    else if (rin < cur) ++lt;
+  }
+  if (rout != 0xffff) {
+    bits[(rout >> 5) * kWalkThreads] &= ~(1u << (rout & 31));
+    --size;
+    if (rout < cur) {
+      --lt;
+    } else if (rout == cur) {
+      const int nx = next_set(bits, rout, nwords);
+      if (nx >= 0) cur = nx;
+      else { cur = prev_set(bits, rout); --lt; }
+    }
+  }
+  if (size == 0) { cur = -1; lt = 0; return true; }
+  const int target = (size - 1) >> 1;
+  while (lt < target && cur >= 0) { cur = next_set(bits, cur + 1, nwords); ++lt; }
+  while (lt > target && cur >= 0) { cur = prev_set(bits, cur - 1); --lt; }
+  return cur >= 0;
+}
+
 // zbuf holds z on entry and z - running median on exit ([pixel][channel]).
+// steps: the stream written by k_rank (walk_stride words per pixel).
 __global__ void __launch_bounds__(kWalkThreads)
-k_walk(float* __restrict__ zbuf, const float* __restrict__ sv, const uint16_t* __restrict__ rank,
+k_walk(float* __restrict__ zbuf, const float* __restrict__ sv, const uint32_t* __restrict__ steps,
        int n_valid, int nc, int h) {
   extern __shared__ uint32_t bits_all[];
   const int t = threadIdx.x;
@@ -369,78 +413,45 @@ k_walk(float* __restrict__ zbuf, const float* __restrict__ sv, const uint16_t* _
   uint32_t* bits = bits_all + t;                         // word w at bits[w * kWalkThreads]
   for (int w = 0; w < nwords; ++w) bits[w * kWalkThreads] = 0u;
   if (p >= n_valid) return;
+  const int H = (h + 3) & ~3;
   float* zp = zbuf + static_cast<long long>(p) * nc;
   const float* svp = sv + static_cast<long long>(p) * nc;
-  const uint16_t* rp = rank + static_cast<long long>(p) * nc;
-
-  // window for k = 0: [0, min(h, nc - 1)]
-  int size = 0;
-  const int hi0 = min(h, nc - 1);
-  for (int j = 0; j <= hi0; ++j) {
-    const int r = rp[j];
-    bits[(r >> 5) * kWalkThreads] |= 1u << (r & 31);
-    ++size;
-  }
-  // cursor on the lower median: the t-th smallest set bit
-  int target = (size - 1) >> 1;
-  int cur = next_set(bits, 0, nwords);
-  int lt = 0;
-  while (lt < target && cur >= 0) { cur = next_set(bits, cur + 1, nwords); ++lt; }
-  if (cur < 0) {
-    atomicExch(&g_detect_status, 3);
-    return;
-  }
-
-  for (int k = 0; k < nc; ++k) {
-    if (k > 0) {
-      const int jin = k + h, jout = k - h - 1;
-      bool removed_cur = false;
-      int rout = -1;
-      if (jin < nc) {
-        const int r = rp[jin];
-        bits[(r >> 5) * kWalkThreads] |= 1u << (r & 31);
-        ++size;
-        if (r < cur) ++lt;
-      }
-      if (jout >= 0) {
-        rout = rp[jout];
-        bits[(rout >> 5) * kWalkThreads] &= ~(1u << (rout & 31));
-        --size;
-        if (rout < cur) --lt;
-        else if (rout == cur) removed_cur = true;
-      }
-      if (removed_cur) {
-        const int nx = next_set(bits, rout, nwords);
-        if (nx >= 0) {
-          cur = nx;
-        } else {
-          cur = prev_set(bits, rout);
-          --lt;
-        }
-      }
-      target = (size - 1) >> 1;
-      while (lt < target && cur >= 0) { cur = next_set(bits, cur + 1, nwords); ++lt; }
-      while (lt > target && cur >= 0) { cur = prev_set(bits, cur - 1); --lt; }
-      if (cur < 0) {                      // cannot happen for a consistent bitset
-        atomicExch(&g_detect_status, 3);
-        return;
-      }
+  const uint32_t* st = steps + static_cast<long long>(p) * walk_stride(nc, h);
+  int size = 0, cur = -1, lt = 0;
+  for (int i = 0; i < H; ++i)
+    if (!walk_step(bits, nwords, st[i], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
+  const bool vec_ok = (nc & 3) == 0;
+  for (int k0 = 0; k0 < nc; k0 += 4) {
+    const uint4 sw = *reinterpret_cast<const uint4*>(st + H + k0);
+    const uint32_t swa[4] = {sw.x, sw.y, sw.z, sw.w};
+    int lower[4], upper[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      lower[q] = upper[q] = 0;
+      if (k0 + q >= nc) continue;
+      if (!walk_step(bits, nwords, swa[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
+      lower[q] = cur;
+      upper[q] = (size & 1) ? cur : next_set(bits, cur + 1, nwords);
+      if (upper[q] < 0) { atomicExch(&g_detect_status, 3); return; }
     }
-    float med = svp[cur];
-    if ((size & 1) == 0) {
-      const int up = next_set(bits, cur + 1, nwords);
-      if (up < 0) {
-        atomicExch(&g_detect_status, 3);
-        return;
-      }
-      med = 0.5f * (med + svp[up]);
+    float med[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) med[q] = 0.5f * (svp[lower[q]] + svp[upper[q]]);
+    if (vec_ok) {
+      float4 zz = *reinterpret_cast<const float4*>(zp + k0);
+      zz.x -= med[0];
+      zz.y -= med[1];
+      zz.z -= med[2];
+      zz.w -= med[3];
+      *reinterpret_cast<float4*>(zp + k0) = zz;
+    } else {
+      for (int q = 0; q < 4 && k0 + q < nc; ++q) zp[k0 + q] -= med[q];
     }
-    zp[k] = zp[k] - med;
   }
 }
 
 // -------------------------------------------------------- a10 matched filter
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_mf(const float* __restrict__ zbuf, int n_valid, int nc, float* __restrict__ snr,
      uint8_t* __restrict__ width, uint32_t hist_key0, int n_bins, unsigned long long* __restrict__ ghist) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -580,6 +591,7 @@ struct DetectPlan {
   std::vector<long long> vox0; // voxel offset of each coarse block in snr/width
   long long n_vox = 0;
   int max_nc = 0;
+  int max_steps = 0;
   int n_valid = 0;
   bool stats_in_smem = false;
 };
@@ -606,6 +618,7 @@ DetectPlan make_plan(int n_chan, int n, double cell, int n_coarse, const int32_t
     p.half.push_back(window_channels(coarse_bw / nfft[c], span) / 2);
     p.n_vox += static_cast<long long>(p.n_valid) * nfft[c];
     p.max_nc = std::max(p.max_nc, static_cast<int>(nfft[c]));
+    p.max_steps = std::max(p.max_steps, walk_stride(nfft[c], p.half.back()));
     c0 += nfft[c];
   }
   p.stats_in_smem = (static_cast<size_t>(p.n_valid) * 4 + 8192 + 256 + 32 + 16384) <= 231000;
@@ -621,7 +634,7 @@ struct DetectWs {
   float* stats32;
   float* zbuf;
   float* sv;
-  uint16_t* rank;
+  uint32_t* steps;
   float* snr;
   uint8_t* width;
   unsigned long long* hist;
@@ -638,7 +651,7 @@ DetectWs carve_detect(void* ws, size_t bytes, const DetectPlan& p, size_t* need)
   w.stats32 = c.take<float>(2 * static_cast<size_t>(p.n_chan));
   w.zbuf = c.take<float>(blk);
   w.sv = c.take<float>(blk);
-  w.rank = c.take<uint16_t>(blk);
+  w.steps = c.take<uint32_t>(static_cast<size_t>(p.n_valid) * p.max_steps);
   w.snr = c.take<float>(static_cast<size_t>(p.n_vox));
   w.width = c.take<uint8_t>(static_cast<size_t>(p.n_vox));
   w.hist = c.take<unsigned long long>(kMaxBins);
@@ -687,14 +700,14 @@ int run_filter(const float* d_img, const DetectPlan& p, const DetectWs& w, uint3
       const size_t sm = (256 * W + 32) * 4 + static_cast<size_t>(nc) * 12;
       OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
       const int blocks = std::min(p.n_valid, 2 * nsm * 8);
-      k_rank<<<blocks, threads, sm, st>>>(w.zbuf, p.n_valid, nc, w.sv, w.rank);
+      k_rank<<<blocks, threads, sm, st>>>(w.zbuf, p.n_valid, nc, p.half[c], w.sv, w.steps);
       OVRO_LAUNCH_CHECK();
     }
     {
       const size_t sm = static_cast<size_t>((nc + 31) / 32) * kWalkThreads * 4;
       OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
       k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(
-          w.zbuf, w.sv, w.rank, p.n_valid, nc, p.half[c]);
+          w.zbuf, w.sv, w.steps, p.n_valid, nc, p.half[c]);
       OVRO_LAUNCH_CHECK();
     }
     if (d_zp_out) {
@@ -704,8 +717,8 @@ int run_filter(const float* d_img, const DetectPlan& p, const DetectWs& w, uint3
     {
       const size_t sm = static_cast<size_t>(kMaxLo + nc + kMaxHi + kVox) * 4 + static_cast<size_t>(n_bins) * 4;
       OVRO_CUDA_TRY(cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-      const int blocks = std::min(p.n_valid, 4 * nsm * 4);
-      k_mf<<<blocks, 256, sm, st>>>(w.zbuf, p.n_valid, nc, w.snr + p.vox0[c], w.width + p.vox0[c],
+      const int blocks = std::min(p.n_valid, 3 * nsm * 8);
+      k_mf<<<blocks, 128, sm, st>>>(w.zbuf, p.n_valid, nc, w.snr + p.vox0[c], w.width + p.vox0[c],
                                     hist_key0, n_bins, w.hist);
       OVRO_LAUNCH_CHECK();
     }
