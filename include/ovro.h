@@ -55,6 +55,14 @@ const char* ovro_last_error(void);
 int ovro_version(void);
 /* Number of kernels this library has launched in this process. */
 unsigned long long ovro_launch_count(void);
+/* Kernel tracing.  ovro_profile(1) clears the trace and starts recording a
+ * CUDA event pair on the launch stream around every launch of the main
+ * kernels (k_upchan, k_xeng_tc, k_xeng_simt, k_grid_rows, k_fft_cols,
+ * k_stats, k_ztrans, k_rank, k_walk, k_mf); ovro_profile(0) stops recording.
+ * ovro_profile_query waits for the recorded launches of one kernel and
+ * returns their summed device time and count. */
+int ovro_profile(int enable);
+int ovro_profile_query(const char* kernel, double* total_ms, int* launches);
 
 /* -------------------------------------------------------------------------
  * a1-a3  Unpack + FFT upchannelizer + 8-bit requantisation

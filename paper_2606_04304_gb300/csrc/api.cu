@@ -2,6 +2,10 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -13,6 +17,34 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(const char* where, cudaError_t e) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+}
+
+// ---- tracing
+static std::atomic<bool> g_prof_on{false};
+static std::mutex g_prof_mu;
+struct ProfRec {
+  std::vector<cudaEvent_t> begin, end;
+};
+static std::map<std::string, ProfRec> g_prof;
+
+bool profiling() { return g_prof_on.load(std::memory_order_relaxed); }
+
+void prof_mark(const char* name, cudaStream_t st, bool begin) {
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, st);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfRec& r = g_prof[name];
+  (begin ? r.begin : r.end).push_back(e);
+}
+
+static void prof_clear() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& kv : g_prof) {
+    for (cudaEvent_t e : kv.second.begin) cudaEventDestroy(e);
+    for (cudaEvent_t e : kv.second.end) cudaEventDestroy(e);
+  }
+  g_prof.clear();
 }
 
 void snprintf_last_error(const char* fmt, ...) {
@@ -44,5 +76,30 @@ const char* ovro_last_error(void) { return ovro::g_last_error; }
 int ovro_version(void) { return (1 << 16) | 0; }
 
 unsigned long long ovro_launch_count(void) { return ovro::g_launches.load(); }
+
+int ovro_profile(int enable) {
+  if (enable) ovro::prof_clear();
+  ovro::g_prof_on.store(enable != 0);
+  return OVRO_OK;
+}
+
+int ovro_profile_query(const char* kernel, double* total_ms, int* launches) {
+  if (!kernel || !total_ms || !launches) return OVRO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ovro::g_prof_mu);
+  *total_ms = 0.0;
+  *launches = 0;
+  auto it = ovro::g_prof.find(kernel);
+  if (it == ovro::g_prof.end()) return OVRO_OK;
+  const auto& r = it->second;
+  const size_t n = r.begin.size() < r.end.size() ? r.begin.size() : r.end.size();
+  for (size_t i = 0; i < n; ++i) {
+    if (cudaEventSynchronize(r.end[i]) != cudaSuccess) return OVRO_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.begin[i], r.end[i]) != cudaSuccess) return OVRO_ERR_CUDA;
+    *total_ms += ms;
+  }
+  *launches = static_cast<int>(n);
+  return OVRO_OK;
+}
 
 }  // extern "C"

@@ -17,6 +17,24 @@ void count_launch();
 // printf-style message for ovro_last_error().
 void snprintf_last_error(const char* fmt, ...);
 
+// Optional kernel tracing (ovro_profile): when enabled, CUDA events are
+// recorded on the launch stream around each traced kernel.
+bool profiling();
+void prof_mark(const char* name, cudaStream_t st, bool begin);
+
+struct ProfScope {
+  const char* name;
+  cudaStream_t st;
+  bool on;
+  ProfScope(const char* n, cudaStream_t s) : name(n), st(s), on(profiling()) {
+    if (on) prof_mark(name, st, true);
+  }
+  ~ProfScope() {
+    if (on) prof_mark(name, st, false);
+  }
+};
+#define OVRO_PROF(name, st) ::ovro::ProfScope ovro_prof_scope_(name, st)
+
 #define OVRO_CUDA_TRY(expr)                                   \
   do {                                                        \
     cudaError_t e_ = (expr);                                  \

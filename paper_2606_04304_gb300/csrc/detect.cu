@@ -678,6 +678,7 @@ int run_stats(const float* d_img, const DetectPlan& p, const DetectWs& w, cudaSt
   const size_t base = 2048 * 4 + 64 * 4 + 8 * 4 + 2048 * 8;
   const size_t sm = base + (p.stats_in_smem ? static_cast<size_t>(p.n_valid) * 4 : 0);
   OVRO_CUDA_TRY(cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  OVRO_PROF("k_stats", st);
   k_stats<<<p.n_chan, 1024, sm, st>>>(d_img, w.pix, p.n_valid, p.npix, p.stats_in_smem ? 1 : 0,
                                       w.stats64, w.stats32);
   OVRO_LAUNCH_CHECK();
@@ -692,6 +693,7 @@ int run_filter(const float* d_img, const DetectPlan& p, const DetectWs& w, uint3
     const int nc = p.nfft[c];
     {
       dim3 g((p.n_valid + 31) / 32, (nc + 31) / 32);
+      OVRO_PROF("k_ztrans", st);
       k_ztrans<<<g, 256, 0, st>>>(d_img, w.pix, p.n_valid, p.npix, p.chan0[c], nc, w.stats32, w.zbuf);
       OVRO_LAUNCH_CHECK();
     }
@@ -700,12 +702,14 @@ int run_filter(const float* d_img, const DetectPlan& p, const DetectWs& w, uint3
       const size_t sm = (256 * W + 32) * 4 + static_cast<size_t>(nc) * 12;
       OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
       const int blocks = std::min(p.n_valid, 2 * nsm * 8);
+      OVRO_PROF("k_rank", st);
       k_rank<<<blocks, threads, sm, st>>>(w.zbuf, p.n_valid, nc, p.half[c], w.sv, w.steps);
       OVRO_LAUNCH_CHECK();
     }
     {
       const size_t sm = static_cast<size_t>((nc + 31) / 32) * kWalkThreads * 4;
       OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+      OVRO_PROF("k_walk", st);
       k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(
           w.zbuf, w.sv, w.steps, p.n_valid, nc, p.half[c]);
       OVRO_LAUNCH_CHECK();
@@ -718,6 +722,7 @@ int run_filter(const float* d_img, const DetectPlan& p, const DetectWs& w, uint3
       const size_t sm = static_cast<size_t>(kMaxLo + nc + kMaxHi + kVox) * 4 + static_cast<size_t>(n_bins) * 4;
       OVRO_CUDA_TRY(cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
       const int blocks = std::min(p.n_valid, 3 * nsm * 8);
+      OVRO_PROF("k_mf", st);
       k_mf<<<blocks, 128, sm, st>>>(w.zbuf, p.n_valid, nc, w.snr + p.vox0[c], w.width + p.vox0[c],
                                     hist_key0, n_bins, w.hist);
       OVRO_LAUNCH_CHECK();

@@ -146,8 +146,19 @@ struct GridEntry {
   float dxh, dxl, dyh, dyl;
 };
 
+// Row pitch of a shared-memory grid band: G + G/16 pad slots, rounded so the
+// pitch is 7 (mod 16) float2 -- consecutive rows then start 14 banks apart and
+// the 7 rows of one kernel footprint, or 16 consecutive transposed columns, hit
+// distinct banks.
+__host__ __device__ constexpr int band_pitch(int g) { return (g + g / 16) + ((7 - (g + g / 16) % 16) + 16) % 16; }
+
+constexpr int kRecMax = 512;       // visibilities prepared per chunk
+
 // One band of grid rows of one channel: grid in shared memory, row FFTs in
-// place, central N columns written to h ([batch][G][N]).
+// place, central N columns written to h ([batch][G][N]).  The band's candidate
+// list is taken in chunks: each thread prepares one visibility (exact uv, keep
+// test, the seven u-weights times V), then the CTA sweeps (visibility, row)
+// items, seven taps each, with shared-memory atomics.
 template <int LOG2G>
 __global__ void __launch_bounds__(512)
 k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_off,
@@ -156,71 +167,103 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
             const float2* __restrict__ tw_g, int ch0, int n_img, int band_h,
             int* __restrict__ kept, float2* __restrict__ h) {
   constexpr int G = 1 << LOG2G;
-  constexpr int LDP = G + G / 16 + 1;
+  constexpr int LDP = band_pitch(G);
   extern __shared__ __align__(16) unsigned char smem[];
   float2* band = reinterpret_cast<float2*>(smem);                     // [band_h][LDP]
   float2* tw = band + band_h * LDP;                                   // [G]
-  float* stab = reinterpret_cast<float*>(tw + G);                     // [kTabLen]
-  __shared__ int n_home;
+  float2* r_wuv = tw + G;                                             // [kRecMax][7]
+  int* r_ku0 = reinterpret_cast<int*>(r_wuv + kRecMax * kSupport);    // [kRecMax]
+  int* r_kv0 = r_ku0 + kRecMax;                                       // first row, band-relative
+  int* r_offv = r_kv0 + kRecMax;
+  __shared__ int n_home, n_rec;
   const int b = blockIdx.x, cb = blockIdx.y;
   const long long chan = ch0 + cb;
   for (int i = threadIdx.x; i < band_h * LDP; i += blockDim.x) band[i] = make_float2(0.f, 0.f);
-  for (int i = threadIdx.x; i < kTabLen; i += blockDim.x) stab[i] = tab[i];
   for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
   if (threadIdx.x == 0) n_home = 0;
-  __syncthreads();
   const ChanScale s = cs[chan];
   const int row0 = b * band_h;
   const int cmax = G / 2 - kHalfSup - 1;
+  const int lane = threadIdx.x & 31;
   int my_home = 0;
   const int e0 = band_off[b], e1 = band_off[b + 1];
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const GridEntry en = entries[e];
-    long long pu = 0, pv = 0;
-    const bool fast = fast_rint_prod(en.dxh, en.dxl, s, &pu) & fast_rint_prod(en.dyh, en.dyl, s, &pv);
-    if (!fast) {                                       // FP64 product of the definition
-      const Baseline B = base[en.cross];
-      pu = __double2ll_rn(__dmul_rn(B.dx, s.s));
-      pv = __double2ll_rn(__dmul_rn(B.dy, s.s));
-    }
-    const long long lim = static_cast<long long>(cmax + 1) * kQ;
-    if (pu <= -lim || pu >= lim || pv <= -lim || pv >= lim) continue;
-    int c0u, offu, c0v, offv;
-    centre_cell(pu, c0u, offu);
-    centre_cell(pv, c0v, offv);
-    if (c0u > cmax || c0u < -cmax || c0v > cmax || c0v < -cmax) continue;
-    const int kv_home = G / 2 + c0v;
-    if (kv_home >= row0 && kv_home < row0 + band_h) ++my_home;
-    const int kv_lo = kv_home - kHalfSup;
-    if (kv_lo + kSupport <= row0 || kv_lo >= row0 + band_h) continue;
-    const int4* v = reinterpret_cast<const int4*>(vis + (chan * n_bl + en.bl) * 8);
-    const int4 xx_xy = __ldg(v);
-    const int4 yx_yy = __ldg(v + 1);
-    // conj of Stokes I: the exp(+) image transform is done as a forward FFT of conj(G)
-    const float vr = 0.5f * static_cast<float>(xx_xy.x + yx_yy.z);
-    const float vi = -0.5f * static_cast<float>(xx_xy.y + yx_yy.w);
-    float wu[kSupport];
-    const int ku0 = G / 2 + c0u - kHalfSup;
-#pragma unroll
-    for (int t = 0; t < kSupport; ++t) {
-      const float w = stab[kHalfTab + (t - kHalfSup) * kQ - offu];
-      wu[t] = ((ku0 + t) & 1) ? -w : w;
-    }
-#pragma unroll
-    for (int tv = 0; tv < kSupport; ++tv) {
-      const int row = kv_lo + tv - row0;
-      if (row < 0 || row >= band_h) continue;
-      float wv = stab[kHalfTab + (tv - kHalfSup) * kQ - offv];
-      if ((kv_lo + tv) & 1) wv = -wv;
-      float2* dst = band + row * LDP;
-#pragma unroll
-      for (int tu = 0; tu < kSupport; ++tu) {
-        const float w = wv * wu[tu];
-        float2* cell = dst + pad16(ku0 + tu);
-        atomicAdd(&cell->x, w * vr);
-        atomicAdd(&cell->y, w * vi);
+  for (int c0 = e0; c0 < e1; c0 += blockDim.x) {
+    if (threadIdx.x == 0) n_rec = 0;
+    __syncthreads();
+    // ---- prepare: one candidate per thread
+    const int e = c0 + threadIdx.x;
+    bool use = false;
+    int ku0 = 0, kv_rel = 0, offv = 0, offu = 0;
+    float vr = 0.f, vi = 0.f;
+    if (e < e1) {
+      const GridEntry en = entries[e];
+      long long pu = 0, pv = 0;
+      const bool fast = fast_rint_prod(en.dxh, en.dxl, s, &pu) & fast_rint_prod(en.dyh, en.dyl, s, &pv);
+      if (!fast) {                                     // FP64 product of the definition
+        const Baseline B = base[en.cross];
+        pu = __double2ll_rn(__dmul_rn(B.dx, s.s));
+        pv = __double2ll_rn(__dmul_rn(B.dy, s.s));
+      }
+      const long long lim = static_cast<long long>(cmax + 1) * kQ;
+      if (pu > -lim && pu < lim && pv > -lim && pv < lim) {
+        int c0u, c0v;
+        centre_cell(pu, c0u, offu);
+        centre_cell(pv, c0v, offv);
+        if (c0u <= cmax && c0u >= -cmax && c0v <= cmax && c0v >= -cmax) {
+          const int kv_home = G / 2 + c0v;
+          if (kv_home >= row0 && kv_home < row0 + band_h) ++my_home;
+          kv_rel = kv_home - kHalfSup - row0;
+          ku0 = G / 2 + c0u - kHalfSup;
+          if (kv_rel + kSupport > 0 && kv_rel < band_h) {
+            use = true;
+            const int4* v = reinterpret_cast<const int4*>(vis + (chan * n_bl + en.bl) * 8);
+            const int4 xx_xy = __ldg(v);
+            const int4 yx_yy = __ldg(v + 1);
+            // conj of Stokes I: the exp(+) transform is a forward FFT of conj(G)
+            vr = 0.5f * static_cast<float>(xx_xy.x + yx_yy.z);
+            vi = -0.5f * static_cast<float>(xx_xy.y + yx_yy.w);
+          }
+        }
       }
     }
+    const unsigned m = __ballot_sync(0xffffffffu, use);
+    int base_slot = 0;
+    if (lane == 0 && m) base_slot = atomicAdd(&n_rec, __popc(m));
+    base_slot = __shfl_sync(0xffffffffu, base_slot, 0);
+    if (use) {
+      const int slot = base_slot + __popc(m & ((1u << lane) - 1u));
+      r_ku0[slot] = ku0;
+      r_kv0[slot] = kv_rel;
+      r_offv[slot] = offv;
+#pragma unroll
+      for (int t = 0; t < kSupport; ++t) {
+        float w = __ldg(tab + kHalfTab + (t - kHalfSup) * kQ - offu);
+        if ((ku0 + t) & 1) w = -w;                                   // (-1)^ku centring sign
+        r_wuv[slot * kSupport + t] = make_float2(w * vr, w * vi);
+      }
+    }
+    __syncthreads();
+    // ---- sweep (visibility, row) items: seven taps each
+    const int nr = n_rec;
+    for (int it = threadIdx.x; it < nr * kSupport; it += blockDim.x) {
+      const int rec = it / kSupport, tv = it - rec * kSupport;
+      const int row = r_kv0[rec] + tv;
+      if (row < 0 || row >= band_h) continue;
+      const int kv = row0 + row;
+      float wv = __ldg(tab + kHalfTab + (tv - kHalfSup) * kQ - r_offv[rec]);
+      if (kv & 1) wv = -wv;                                          // (-1)^kv centring sign
+      const int k0 = r_ku0[rec];
+      float2* dst = band + row * LDP;
+      const float2* wuv = r_wuv + rec * kSupport;
+#pragma unroll
+      for (int tu = 0; tu < kSupport; ++tu) {
+        const float2 a = wuv[tu];
+        float2* cell = dst + pad16(k0 + tu);
+        atomicAdd(&cell->x, wv * a.x);
+        atomicAdd(&cell->y, wv * a.y);
+      }
+    }
+    __syncthreads();
   }
   if (my_home) atomicAdd(&n_home, my_home);
   __syncthreads();
@@ -242,7 +285,7 @@ k_fft_cols(const float2* __restrict__ h, int n_img, int cols_per_cta, int ch0,
            const float2* __restrict__ tw_g, const float* __restrict__ inv_corr,
            const uint8_t* __restrict__ mask, const int* __restrict__ kept, float* __restrict__ img) {
   constexpr int G = 1 << LOG2G;
-  constexpr int LDP = G + G / 16 + 1;
+  constexpr int LDP = band_pitch(G);
   extern __shared__ __align__(16) unsigned char smem[];
   float2* A = reinterpret_cast<float2*>(smem);        // [C][LDP]
   float2* tw = A + cols_per_cta * LDP;
@@ -411,14 +454,15 @@ template <int L>
 int launch_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long n_bl, int ch0, int nb,
                  float* img, cudaStream_t st) {
   constexpr int G = 1 << L;
-  constexpr int LDP = G + G / 16 + 1;
+  constexpr int LDP = band_pitch(G);
   {
     const size_t sm = static_cast<size_t>(p.band_h) * LDP * sizeof(float2) + G * sizeof(float2) +
-                      kTabLen * sizeof(float);
+                      kRecMax * (kSupport * sizeof(float2) + 3 * sizeof(int));
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid_rows<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm)));
     const int threads = p.band_h * G / 16;
     dim3 grid(p.n_bands, nb);
+    OVRO_PROF("k_grid_rows", st);
     k_grid_rows<L><<<grid, threads, sm, st>>>(w.entries, w.band_off, vis, n_bl, w.base, w.cs, w.tab, w.tw, ch0,
                                               p.n, p.band_h, w.kept, w.h);
     OVRO_LAUNCH_CHECK();
@@ -429,6 +473,7 @@ int launch_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long
                                        static_cast<int>(sm)));
     const int threads = p.cols_per_cta * G / 16;
     dim3 grid(p.n / p.cols_per_cta, nb);
+    OVRO_PROF("k_fft_cols", st);
     k_fft_cols<L><<<grid, threads, sm, st>>>(w.h, p.n, p.cols_per_cta, ch0, w.tw, w.inv_corr, w.mask, w.kept,
                                              img);
     OVRO_LAUNCH_CHECK();

@@ -403,6 +403,7 @@ int launch_upchan_t(const UpchanArgs& a, cudaStream_t st) {
   OVRO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(sm)));
   dim3 grid((a.n_input + a.group - 1) / a.group, a.n_spec);
+  OVRO_PROF("k_upchan", st);
   kern<<<grid, P::THREADS, sm, st>>>(a);
   OVRO_LAUNCH_CHECK();
   return OVRO_OK;

@@ -320,6 +320,7 @@ int ovro_correlate(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec, in
   if (mode == OVRO_XENG_FP32) {
     const int n_tiles = (n_input + kSimtTile - 1) / kSimtTile;
     dim3 grid(n_tiles * (n_tiles + 1) / 2, n_chan);
+    OVRO_PROF("k_xeng_simt", st);
     k_xeng_simt<<<grid, 256, 0, st>>>(d_fine_q, n_ant, n_spec, n_tiles, d_vis);
     OVRO_LAUNCH_CHECK();
     return OVRO_OK;
@@ -335,6 +336,7 @@ int ovro_correlate(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec, in
   OVRO_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   long long grid = 2LL * num_sms();
   if (grid > n_items) grid = n_items;
+  OVRO_PROF("k_xeng_tc", st);
   k_xeng_tc<<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(d_fine_q, n_ant, n_spec, n_tiles,
                                                                   n_pairs, n_items, d_vis);
   OVRO_LAUNCH_CHECK();

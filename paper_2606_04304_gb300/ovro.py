@@ -58,6 +58,8 @@ def _load() -> ctypes.CDLL:
         "ovro_last_error": (ctypes.c_char_p, []),
         "ovro_version": (I, []),
         "ovro_launch_count": (ctypes.c_ulonglong, []),
+        "ovro_profile": (I, [I]),
+        "ovro_profile_query": (I, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
         "ovro_upchan_workspace_size": (S, [I, I]),
         "ovro_upchan": (I, [P, I, I, L, P, P, P, P, P, S, P]),
         "ovro_correlate": (I, [P, I, I, I, I, P, P]),
@@ -87,6 +89,23 @@ def lib() -> ctypes.CDLL:
 
 def launch_count() -> int:
     return int(_lib.ovro_launch_count())
+
+
+def profile(enable: bool) -> None:
+    """Start (clearing the trace) or stop per-kernel CUDA-event tracing."""
+    _check("ovro_profile", _lib.ovro_profile(1 if enable else 0))
+
+
+def profile_query(kernel: str):
+    """(summed device ms, launches) of one traced kernel."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int(0)
+    _check("ovro_profile_query", _lib.ovro_profile_query(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+TRACED_KERNELS = ("k_upchan", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
+                  "k_rank", "k_walk", "k_mf")
 
 
 def _check(fn: str, status: int) -> int:
