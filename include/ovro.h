@@ -258,6 +258,43 @@ int ovro_detect_filter(const float* d_img, const double* d_stats, int n_chan, in
                        const ovro_detect_params* params, float* d_zp_or_null, float* d_snr,
                        int32_t* d_width, void* d_ws, size_t ws_bytes, void* stream);
 
+/* -------------------------------------------------------------------------
+ * a13  Learned candidate scorer (no counterpart in the paper, which keeps or
+ * drops Stage I triggers by threshold alone; the plain detector stays the
+ * fallback and the judge of recall and false alarms).
+ *
+ * Network: 1600 -> 128 -> 32 -> 1, GELU (erf form) hidden units, logit out.
+ * Parameters: one flat vector of ovro_scorer_n_params() values, layer by
+ * layer, W row-major [out][in] then b.  Served as BF16 (d_w_bf16, uint16 bit
+ * patterns); every product is accumulated in FP32.  Training keeps FP32
+ * master weights and Adam moments (b1 = 0.9, b2 = 0.999, eps = 1e-8).
+ * Input: cutouts of the high-passed standardised cube (ovro_detect_filter's
+ * d_zp) -- 64 channels x 5 x 5 pixels centred on a trigger, channel-major,
+ * zero outside the trigger's coarse channel or the image.
+ * ------------------------------------------------------------------------- */
+int ovro_scorer_n_params(void);
+/* Workspace for batch cutouts/activations (and n_coarse channel offsets). */
+size_t ovro_scorer_workspace_size(int batch, int n_coarse);
+/* d_zp float [n_chan][N][N]; d_trig int32 [n_trig][3] = (channel, row, col);
+ * d_x float [n_trig][1600]. */
+int ovro_scorer_cutouts(const float* d_zp, int n_chan, int image_size, int n_coarse,
+                        const int32_t* h_nfft, const int32_t* d_trig, int n_trig, float* d_x,
+                        void* d_ws, size_t ws_bytes, void* stream);
+/* d_logit float [batch]. */
+int ovro_scorer_forward(const void* d_w_bf16, const float* d_x, int batch, float* d_logit,
+                        void* d_ws, size_t ws_bytes, void* stream);
+/* Gradient of the mean binary cross-entropy (labels d_y in {0, 1}) with
+ * respect to all parameters, evaluated at d_w (BF16 if w_is_bf16, else FP32);
+ * d_grad float [n_params]; d_loss_or_null float [1]. */
+int ovro_scorer_grad(const void* d_w, int w_is_bf16, const float* d_x, const float* d_y, int batch,
+                     float* d_grad, float* d_loss_or_null, void* d_ws, size_t ws_bytes, void* stream);
+/* One Adam step (step >= 1) on the FP32 master weights; refreshes the BF16
+ * copy when d_w_bf16_or_null is given. */
+int ovro_scorer_adam(float* d_master, float* d_m, float* d_v, const float* d_grad, int step, float lr,
+                     void* d_w_bf16_or_null, void* stream);
+/* BF16 copy (round to nearest even) of the FP32 master weights. */
+int ovro_scorer_to_bf16(const float* d_master, void* d_w_bf16, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,13 @@ def _load() -> ctypes.CDLL:
         "ovro_detect": (I, [P, I, I, D, I, P, P, P, P, I, P, P, S, P]),
         "ovro_detect_stats": (I, [P, I, I, D, P, P, S, P]),
         "ovro_detect_filter": (I, [P, P, I, I, D, I, P, P, P, P, P, P, S, P]),
+        "ovro_scorer_n_params": (I, []),
+        "ovro_scorer_workspace_size": (S, [I, I]),
+        "ovro_scorer_cutouts": (I, [P, I, I, I, P, P, I, P, P, S, P]),
+        "ovro_scorer_forward": (I, [P, P, I, P, P, S, P]),
+        "ovro_scorer_grad": (I, [P, I, P, P, I, P, P, P, S, P]),
+        "ovro_scorer_adam": (I, [P, P, P, P, I, ctypes.c_float, P, P]),
+        "ovro_scorer_to_bf16": (I, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -285,3 +292,62 @@ def detect_filter(img: torch.Tensor, stats: torch.Tensor, cell: float, nfft: Seq
         _ptr(img), _ptr(stats), n_chan, n, float(cell), len(nf), nf.ctypes.data_as(ctypes.c_void_p),
         ctypes.byref(prm), _ptr(zp), _ptr(snr), _ptr(wid), _ptr(ws), ws.numel(), _stream(stream)))
     return zp, snr, wid
+
+
+# ------------------------------------------------------------------------ a13
+def scorer_n_params() -> int:
+    return int(_lib.ovro_scorer_n_params())
+
+
+def scorer_cutouts(zp: torch.Tensor, nfft: Sequence[int], trig: torch.Tensor, stream=None) -> torch.Tensor:
+    """zp float [n_chan][N][N]; trig int32 [n][3] (channel, row, col) -> [n][1600]."""
+    _cuda(zp, torch.float32, "zp")
+    _cuda(trig, torch.int32, "trig")
+    n_chan, n, _ = zp.shape
+    nf = _host(nfft, np.int32)
+    x = torch.empty((trig.shape[0], 1600), dtype=torch.float32, device=zp.device)
+    ws = workspace(_lib.ovro_scorer_workspace_size(1, len(nf)), zp.device)
+    _check("ovro_scorer_cutouts", _lib.ovro_scorer_cutouts(
+        _ptr(zp), n_chan, n, len(nf), nf.ctypes.data_as(ctypes.c_void_p), _ptr(trig), trig.shape[0], _ptr(x),
+        _ptr(ws), ws.numel(), _stream(stream)))
+    return x
+
+
+def scorer_forward(w_bf16: torch.Tensor, x: torch.Tensor, ws: Optional[torch.Tensor] = None, stream=None):
+    _cuda(w_bf16, torch.bfloat16, "w_bf16")
+    _cuda(x, torch.float32, "x")
+    B = x.shape[0]
+    logit = torch.empty(B, dtype=torch.float32, device=x.device)
+    need = _lib.ovro_scorer_workspace_size(B, 1)
+    ws = ws if ws is not None and ws.numel() >= need else workspace(need, x.device)
+    _check("ovro_scorer_forward", _lib.ovro_scorer_forward(_ptr(w_bf16), _ptr(x), B, _ptr(logit), _ptr(ws),
+                                                           ws.numel(), _stream(stream)))
+    return logit
+
+
+def scorer_grad(w: torch.Tensor, x: torch.Tensor, y: torch.Tensor, ws: Optional[torch.Tensor] = None,
+                stream=None):
+    """Returns (grad float [n_params], loss float [1]); w is BF16 or FP32."""
+    _cuda(x, torch.float32, "x")
+    _cuda(y, torch.float32, "y")
+    if not (w.is_cuda and w.is_contiguous() and w.dtype in (torch.bfloat16, torch.float32)):
+        raise ValueError("w must be a contiguous CUDA bf16 or float32 tensor")
+    B = x.shape[0]
+    g = torch.empty(scorer_n_params(), dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    need = _lib.ovro_scorer_workspace_size(B, 1)
+    ws = ws if ws is not None and ws.numel() >= need else workspace(need, x.device)
+    _check("ovro_scorer_grad", _lib.ovro_scorer_grad(_ptr(w), 1 if w.dtype == torch.bfloat16 else 0, _ptr(x),
+                                                     _ptr(y), B, _ptr(g), _ptr(loss), _ptr(ws), ws.numel(),
+                                                     _stream(stream)))
+    return g, loss
+
+
+def scorer_adam(master: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, step: int,
+                lr: float, w_bf16: Optional[torch.Tensor] = None, stream=None):
+    _check("ovro_scorer_adam", _lib.ovro_scorer_adam(_ptr(master), _ptr(m), _ptr(v), _ptr(grad), step,
+                                                     float(lr), _ptr(w_bf16), _stream(stream)))
+
+
+def scorer_to_bf16(master: torch.Tensor, w_bf16: torch.Tensor, stream=None):
+    _check("ovro_scorer_to_bf16", _lib.ovro_scorer_to_bf16(_ptr(master), _ptr(w_bf16), _stream(stream)))

@@ -8,6 +8,7 @@ path can be fed the same bytes without sharing any of the computation.
 """
 from .workloads import (  # noqa: F401
     C_LIGHT,
+    Burst,
     Config,
     CONFIGS,
     Tone,

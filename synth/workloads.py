@@ -71,6 +71,18 @@ class Tone:
 
 
 @dataclass
+class Burst:
+    """Broadband radio-frequency interference: a point source of complex white
+    noise (all fine channels) switched on for a fraction of a second."""
+    coarse: int
+    t0_s: float
+    dur_s: float
+    row: int
+    col: int
+    amp: float           # rms amplitude per component, 4-bit levels
+
+
+@dataclass
 class Config:
     name: str
     n_ant: int
@@ -84,6 +96,8 @@ class Config:
     outer_radius_m: float = 1500.0
     cell_dircos: float = 0.0          # 0 -> all-sky default 2 / image_size
     tones: List[Tone] = field(default_factory=list)
+    carriers: List[Tone] = field(default_factory=list)   # stationary CW tones at the horizon (RFI)
+    bursts: List[Burst] = field(default_factory=list)
 
     @property
     def n_input(self) -> int:
@@ -104,6 +118,8 @@ class Config:
     def describe(self) -> dict:
         d = dataclasses.asdict(self)
         d["tones"] = len(self.tones)
+        d["carriers"] = len(self.carriers)
+        d["bursts"] = len(self.bursts)
         return d
 
 
@@ -179,11 +195,12 @@ def generate(cfg: Config, coarse: Optional[Sequence[int]] = None,
     pos = antenna_positions(cfg)
     out = np.empty((len(coarse), cfg.n_time, cfg.n_input), dtype=np.uint8)
     for ci, c in enumerate(coarse):
-        tones = [t for t in cfg.tones if t.coarse == c]
+        tones = [t for t in cfg.tones + cfg.carriers if t.coarse == c]
+        bursts = [b for b in cfg.bursts if b.coarse == c]
         for t0 in range(0, cfg.n_time, time_block):
             nt = min(time_block, cfg.n_time - t0)
             g = substream(cfg.seed, 2, c, t0 // time_block)
-            if not tones:
+            if not tones and not bursts:
                 re = _noise_levels(g, nt * cfg.n_input)
                 im = _noise_levels(g, nt * cfg.n_input)
                 out[ci, t0:t0 + nt] = pack_nibbles(re, im).reshape(nt, cfg.n_input)
@@ -192,15 +209,33 @@ def generate(cfg: Config, coarse: Optional[Sequence[int]] = None,
             xi = g.standard_normal((nt, cfg.n_input)) * SIGMA_LEVELS
             tt = (t0 + np.arange(nt, dtype=np.float64)) / F_COARSE_HZ
             n = cfg.nfft[c]
+            # every source is rank one in (time, input): a time series times a
+            # per-antenna geometric phasor, so the block is one complex product
+            et, ga = [], []
             for tone in tones:
                 f0 = (tone.fine - n / 2) * (F_COARSE_HZ / n)          # baseband Hz
                 nu = coarse_centre_hz(c) + f0
                 l0, m0 = pixel_dircos(tone.row, tone.col, cfg.image_size, cfg.cell)
                 geo = -2 * np.pi * nu * (pos[:, 0] * l0 + pos[:, 1] * m0) / C_LIGHT
                 ph_t = 2 * np.pi * (f0 * tt + 0.5 * tone.drift_hz_s * tt * tt) + tone.phase
-                ph = ph_t[:, None] + np.repeat(geo, 2)[None, :]
-                xr += tone.amp * np.cos(ph)
-                xi += tone.amp * np.sin(ph)
+                et.append(tone.amp * np.exp(1j * ph_t))
+                ga.append(np.exp(1j * np.repeat(geo, 2)))
+            for bi, burst in enumerate(bursts):
+                on = (tt >= burst.t0_s) & (tt < burst.t0_s + burst.dur_s)
+                if not on.any():
+                    continue
+                gb = substream(cfg.seed, 5, c, bi, t0 // time_block)
+                sig = np.zeros(nt, dtype=np.complex128)
+                k = int(on.sum())
+                sig[on] = (gb.standard_normal(k) + 1j * gb.standard_normal(k)) * burst.amp
+                l0, m0 = pixel_dircos(burst.row, burst.col, cfg.image_size, cfg.cell)
+                geo = -2 * np.pi * coarse_centre_hz(c) * (pos[:, 0] * l0 + pos[:, 1] * m0) / C_LIGHT
+                et.append(sig)
+                ga.append(np.exp(1j * np.repeat(geo, 2)))
+            if et:
+                inj = np.stack(et, axis=1) @ np.stack(ga, axis=0)        # [nt][n_input]
+                xr += inj.real
+                xi += inj.imag
             out[ci, t0:t0 + nt] = pack_nibbles(_quantise(xr), _quantise(xi))
     return out
 
@@ -237,6 +272,33 @@ def _seeded_tones(cfg: Config, n: int, snr_lo: float, snr_hi: float,
     return tones
 
 
+def _add_rfi(cfg: Config, n_carriers: int, n_bursts: int):
+    """Stationary CW carriers just above the horizon and broadband bursts."""
+    g = substream(cfg.seed, 6)
+    N = cfg.image_size
+    n_bl = cfg.n_ant * (cfg.n_ant - 1) // 2
+    while len(cfg.carriers) < n_carriers:
+        row, col = int(g.integers(0, N)), int(g.integers(0, N))
+        l0, m0 = pixel_dircos(row, col, N, cfg.cell)
+        if not (0.95 <= l0 * l0 + m0 * m0 < 1.0):
+            continue
+        c = int(g.integers(0, cfg.n_coarse))
+        nf = cfg.nfft[c]
+        snr = float(g.uniform(8.0, 30.0))
+        cfg.carriers.append(Tone(c, int(g.integers(nf // 8, nf - nf // 8)), row, col,
+                                 tone_amplitude(snr, nf, cfg.n_time // nf, n_bl),
+                                 float(g.uniform(0, 2 * np.pi)), 0.0, snr))
+    T = cfg.n_time / F_COARSE_HZ
+    while len(cfg.bursts) < n_bursts:
+        row, col = int(g.integers(0, N)), int(g.integers(0, N))
+        l0, m0 = pixel_dircos(row, col, N, cfg.cell)
+        if l0 * l0 + m0 * m0 > 0.8:
+            continue
+        dur = float(g.uniform(0.2, 1.0))
+        cfg.bursts.append(Burst(int(g.integers(0, cfg.n_coarse)), float(g.uniform(0, T - dur)), dur, row, col,
+                                float(g.uniform(0.6, 1.5))))
+
+
 SEED_BASE = 20240406
 
 
@@ -251,7 +313,7 @@ def make_config(name: str, **over) -> Config:
     precision 352 antennas, 4 coarse x 4096-pt (K = 58), 1024^2 grids
     scorer    352 antennas, 8 coarse x 8192-pt, 256^2, tones SNR 4-20, drift 0-1 Hz/s
     """
-    idx = {"tiny": 0, "full": 1, "batched": 2, "precision": 3, "scorer": 4}[name]
+    idx = {"tiny": 0, "full": 1, "batched": 2, "precision": 3, "scorer": 4, "scorer_train": 5}[name]
     seed = SEED_BASE + idx
     if name == "tiny":
         cfg = Config(name, 16, 2, [256, 256], 64 * 256, 64, seed)
@@ -263,8 +325,11 @@ def make_config(name: str, **over) -> Config:
         cfg = Config(name, 352, 32, nf, 240_000, 256, seed, core_ant=251)
     elif name == "precision":
         cfg = Config(name, 352, 4, [4096] * 4, 240_000, 1024, seed, core_ant=251)
-    else:
+    elif name == "scorer":
         cfg = Config(name, 352, 8, [8192] * 8, 240_000, 256, seed, core_ant=251)
+    else:
+        # a compact 64-antenna array whose baselines all fit the 128^2 all-sky grid
+        cfg = Config(name, 64, 2, [2048, 2048], 240_000, 128, seed, core_radius_m=70.0)
     n_tones = over.pop("n_tones", None)
     for k, v in over.items():
         setattr(cfg, k, v)
@@ -274,9 +339,13 @@ def make_config(name: str, **over) -> Config:
         cfg.tones = _seeded_tones(cfg, 20 if n_tones is None else n_tones, 5.0, 30.0, 0.5)
     elif name == "scorer":
         cfg.tones = _seeded_tones(cfg, 64 if n_tones is None else n_tones, 4.0, 20.0, 1.0)
+        _add_rfi(cfg, 16, 16)
+    elif name == "scorer_train":
+        cfg.tones = _seeded_tones(cfg, 24 if n_tones is None else n_tones, 4.0, 20.0, 1.0)
+        _add_rfi(cfg, 8, 6)
     elif n_tones:
         cfg.tones = _seeded_tones(cfg, n_tones, 10.0, 30.0, 0.0)
     return cfg
 
 
-CONFIGS = ("tiny", "full", "batched", "precision", "scorer")
+CONFIGS = ("tiny", "full", "batched", "precision", "scorer", "scorer_train")
