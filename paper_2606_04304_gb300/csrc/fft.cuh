@@ -148,9 +148,14 @@ namespace ovro {
 // stride 16 become conflict-free.
 __device__ __forceinline__ int pad16(int x) { return x + (x >> 4); }
 
-template <int R>
+// One Stockham pass in place.  With PLANAR the pass reads its input from two
+// real arrays (re, im: row f, element x at f * pp + x), which may overlap `a`:
+// every read completes before the first write.
+template <int R, bool PLANAR = false>
 __device__ __forceinline__ void inplace_pass(float2* a, int ldp, int G, int Ns,
-                                             const float2* __restrict__ tw) {
+                                             const float2* __restrict__ tw,
+                                             const float* pre = nullptr, const float* pim = nullptr,
+                                             int pp = 0) {
   // every thread holds exactly 16 values: 16 / R butterflies of radix R
   constexpr int NB = 16 / R;
   const int per = G / R;
@@ -163,7 +168,14 @@ __device__ __forceinline__ void inplace_pass(float2* a, int ldp, int G, int Ns,
     const int f = gb / per, j = gb - f * per;
     fj[b] = gb;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b * R + r] = a[f * ldp + pad16(j + r * per)];
+    for (int r = 0; r < R; ++r) {
+      if (PLANAR) {
+        const int x = f * pp + j + r * per;
+        v[b * R + r] = make_float2(pre[x], pim[x]);
+      } else {
+        v[b * R + r] = a[f * ldp + pad16(j + r * per)];
+      }
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -189,14 +201,21 @@ __device__ __forceinline__ void inplace_pass(float2* a, int ldp, int G, int Ns,
 // In-place forward FFTs of the rows of `a` (row f at a[f * ldp], element x at
 // pad16(x)), G = 2^LOG2G >= 32, with blockDim.x * 16 == rows * G.
 // tw: omega_G^k, k < G (shared memory).
+// With `pre` non-null the rows are first read from the planar arrays
+// (pre, pim, row pitch pp floats; see inplace_pass), G >= 16.
 template <int LOG2G>
-__device__ void fft_rows_inplace(float2* a, int ldp, const float2* tw) {
+__device__ void fft_rows_inplace(float2* a, int ldp, const float2* tw, const float* pre = nullptr,
+                                 const float* pim = nullptr, int pp = 0) {
   constexpr int G = 1 << LOG2G;
   constexpr int n16 = LOG2G / 4;
   constexpr int rem = LOG2G % 4;
+  static_assert(n16 >= 1, "G >= 16");
   int Ns = 1;
+  if (pre) inplace_pass<16, true>(a, ldp, G, Ns, tw, pre, pim, pp);
+  else inplace_pass<16>(a, ldp, G, Ns, tw);
+  Ns = 16;
 #pragma unroll
-  for (int p = 0; p < n16; ++p) {
+  for (int p = 1; p < n16; ++p) {
     inplace_pass<16>(a, ldp, G, Ns, tw);
     Ns *= 16;
   }

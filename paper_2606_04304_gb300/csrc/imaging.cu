@@ -152,13 +152,25 @@ struct GridEntry {
 // distinct banks.
 __host__ __device__ constexpr int band_pitch(int g) { return (g + g / 16) + ((7 - (g + g / 16) % 16) + 16) % 16; }
 
-constexpr int kRecMax = 512;       // visibilities prepared per chunk
+// Gridding records per chunk (one per prepared visibility).
+constexpr int kRecMax = 256;
+constexpr int kWuStride = 5;       // float2 per record: (w_t, w_{t+4}), t < 4; odd word stride
+constexpr int kWvStride = 9;       // floats per record: w_t, t < 8 (w_7 = 0)
+
+// Planar row pitch of a band during gridding: G + 4 floats, so that the 7 rows
+// x 4 columns of one footprint quarter fall in 28 distinct banks.
+__host__ __device__ constexpr int planar_pitch(int g) { return g + 4; }
 
 // One band of grid rows of one channel: grid in shared memory, row FFTs in
 // place, central N columns written to h ([batch][G][N]).  The band's candidate
-// list is taken in chunks: each thread prepares one visibility (exact uv, keep
-// test, the seven u-weights times V), then the CTA sweeps (visibility, row)
-// items, seven taps each, with shared-memory atomics.
+// list is taken in chunks of blockDim/2 visibilities; a pair of threads
+// prepares one (exact u on the even thread, exact v on the odd one, the keep
+// test, the seven separable weights of each axis with the centring sign, and
+// Stokes I), then every warp takes whole records: lane (tv, tu) = (lane / 4,
+// lane % 4) adds taps (tv, tu) and (tv, tu + 4) of the 7 x 7 footprint.  The
+// band is held as two real planes during gridding (every atomic of a warp hits
+// its own bank) and in the interleaved, padded FFT layout afterwards; the
+// first FFT pass converts.
 template <int LOG2G>
 __global__ void __launch_bounds__(512)
 k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_off,
@@ -168,99 +180,120 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
             int* __restrict__ kept, float2* __restrict__ h) {
   constexpr int G = 1 << LOG2G;
   constexpr int LDP = band_pitch(G);
+  constexpr int P = planar_pitch(G);
+  static_assert(P <= LDP, "planar band fits in the FFT layout");
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* band = reinterpret_cast<float2*>(smem);                     // [band_h][LDP]
+  float2* band = reinterpret_cast<float2*>(smem);                     // [band_h][LDP] (FFT layout)
+  float* pre = reinterpret_cast<float*>(smem);                        // [band_h][P]   (gridding)
+  float* pim = pre + band_h * P;
   float2* tw = band + band_h * LDP;                                   // [G]
-  float2* r_wuv = tw + G;                                             // [kRecMax][7]
-  int* r_ku0 = reinterpret_cast<int*>(r_wuv + kRecMax * kSupport);    // [kRecMax]
-  int* r_kv0 = r_ku0 + kRecMax;                                       // first row, band-relative
-  int* r_offv = r_kv0 + kRecMax;
+  float4* r_hdr = reinterpret_cast<float4*>(tw + G);                  // [kRecMax] (Vr, Vi, base, kv_rel)
+  float2* r_wu = reinterpret_cast<float2*>(r_hdr + kRecMax);          // [kRecMax][kWuStride]
+  float* r_wv = reinterpret_cast<float*>(r_wu + kRecMax * kWuStride); // [kRecMax][kWvStride]
   __shared__ int n_home, n_rec;
   const int b = blockIdx.x, cb = blockIdx.y;
   const long long chan = ch0 + cb;
-  for (int i = threadIdx.x; i < band_h * LDP; i += blockDim.x) band[i] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < 2 * band_h * P; i += blockDim.x) pre[i] = 0.0f;
   for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
   if (threadIdx.x == 0) n_home = 0;
   const ChanScale s = cs[chan];
   const int row0 = b * band_h;
   const int cmax = G / 2 - kHalfSup - 1;
-  const int lane = threadIdx.x & 31;
+  const long long lim = static_cast<long long>(cmax + 1) * kQ;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  const int axis = threadIdx.x & 1;                  // 0: u, 1: v
+  const int chunk = blockDim.x >> 1;
+  const unsigned full = 0xffffffffu;
+  const int4* vis4 = reinterpret_cast<const int4*>(vis);
   int my_home = 0;
   const int e0 = band_off[b], e1 = band_off[b + 1];
-  for (int c0 = e0; c0 < e1; c0 += blockDim.x) {
+  for (int c0 = e0; c0 < e1; c0 += chunk) {
     if (threadIdx.x == 0) n_rec = 0;
     __syncthreads();
-    // ---- prepare: one candidate per thread
-    const int e = c0 + threadIdx.x;
-    bool use = false;
-    int ku0 = 0, kv_rel = 0, offv = 0, offu = 0;
-    float vr = 0.f, vi = 0.f;
-    if (e < e1) {
+    // ---- prepare: one visibility per thread pair
+    const int e = c0 + (threadIdx.x >> 1);
+    const bool valid = e < e1;
+    int bl = 0, cc = 0, off = 0;
+    bool in = false;
+    if (valid) {
       const GridEntry en = entries[e];
-      long long pu = 0, pv = 0;
-      const bool fast = fast_rint_prod(en.dxh, en.dxl, s, &pu) & fast_rint_prod(en.dyh, en.dyl, s, &pv);
-      if (!fast) {                                     // FP64 product of the definition
-        const Baseline B = base[en.cross];
-        pu = __double2ll_rn(__dmul_rn(B.dx, s.s));
-        pv = __double2ll_rn(__dmul_rn(B.dy, s.s));
+      bl = en.bl;
+      long long pc;
+      if (!fast_rint_prod(axis ? en.dyh : en.dxh, axis ? en.dyl : en.dxl, s, &pc)) {
+        const Baseline B = base[en.cross];           // FP64 product of the definition
+        pc = __double2ll_rn(__dmul_rn(axis ? B.dy : B.dx, s.s));
       }
-      const long long lim = static_cast<long long>(cmax + 1) * kQ;
-      if (pu > -lim && pu < lim && pv > -lim && pv < lim) {
-        int c0u, c0v;
-        centre_cell(pu, c0u, offu);
-        centre_cell(pv, c0v, offv);
-        if (c0u <= cmax && c0u >= -cmax && c0v <= cmax && c0v >= -cmax) {
-          const int kv_home = G / 2 + c0v;
-          if (kv_home >= row0 && kv_home < row0 + band_h) ++my_home;
-          kv_rel = kv_home - kHalfSup - row0;
-          ku0 = G / 2 + c0u - kHalfSup;
-          if (kv_rel + kSupport > 0 && kv_rel < band_h) {
-            use = true;
-            const int4* v = reinterpret_cast<const int4*>(vis + (chan * n_bl + en.bl) * 8);
-            const int4 xx_xy = __ldg(v);
-            const int4 yx_yy = __ldg(v + 1);
-            // conj of Stokes I: the exp(+) transform is a forward FFT of conj(G)
-            vr = 0.5f * static_cast<float>(xx_xy.x + yx_yy.z);
-            vi = -0.5f * static_cast<float>(xx_xy.y + yx_yy.w);
-          }
-        }
+      if (pc > -lim && pc < lim) {
+        centre_cell(pc, cc, off);
+        in = cc <= cmax && cc >= -cmax;
       }
     }
-    const unsigned m = __ballot_sync(0xffffffffu, use);
+    const int cc_o = __shfl_xor_sync(full, cc, 1);
+    const int in_o = __shfl_xor_sync(full, in ? 1 : 0, 1);   // every lane takes part
+    const bool keep = in && in_o;
+    const int cu = axis ? cc_o : cc, cv = axis ? cc : cc_o;
+    const int kv_home = G / 2 + cv;
+    const int kv_rel = kv_home - kHalfSup - row0;
+    const int ku0 = G / 2 + cu - kHalfSup;
+    if (keep && axis && kv_home >= row0 && kv_home < row0 + band_h) ++my_home;
+    const bool use = keep && kv_rel + kSupport > 0 && kv_rel < band_h;
+    // Stokes I = (XX + YY) / 2: XX on the even thread, YY on the odd one
+    int sr = 0, si = 0;
+    if (use) {
+      const int4 q = __ldg(vis4 + (chan * n_bl + bl) * 2 + axis);
+      sr = axis ? q.z : q.x;
+      si = axis ? q.w : q.y;
+    }
+    sr += __shfl_xor_sync(full, sr, 1);
+    si += __shfl_xor_sync(full, si, 1);
+    const unsigned m = __ballot_sync(full, use) & 0x55555555u;
     int base_slot = 0;
     if (lane == 0 && m) base_slot = atomicAdd(&n_rec, __popc(m));
-    base_slot = __shfl_sync(0xffffffffu, base_slot, 0);
+    base_slot = __shfl_sync(full, base_slot, 0);
     if (use) {
-      const int slot = base_slot + __popc(m & ((1u << lane) - 1u));
-      r_ku0[slot] = ku0;
-      r_kv0[slot] = kv_rel;
-      r_offv[slot] = offv;
+      const int slot = base_slot + __popc(m & ((1u << (lane & ~1)) - 1u));
+      float w[8];
 #pragma unroll
-      for (int t = 0; t < kSupport; ++t) {
-        float w = __ldg(tab + kHalfTab + (t - kHalfSup) * kQ - offu);
-        if ((ku0 + t) & 1) w = -w;                                   // (-1)^ku centring sign
-        r_wuv[slot * kSupport + t] = make_float2(w * vr, w * vi);
+      for (int t = 0; t < kSupport; ++t) w[t] = __ldg(tab + kHalfTab + (t - kHalfSup) * kQ - off);
+      w[7] = 0.0f;
+      if (axis == 0) {
+        // (-1)^ku centring sign; conj of Stokes I: the exp(+) transform is a
+        // forward FFT of conj(G)
+#pragma unroll
+        for (int t = 0; t < kSupport; ++t)
+          if ((ku0 + t) & 1) w[t] = -w[t];
+        r_hdr[slot] = make_float4(0.5f * static_cast<float>(sr), -0.5f * static_cast<float>(si),
+                                  __int_as_float(kv_rel * P + ku0), __int_as_float(kv_rel));
+#pragma unroll
+        for (int t = 0; t < 4; ++t) r_wu[slot * kWuStride + t] = make_float2(w[t], w[t + 4]);
+      } else {
+        const int kv0 = row0 + kv_rel;               // (-1)^kv centring sign
+#pragma unroll
+        for (int t = 0; t < kSupport; ++t)
+          if ((kv0 + t) & 1) w[t] = -w[t];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) r_wv[slot * kWvStride + t] = w[t];
       }
     }
     __syncthreads();
-    // ---- sweep (visibility, row) items: seven taps each
+    // ---- sweep: one record per warp, 49 taps in four atomic instructions
     const int nr = n_rec;
-    for (int it = threadIdx.x; it < nr * kSupport; it += blockDim.x) {
-      const int rec = it / kSupport, tv = it - rec * kSupport;
-      const int row = r_kv0[rec] + tv;
-      if (row < 0 || row >= band_h) continue;
-      const int kv = row0 + row;
-      float wv = __ldg(tab + kHalfTab + (tv - kHalfSup) * kQ - r_offv[rec]);
-      if (kv & 1) wv = -wv;                                          // (-1)^kv centring sign
-      const int k0 = r_ku0[rec];
-      float2* dst = band + row * LDP;
-      const float2* wuv = r_wuv + rec * kSupport;
-#pragma unroll
-      for (int tu = 0; tu < kSupport; ++tu) {
-        const float2 a = wuv[tu];
-        float2* cell = dst + pad16(k0 + tu);
-        atomicAdd(&cell->x, wv * a.x);
-        atomicAdd(&cell->y, wv * a.y);
+    const int tv = lane >> 2, tu = lane & 3;
+    for (int rec = warp; rec < nr; rec += n_warps) {
+      const float4 hd = r_hdr[rec];
+      const float2 wp = r_wu[rec * kWuStride + tu];
+      const float wv = r_wv[rec * kWvStride + tv];
+      const int row = __float_as_int(hd.w) + tv;
+      if (tv < kSupport && static_cast<unsigned>(row) < static_cast<unsigned>(band_h)) {
+        const int a = __float_as_int(hd.z) + tv * P + tu;
+        const float w0 = wv * wp.x;
+        atomicAdd(pre + a, w0 * hd.x);
+        atomicAdd(pim + a, w0 * hd.y);
+        if (tu < kSupport - 4) {
+          const float w1 = wv * wp.y;
+          atomicAdd(pre + a + 4, w1 * hd.x);
+          atomicAdd(pim + a + 4, w1 * hd.y);
+        }
       }
     }
     __syncthreads();
@@ -268,13 +301,13 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
   if (my_home) atomicAdd(&n_home, my_home);
   __syncthreads();
   if (threadIdx.x == 0 && n_home) atomicAdd(kept + chan, n_home);
-  fft_rows_inplace<LOG2G>(band, LDP, tw);
+  fft_rows_inplace<LOG2G>(band, LDP, tw, pre, pim, P);
   // central N columns of each transformed row
-  const int off = G / 2 - n_img / 2;
+  const int offc = G / 2 - n_img / 2;
   float2* hb = h + (static_cast<long long>(cb) * G + row0) * n_img;
   for (int i = threadIdx.x; i < band_h * n_img; i += blockDim.x) {
     const int r = i / n_img, c = i - r * n_img;
-    hb[static_cast<long long>(r) * n_img + c] = band[r * LDP + pad16(off + c)];
+    hb[static_cast<long long>(r) * n_img + c] = band[r * LDP + pad16(offc + c)];
   }
 }
 
@@ -457,7 +490,7 @@ int launch_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long
   constexpr int LDP = band_pitch(G);
   {
     const size_t sm = static_cast<size_t>(p.band_h) * LDP * sizeof(float2) + G * sizeof(float2) +
-                      kRecMax * (kSupport * sizeof(float2) + 3 * sizeof(int));
+                      kRecMax * (sizeof(float4) + kWuStride * sizeof(float2) + kWvStride * sizeof(float));
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid_rows<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm)));
     const int threads = p.band_h * G / 16;
