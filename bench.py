@@ -105,6 +105,8 @@ def roofline_models(cfg, n_kept_vis, peaks):
         "k_walk": ("hbm", vox * 16, "B", n_chan),
         # boxcars: read z', write SNR and width
         "k_mf": ("hbm", vox * 9, "B", n_chan),
+        # NMS: a count pass and a write pass, each reading the SNR cube
+        "k_nms_warp": ("hbm", vox * 8, "B", n_chan),
     }, {"hbm": hbm, "alu": fp32_tflops, "tensor": bf16}
 
 

@@ -18,11 +18,15 @@
 //                    neighbourhood as register prefix sums and evaluates all 29
 //                    boxcars as prefix differences; keeps max SNR and width and
 //                    histograms the SNRs above the p = alpha floor.
-//  a11 host          Benjamini-Hochberg: the histogram bounds the cut to one
-//                    bin; k_compact gathers every voxel at or above that bin
-//                    and the exact step-up rule runs on that small set in FP64.
-//  a12 host          greedy 1D non-maximum suppression per pixel and coarse
-//                    channel.
+//  a11 host + k_gather_bin  Benjamini-Hochberg: counts above every histogram
+//                    bin edge are exact, so the step-up rule is decided bin by
+//                    bin in FP64; only a bin whose outcome the edges leave open
+//                    is gathered and ranked value by value.
+//  a12 k_nms_warp    greedy 1D non-maximum suppression per (pixel, coarse
+//      k_nms_big     channel) on the device, one warp per pair (one CTA with a
+//                    bitonic sort for pairs with many detections); a count
+//                    pass, a prefix sum and a write pass give the candidates
+//                    in (pixel, coarse, channel) order.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -511,30 +515,315 @@ k_mf(const float* __restrict__ zbuf, int n_valid, int nc, float* __restrict__ sn
     if (hist[i]) atomicAdd(ghist + i, static_cast<unsigned long long>(hist[i]));
 }
 
-// ---------------------------------------------------------- a11 compaction
-struct Det {
-  int coarse, p, k, width;
-  float snr;
-};
+// ------------------------------------------------- a11 exact BH cut, a12 NMS
+// ln Q(s), Q the upper Gaussian tail (same formula as the host side).
+__device__ double log_q_dev(double s) {
+  if (s < 25.0) return log(0.5 * erfc(s * 0.70710678118654752440));
+  const double s2 = s * s;
+  const double series = 1.0 - 1.0 / s2 + 3.0 / (s2 * s2) - 15.0 / (s2 * s2 * s2) + 105.0 / (s2 * s2 * s2 * s2);
+  return -0.5 * s2 - log(s * 2.50662827463100050242) + log(series);
+}
 
-__global__ void k_compact(const float* __restrict__ snr, const uint8_t* __restrict__ width,
-                          long long n, int n_valid, int nc, int coarse, float cut, Det* __restrict__ out,
-                          int cap, int* __restrict__ count) {
+// Values of one histogram bin (key >> kHistShift == kb; the top bin takes
+// every larger key as well), for the exact BH step-up inside that bin.
+__global__ void k_gather_bin(const float* __restrict__ snr, long long n, uint32_t kb, int top,
+                             float* __restrict__ out, int cap, int* __restrict__ count) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const float v = snr[i];
-    if (v >= cut) {
+    const uint32_t b = f2key(v) >> kHistShift;
+    if (b == kb || (top && b > kb)) {
       const int slot = atomicAdd(count, 1);
-      if (slot < cap) {
-        Det d;
-        d.coarse = coarse;
-        d.p = static_cast<int>(i / nc);
-        d.k = static_cast<int>(i - static_cast<long long>(d.p) * nc);
-        d.width = width[i];
-        d.snr = v;
-        out[slot] = d;
+      if (slot < cap) out[slot] = v;
+    }
+  }
+}
+
+// One detection as the kernels hand it to the host.
+struct CandRec {
+  int coarse, p, k, width;
+  float snr, pad;
+  double log10_p;
+};
+
+constexpr int kNmsCap = 256;          // detections a warp holds for one (pixel, coarse) pair
+constexpr int kNmsWarps = 8;
+
+// a12, one warp per (pixel, coarse) pair, pair q = p * n_coarse + c (the output
+// order).  The pair's detections (SNR >= cut) are gathered in channel order;
+// greedy NMS repeatedly accepts the undecided detection of highest SNR
+// (lowest channel on ties) and suppresses the undecided ones within
+// max(1, w / 2) channels of it, w the accepted width -- the same decisions as
+// walking the list in descending SNR.  mode 0 counts the accepted detections
+// of each pair (pairs with more than kNmsCap detections go to the overflow
+// list and k_nms_big); mode 1 writes them, in channel order, at pair_off[q].
+__global__ void __launch_bounds__(kNmsWarps * 32)
+k_nms_warp(const float* __restrict__ snr, const uint8_t* __restrict__ width, const long long* __restrict__ vox0,
+           const int* __restrict__ nfft, int n_coarse, long long n_pairs, float cut, int mode,
+           int* __restrict__ pair_cnt, const int* __restrict__ pair_off, int* __restrict__ ovf,
+           int* __restrict__ n_ovf, CandRec* __restrict__ out, int out_cap) {
+  __shared__ uint32_t lk[kNmsWarps][kNmsCap];       // (k << 8) | width
+  __shared__ float lv[kNmsWarps][kNmsCap];
+  __shared__ uint8_t st[kNmsWarps][kNmsCap];        // 0 undecided, 1 accepted, 2 suppressed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long q = static_cast<long long>(blockIdx.x) * kNmsWarps + warp;
+  if (q >= n_pairs) return;                         // whole warps leave together
+  const int p = static_cast<int>(q / n_coarse), c = static_cast<int>(q - static_cast<long long>(p) * n_coarse);
+  const int nc = nfft[c];
+  const long long base = vox0[c] + static_cast<long long>(p) * nc;
+  const unsigned full = 0xffffffffu, lt = (1u << lane) - 1u;
+  uint32_t* K = lk[warp];
+  float* V = lv[warp];
+  uint8_t* S = st[warp];
+  int n = 0;
+  bool over = false;
+  for (int k0 = 0; k0 < nc; k0 += 32) {
+    const int k = k0 + lane;
+    const float v = k < nc ? snr[base + k] : -INFINITY;
+    const bool hit = v >= cut;
+    const unsigned m = __ballot_sync(full, hit);
+    if (!m) continue;
+    if (n + __popc(m) > kNmsCap) { over = true; break; }
+    if (hit) {
+      const int i = n + __popc(m & lt);
+      K[i] = (static_cast<uint32_t>(k) << 8) | width[base + k];
+      V[i] = v;
+      S[i] = 0;
+    }
+    n += __popc(m);
+  }
+  if (over) {
+    if (mode == 0 && lane == 0) {
+      ovf[atomicAdd(n_ovf, 1)] = static_cast<int>(q);
+      pair_cnt[q] = 0;                              // k_nms_big writes the count
+    }
+    return;
+  }
+  __syncwarp();
+  int n_acc = 0;
+  for (;;) {
+    float bv = -INFINITY;
+    int bi = -1;
+    for (int i = lane; i < n; i += 32)
+      if (S[i] == 0 && (bi < 0 || V[i] > bv)) { bv = V[i]; bi = i; }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const float ov = __shfl_xor_sync(full, bv, o);
+      const int oi = __shfl_xor_sync(full, bi, o);
+      if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+    }
+    if (bi < 0) break;
+    const int ka = static_cast<int>(K[bi] >> 8);
+    const int r = max(1, static_cast<int>(K[bi] & 255u) / 2);
+    for (int i = lane; i < n; i += 32)
+      if (S[i] == 0) {
+        if (i == bi) S[i] = 1;
+        else if (abs(static_cast<int>(K[i] >> 8) - ka) <= r) S[i] = 2;
+      }
+    __syncwarp();
+    ++n_acc;
+  }
+  if (mode == 0) {
+    if (lane == 0) pair_cnt[q] = n_acc;
+    return;
+  }
+  int j = pair_off[q];
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    const bool a = i < n && S[i] == 1;
+    const unsigned m = __ballot_sync(full, a);
+    if (a) {
+      const int o = j + __popc(m & lt);
+      if (o < out_cap) {
+        CandRec rc;
+        rc.coarse = c;
+        rc.p = p;
+        rc.k = static_cast<int>(K[i] >> 8);
+        rc.width = static_cast<int>(K[i] & 255u);
+        rc.snr = V[i];
+        rc.pad = 0.f;
+        rc.log10_p = log_q_dev(static_cast<double>(V[i])) * 0.43429448190325182765;
+        out[o] = rc;
       }
     }
+    j += __popc(m);
+  }
+}
+
+// a12 for pairs with more than kNmsCap detections: one CTA per pair.  The
+// detections are sorted by (SNR descending, channel ascending) with a bitonic
+// sort in shared memory, then one warp walks them in that order against a
+// bitmap of covered channels.  Shared memory: p2max 64-bit keys and two
+// bitmaps of nc_max bits.
+__global__ void __launch_bounds__(1024)
+k_nms_big(const float* __restrict__ snr, const uint8_t* __restrict__ width, const long long* __restrict__ vox0,
+          const int* __restrict__ nfft, int n_coarse, const int* __restrict__ ovf, const int* __restrict__ n_ovf,
+          int p2max, float cut, int mode, int* __restrict__ pair_cnt, const int* __restrict__ pair_off,
+          CandRec* __restrict__ out, int out_cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);       // [p2max]
+  uint32_t* cov = reinterpret_cast<uint32_t*>(keys + p2max);                     // [p2max / 32]
+  uint32_t* acc = cov + p2max / 32;                                              // [p2max / 32]
+  uint32_t* scan = acc + p2max / 32;                                             // [1024]
+  uint32_t* wtot = scan + 1024;                                                  // [32]
+  __shared__ int s_n;
+  if (blockIdx.x >= *n_ovf) return;
+  const int q = ovf[blockIdx.x];
+  const int p = q / n_coarse, c = q - p * n_coarse;
+  const int nc = nfft[c];
+  const long long base = vox0[c] + static_cast<long long>(p) * nc;
+  const int tid = threadIdx.x, T = blockDim.x;
+  if (tid == 0) s_n = 0;
+  for (int i = tid; i < p2max / 32; i += T) { cov[i] = 0u; acc[i] = 0u; }
+  __syncthreads();
+  // gather in channel order
+  for (int k0 = 0; k0 < nc; k0 += T) {
+    const int k = k0 + tid;
+    const float v = k < nc ? snr[base + k] : -INFINITY;
+    const bool hit = v >= cut;
+    scan[tid] = hit ? 1u : 0u;
+    __syncthreads();
+    block_exclusive_scan(scan, T, wtot);
+    const int n0 = s_n;
+    if (hit) {
+      const uint32_t lo = (static_cast<uint32_t>(k) << 8) | width[base + k];
+      keys[n0 + scan[tid]] = (static_cast<unsigned long long>(~f2key(v)) << 32) | lo;
+    }
+    __syncthreads();
+    if (tid == T - 1) s_n = n0 + static_cast<int>(scan[tid]) + (hit ? 1 : 0);
+    __syncthreads();
+  }
+  const int n = s_n;
+  int p2 = 1;
+  while (p2 < n) p2 <<= 1;
+  for (int i = n + tid; i < p2; i += T) keys[i] = ~0ull;
+  __syncthreads();
+  for (int size = 2; size <= p2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = tid; t < p2 / 2; t += T) {
+        const int i = (t / stride) * 2 * stride + (t % stride);
+        const int j = i + stride;
+        const bool up = (i & size) == 0;
+        const unsigned long long a = keys[i], b = keys[j];
+        if ((a > b) == up) { keys[i] = b; keys[j] = a; }
+      }
+      __syncthreads();
+    }
+  if (tid < 32) {
+    for (int i = 0; i < n; ++i) {
+      const uint32_t lo = static_cast<uint32_t>(keys[i]);
+      const int k = static_cast<int>(lo >> 8);
+      if ((cov[k >> 5] >> (k & 31)) & 1u) continue;
+      const int r = max(1, static_cast<int>(lo & 255u) / 2);
+      const int a = max(0, k - r), b = min(nc - 1, k + r);
+      for (int x = a + tid; x <= b; x += 32) atomicOr(&cov[x >> 5], 1u << (x & 31));
+      if (tid == 0) acc[k >> 5] |= 1u << (k & 31);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const int words = (nc + 31) / 32;
+  if (mode == 0) {
+    int my = 0;
+    for (int i = tid; i < words; i += T) my += __popc(acc[i]);
+    for (int o = 16; o; o >>= 1) my += __shfl_xor_sync(0xffffffffu, my, o);
+    if ((tid & 31) == 0 && my) atomicAdd(&pair_cnt[q], my);
+    return;
+  }
+  int j0 = pair_off[q];
+  for (int w0 = 0; w0 < words; w0 += T) {
+    const int wi = w0 + tid;
+    const uint32_t bits = wi < words ? acc[wi] : 0u;
+    scan[tid] = __popc(bits);
+    __syncthreads();
+    block_exclusive_scan(scan, T, wtot);
+    int o = j0 + static_cast<int>(scan[tid]);
+    for (uint32_t b = bits; b; b &= b - 1) {
+      const int k = wi * 32 + __ffs(b) - 1;
+      if (o < out_cap) {
+        CandRec rc;
+        rc.coarse = c;
+        rc.p = p;
+        rc.k = k;
+        rc.width = width[base + k];
+        rc.snr = snr[base + k];
+        rc.pad = 0.f;
+        rc.log10_p = log_q_dev(static_cast<double>(rc.snr)) * 0.43429448190325182765;
+        out[o] = rc;
+      }
+      ++o;
+    }
+    __syncthreads();
+    if (tid == T - 1) scan[0] = scan[tid] + __popc(bits);
+    __syncthreads();
+    j0 += static_cast<int>(scan[0]);
+    __syncthreads();
+  }
+}
+
+// Exclusive prefix sums of pair_cnt (n entries) into pair_off[0..n]: per-block
+// sums, a single-block scan of those, then the block offsets.
+constexpr int kScanPer = 4096;         // entries per block (1024 threads x 4)
+__global__ void k_scan_blocks(const int* __restrict__ a, long long n, int* __restrict__ sums) {
+  __shared__ int red[32];
+  const long long b0 = static_cast<long long>(blockIdx.x) * kScanPer;
+  int s = 0;
+  for (int i = threadIdx.x; i < kScanPer; i += blockDim.x)
+    if (b0 + i < n) s += a[b0 + i];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) sums[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_scan_sums(int* __restrict__ sums, int nb, int* __restrict__ total) {
+  // single block: exclusive scan of nb block sums, sequential per thread chunk
+  __shared__ uint32_t sc[1024];
+  __shared__ uint32_t wt[32];
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int per = (nb + T - 1) / T;
+  uint32_t my = 0;
+  for (int i = tid * per; i < min(nb, (tid + 1) * per); ++i) my += static_cast<uint32_t>(sums[i]);
+  sc[tid] = my;
+  __syncthreads();
+  block_exclusive_scan(sc, T, wt);
+  uint32_t run = sc[tid];
+  for (int i = tid * per; i < min(nb, (tid + 1) * per); ++i) {
+    const uint32_t v = static_cast<uint32_t>(sums[i]);
+    sums[i] = static_cast<int>(run);
+    run += v;
+  }
+  if (tid == T - 1) *total = static_cast<int>(sc[tid] + my);
+}
+
+__global__ void k_scan_apply(const int* __restrict__ a, long long n, const int* __restrict__ sums,
+                             int* __restrict__ out) {
+  __shared__ uint32_t sc[1024];
+  __shared__ uint32_t wt[32];
+  const long long b0 = static_cast<long long>(blockIdx.x) * kScanPer;
+  const int T = blockDim.x, tid = threadIdx.x;
+  constexpr int per = kScanPer / 1024;
+  int v[per];
+  uint32_t my = 0;
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    const long long i = b0 + static_cast<long long>(tid) * per + j;
+    v[j] = i < n ? a[i] : 0;
+    my += static_cast<uint32_t>(v[j]);
+  }
+  sc[tid] = my;
+  __syncthreads();
+  block_exclusive_scan(sc, T, wt);
+  int run = sums[blockIdx.x] + static_cast<int>(sc[tid]);
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    const long long i = b0 + static_cast<long long>(tid) * per + j;
+    if (i < n) out[i] = run;
+    run += v[j];
   }
 }
 
@@ -626,7 +915,8 @@ DetectPlan make_plan(int n_chan, int n, double cell, int n_coarse, const int32_t
 }
 
 constexpr int kMaxBins = 2048;
-constexpr int kDetCap = 1 << 22;
+constexpr int kGatherCap = 1 << 23;     // values of one histogram bin (exact BH step-up)
+constexpr int kCandCap = 1 << 21;       // candidates written by the NMS kernels
 
 struct DetectWs {
   int* pix;
@@ -638,14 +928,24 @@ struct DetectWs {
   float* snr;
   uint8_t* width;
   unsigned long long* hist;
-  Det* dets;
-  int* count;
+  float* vals;
+  long long* vox0;
+  int* nfft;
+  int* pair_cnt;
+  int* pair_off;
+  int* sums;
+  int* ovf;
+  CandRec* recs;
+  int* count;            // [0] gathered values, [1] overflow pairs, [2] candidates
 };
+
+long long n_pairs_of(const DetectPlan& p) { return static_cast<long long>(p.n_valid) * p.n_coarse; }
 
 DetectWs carve_detect(void* ws, size_t bytes, const DetectPlan& p, size_t* need) {
   Carver c(ws, bytes);
   DetectWs w;
   const size_t blk = static_cast<size_t>(p.n_valid) * p.max_nc;
+  const long long np = std::max(1LL, n_pairs_of(p));
   w.pix = c.take<int>(p.n_valid > 0 ? p.n_valid : 1);
   w.stats64 = c.take<double>(2 * static_cast<size_t>(p.n_chan));
   w.stats32 = c.take<float>(2 * static_cast<size_t>(p.n_chan));
@@ -655,7 +955,14 @@ DetectWs carve_detect(void* ws, size_t bytes, const DetectPlan& p, size_t* need)
   w.snr = c.take<float>(static_cast<size_t>(p.n_vox));
   w.width = c.take<uint8_t>(static_cast<size_t>(p.n_vox));
   w.hist = c.take<unsigned long long>(kMaxBins);
-  w.dets = c.take<Det>(kDetCap);
+  w.vals = c.take<float>(kGatherCap);
+  w.vox0 = c.take<long long>(p.n_coarse);
+  w.nfft = c.take<int>(p.n_coarse);
+  w.pair_cnt = c.take<int>(np);
+  w.pair_off = c.take<int>(np + 1);
+  w.sums = c.take<int>((np + kScanPer - 1) / kScanPer + 1);
+  w.ovf = c.take<int>(np);
+  w.recs = c.take<CandRec>(kCandCap);
   w.count = c.take<int>(4);
   *need = c.used;
   return w;
@@ -755,6 +1062,53 @@ void hist_range(const ovro_detect_params& prm, uint32_t* key0, int* n_bins) {
   int nb = static_cast<int>(top > *key0 ? top - *key0 : 0) + 1;   // + overflow bin
   if (nb > kMaxBins) nb = kMaxBins;
   *n_bins = nb;
+}
+
+// Exact Benjamini-Hochberg cut from the SNR histogram.  count(SNR >= s) is
+// known exactly at every bin edge, so a bin either surely holds the step-up
+// threshold's rank range (every value in it passes: cut at its lower edge),
+// surely cannot (no value passes), or is ambiguous -- then its values are
+// gathered and ranked exactly.  Bins are taken from the lowest one where a
+// rejection is possible upwards; the first passing value found is the cut
+// (the largest rank that passes).  Returns 0 with *cut set, 1 when nothing is
+// rejected, or an error status.
+int bh_cut(const std::vector<unsigned long long>& hist, uint32_t key0, int nb, double m, double alpha,
+           const DetectWs& w, const DetectPlan& p, cudaStream_t st, int nsm, float* cut) {
+  std::vector<unsigned long long> above(nb + 1, 0);     // count(SNR >= lower edge of bin b)
+  for (int b = nb - 1; b >= 0; --b) above[b] = above[b + 1] + hist[b];
+  auto edge = [&](int b) { return static_cast<double>(host_key2f((key0 + b) << kHistShift)); };
+  auto passes = [&](double s, unsigned long long rank) {
+    return log_q(s) <= std::log(alpha * static_cast<double>(rank) / m);
+  };
+  for (int b = 0; b < nb; ++b) {
+    if (hist[b] == 0) continue;
+    const unsigned long long hi_rank = above[b], lo_rank = above[b + 1] + 1;
+    const bool top = b == nb - 1;
+    if (!top && !passes(edge(b + 1), hi_rank)) continue;          // no value of the bin can pass
+    if (passes(edge(b), lo_rank)) {                               // every value passes
+      *cut = host_key2f((key0 + b) << kHistShift);
+      return 0;
+    }
+    if (hist[b] > static_cast<unsigned long long>(kGatherCap)) return OVRO_ERR_CAPACITY;
+    OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, sizeof(int), st));
+    k_gather_bin<<<8 * nsm, 256, 0, st>>>(w.snr, p.n_vox, key0 + b, top ? 1 : 0, w.vals, kGatherCap, w.count);
+    OVRO_LAUNCH_CHECK();
+    int nv = 0;
+    OVRO_CUDA_TRY(cudaMemcpyAsync(&nv, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+    if (static_cast<unsigned long long>(nv) != hist[b]) return OVRO_ERR_CAPACITY;
+    std::vector<float> v(nv);
+    OVRO_CUDA_TRY(cudaMemcpy(v.data(), w.vals, nv * sizeof(float), cudaMemcpyDeviceToHost));
+    std::sort(v.begin(), v.end(), std::greater<float>());
+    int best = -1;
+    for (int j = 0; j < nv; ++j)
+      if (passes(v[j], above[b + 1] + j + 1)) best = j;
+    if (best >= 0) {
+      *cut = v[best];
+      return 0;
+    }
+  }
+  return 1;
 }
 
 }  // namespace
@@ -875,91 +1229,86 @@ int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dirc
   OVRO_CUDA_TRY(cudaStreamSynchronize(st));
   if (status) return OVRO_ERR_CAPACITY;
   const double m = static_cast<double>(p.n_valid) * n_chan;
+  const int nsm = num_sms();
   float cut;
   if (params->mode == OVRO_DETECT_FIXED) {
     cut = static_cast<float>(params->nsigma);
   } else {
-    // lowest bin where a rejection is possible: Q(upper edge) <= alpha * count(>= lower edge) / m
-    unsigned long long above = 0;      // count(SNR >= lower edge of bin b)
-    int lowest = -1;
-    for (int b = nb - 1; b >= 0; --b) {
-      above += hist[b];
-      const double up = (b == nb - 1) ? 1e30 : static_cast<double>(host_key2f((key0 + b + 1) << kHistShift));
-      const double lq_up = up >= 1e29 ? -1e300 : log_q(up);
-      if (above > 0 && lq_up <= std::log(params->alpha * static_cast<double>(above) / m)) lowest = b;
-    }
-    if (lowest < 0) return OVRO_OK;    // nothing can be rejected
-    cut = host_key2f((key0 + lowest) << kHistShift);
+    int e = bh_cut(hist, key0, nb, m, params->alpha, w, p, st, nsm, &cut);
+    if (e == 1) return OVRO_OK;        // nothing is rejected
+    if (e) return e;
   }
-  // ---- gather everything at or above the cut
-  OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, sizeof(int), st));
-  const int nsm = num_sms();
-  for (int c = 0; c < p.n_coarse; ++c) {
-    const long long nv = static_cast<long long>(p.n_valid) * p.nfft[c];
-    k_compact<<<8 * nsm, 256, 0, st>>>(w.snr + p.vox0[c], w.width + p.vox0[c], nv, p.n_valid, p.nfft[c], c,
-                                       cut, w.dets, kDetCap, w.count);
+  // ---- a12: NMS on the device, candidates in (pixel, coarse, channel) order
+  const long long np = n_pairs_of(p);
+  if (np > 0x7fffffffLL / 2) return OVRO_ERR_UNSUPPORTED;
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.vox0, p.vox0.data(), p.n_coarse * sizeof(long long), cudaMemcpyHostToDevice, st));
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.nfft, p.nfft.data(), p.n_coarse * sizeof(int), cudaMemcpyHostToDevice, st));
+  OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, 4 * sizeof(int), st));
+  const unsigned nms_blocks = static_cast<unsigned>((np + kNmsWarps - 1) / kNmsWarps);
+  {
+    OVRO_PROF("k_nms_warp", st);
+    k_nms_warp<<<nms_blocks, kNmsWarps * 32, 0, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, np, cut, 0,
+                                                       w.pair_cnt, w.pair_off, w.ovf, w.count + 1, w.recs, kCandCap);
     OVRO_LAUNCH_CHECK();
   }
-  int nd = 0;
-  OVRO_CUDA_TRY(cudaMemcpyAsync(&nd, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int n_ovf = 0;
+  OVRO_CUDA_TRY(cudaMemcpyAsync(&n_ovf, w.count + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   OVRO_CUDA_TRY(cudaStreamSynchronize(st));
-  if (nd > kDetCap) return OVRO_ERR_CAPACITY;
-  std::vector<Det> dets(nd);
-  if (nd) OVRO_CUDA_TRY(cudaMemcpy(dets.data(), w.dets, nd * sizeof(Det), cudaMemcpyDeviceToHost));
-  if (params->mode == OVRO_DETECT_BH) {
-    // exact step-up rule on the gathered set (all voxels with SNR >= cut are present)
-    std::vector<float> s(nd);
-    for (int i = 0; i < nd; ++i) s[i] = dets[i].snr;
-    std::sort(s.begin(), s.end(), std::greater<float>());
-    int kmax = 0;
-    for (int i = 1; i <= nd; ++i)
-      if (log_q(s[i - 1]) <= std::log(static_cast<double>(i) * params->alpha / m)) kmax = i;
-    if (kmax == 0) return OVRO_OK;
-    const float thr = s[kmax - 1];
-    dets.erase(std::remove_if(dets.begin(), dets.end(), [&](const Det& d) { return d.snr < thr; }), dets.end());
+  int p2max = 32;
+  while (p2max < p.max_nc) p2max <<= 1;
+  const size_t big_sm = static_cast<size_t>(p2max) * 8 + 2 * static_cast<size_t>(p2max / 32) * 4 + 1056 * 4;
+  if (n_ovf > 0) {
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_nms_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(big_sm)));
+    k_nms_big<<<n_ovf, 1024, big_sm, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, w.ovf, w.count + 1, p2max,
+                                           cut, 0, w.pair_cnt, w.pair_off, w.recs, kCandCap);
+    OVRO_LAUNCH_CHECK();
   }
-  // ---- a12: greedy NMS per (pixel, coarse channel)
-  std::sort(dets.begin(), dets.end(), [](const Det& a, const Det& b) {
-    if (a.p != b.p) return a.p < b.p;
-    if (a.coarse != b.coarse) return a.coarse < b.coarse;
-    if (a.snr != b.snr) return a.snr > b.snr;
-    return a.k < b.k;
-  });
-  std::vector<Det> keep;
-  size_t i = 0;
-  while (i < dets.size()) {
-    size_t j = i;
-    while (j < dets.size() && dets[j].p == dets[i].p && dets[j].coarse == dets[i].coarse) ++j;
-    std::vector<Det> acc;
-    for (size_t q = i; q < j; ++q) {
-      bool sup = false;
-      for (const Det& a : acc)
-        if (std::abs(dets[q].k - a.k) <= std::max(1, a.width / 2)) { sup = true; break; }
-      if (!sup) acc.push_back(dets[q]);
-    }
-    std::sort(acc.begin(), acc.end(), [](const Det& a, const Det& b) { return a.k < b.k; });
-    keep.insert(keep.end(), acc.begin(), acc.end());
-    i = j;
+  const unsigned sblocks = static_cast<unsigned>((np + kScanPer - 1) / kScanPer);
+  k_scan_blocks<<<sblocks, 1024, 0, st>>>(w.pair_cnt, np, w.sums);
+  OVRO_LAUNCH_CHECK();
+  k_scan_sums<<<1, 1024, 0, st>>>(w.sums, static_cast<int>(sblocks), w.count + 2);
+  OVRO_LAUNCH_CHECK();
+  k_scan_apply<<<sblocks, 1024, 0, st>>>(w.pair_cnt, np, w.sums, w.pair_off);
+  OVRO_LAUNCH_CHECK();
+  {
+    OVRO_PROF("k_nms_warp", st);
+    k_nms_warp<<<nms_blocks, kNmsWarps * 32, 0, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, np, cut, 1,
+                                                       w.pair_cnt, w.pair_off, w.ovf, w.count + 1, w.recs, kCandCap);
+    OVRO_LAUNCH_CHECK();
   }
-  const int total = static_cast<int>(keep.size());
+  if (n_ovf > 0) {
+    k_nms_big<<<n_ovf, 1024, big_sm, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, w.ovf, w.count + 1, p2max,
+                                           cut, 1, w.pair_cnt, w.pair_off, w.recs, kCandCap);
+    OVRO_LAUNCH_CHECK();
+  }
+  int total = 0;
+  OVRO_CUDA_TRY(cudaMemcpyAsync(&total, w.count + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
   *n_out = total;
-  const int nw = std::min(total, max_out);
-  for (int q = 0; q < nw; ++q) {
-    const Det& d = keep[q];
-    ovro_candidate& o = h_out[q];
-    const int pixel = p.pix[d.p];
-    o.coarse = d.coarse;
-    o.fine = d.k;
-    o.chan = p.chan0[d.coarse] + d.k;
-    o.row = pixel / image_size;
-    o.col = pixel % image_size;
-    o.width = d.width;
-    o.snr = d.snr;
-    o.pad_ = 0.f;
-    o.freq_hz = h_chan_freq_hz[o.chan];
-    o.log10_p = log_q(d.snr) / std::log(10.0);
+  const int nw = std::min(std::min(total, max_out), kCandCap);
+  if (nw > 0) {
+    std::vector<CandRec> recs(nw);
+    OVRO_CUDA_TRY(cudaMemcpyAsync(recs.data(), w.recs, nw * sizeof(CandRec), cudaMemcpyDeviceToHost, st));
+    OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int q = 0; q < nw; ++q) {
+      const CandRec& d = recs[q];
+      ovro_candidate& o = h_out[q];
+      const int pixel = p.pix[d.p];
+      o.coarse = d.coarse;
+      o.fine = d.k;
+      o.chan = p.chan0[d.coarse] + d.k;
+      o.row = pixel / image_size;
+      o.col = pixel % image_size;
+      o.width = d.width;
+      o.snr = d.snr;
+      o.pad_ = 0.f;
+      o.freq_hz = h_chan_freq_hz[o.chan];
+      o.log10_p = d.log10_p;
+    }
   }
-  return total > max_out ? OVRO_ERR_CAPACITY : OVRO_OK;
+  if (total > max_out) return OVRO_ERR_CAPACITY;
+  return total > kCandCap ? OVRO_ERR_CAPACITY : OVRO_OK;
 }
 
 }  // extern "C"

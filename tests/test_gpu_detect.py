@@ -115,3 +115,47 @@ def test_tiny_pipeline_end_to_end(lib):
     assert gs == rs
     t = cfg.tones[0]
     assert (sum(cfg.nfft[: t.coarse]) + t.fine, t.row, t.col) in gs
+
+
+def _sets_vs_oracle(lib, cube, cell, nfft, mode, **kw):
+    mask = OI.horizon_mask(cube.shape[1], cell)
+    freqs = synth.fine_freqs_hz(nfft)
+    prm = lib.detect_params(mode=mode, **kw)
+    got = lib.detect(torch.from_numpy(cube).cuda(), cell, nfft, freqs, prm)
+    ref = OD.detect(cube.astype(np.float64), mask, nfft, mode="bh" if mode == lib.DETECT_BH else "fixed", **kw)
+    gs = {(int(c["chan"]), int(c["row"]), int(c["col"]), int(c["width"])) for c in got}
+    rs = {(c.chan, c.row, c.col, c.width) for c in ref}
+    assert gs == rs, (len(gs), len(rs), sorted(gs ^ rs)[:10])
+    # candidates come out in (pixel, coarse, channel) order
+    key = [(int(c["row"]) * cube.shape[1] + int(c["col"]), int(c["coarse"]), int(c["fine"])) for c in got]
+    assert key == sorted(key)
+    return got
+
+
+def test_nms_pair_with_many_detections(lib):
+    # one pixel with spikes in ~40% of 1024 channels: > 256 detections in one
+    # (pixel, coarse) pair takes the one-CTA-per-pair path
+    g = np.random.default_rng(21)
+    nfft = [1024, 256]
+    n, cell = 32, 0.02
+    cube = _cube(g, sum(nfft), n)
+    spikes = np.nonzero(g.uniform(size=1024) < 0.4)[0]
+    cube[spikes, 12, 17] += 30.0
+    cube[[100, 400, 401, 700, 1100], 5, 9] += 30.0  # smaller pairs (warp path)
+    got = _sets_vs_oracle(lib, cube, cell, nfft, lib.DETECT_FIXED, nsigma=5.0)
+    _, aux = OD.detect(cube.astype(np.float64), OI.horizon_mask(n, cell), nfft, mode="fixed", nsigma=5.0,
+                       return_all=True)
+    assert aux["sel"][:1024, 12, 17].sum() > 256 and 0 < aux["sel"][:1024, 5, 9].sum() <= 256
+    assert aux["sel"][1024:, 5, 9].sum() > 0
+    assert any((c["row"], c["col"]) == (12, 17) for c in got)
+
+
+def test_bh_heavy_tails(lib):
+    # Student-t noise: BH rejects many voxels, so the histogram edges leave
+    # bins open and their values are ranked exactly
+    g = np.random.default_rng(22)
+    nfft = [512, 512]
+    n, cell = 32, 0.02
+    cube = (g.standard_t(2.5, size=(sum(nfft), n, n)) * 2.0).astype(np.float32)
+    got = _sets_vs_oracle(lib, cube, cell, nfft, lib.DETECT_BH, alpha=0.05)
+    assert len(got) > 20
