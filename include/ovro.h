@@ -295,6 +295,84 @@ int ovro_scorer_adam(float* d_master, float* d_m, float* d_v, const float* d_gra
 /* BF16 copy (round to nearest even) of the FP32 master weights. */
 int ovro_scorer_to_bf16(const float* d_master, void* d_w_bf16, void* stream);
 
+/* -------------------------------------------------------------------------
+ * a14  Batched pipeline: every coarse channel of an integration, one graph
+ *
+ * Section 2.1 processes the upchannelised data in batches because the
+ * intermediate products are too large to hold at once; this driver streams
+ * coarse channels through fixed buffers: for each coarse channel c,
+ * a1-a3 (ovro_upchan), a4 (ovro_correlate), a5-a7 (ovro_grid_image) and
+ * a8-a10 (the detection filter) run into one set of buffers, and the SNR of
+ * every voxel of every coarse channel is kept; a11-a12 then run once over the
+ * whole integration (one Benjamini-Hochberg family, m = pixels x all fine
+ * channels).  Results equal ovro_upchan + ovro_correlate + ovro_grid_image +
+ * ovro_detect over all coarse channels at once.
+ *
+ * With use_graph, the device work of one integration (everything before the
+ * threshold) is captured once into a CUDA graph and replayed by later runs on
+ * the same voltage buffer (a new buffer address is captured anew).
+ * Launch shapes come from the autotuner's cache (ovro_autotune).
+ *
+ * The pipeline handle owns host memory only; the device workspace is the
+ * caller's (ovro_pipeline_workspace_size bytes, 256-byte aligned, bound with
+ * ovro_pipeline_bind and kept until ovro_pipeline_destroy).  A handle is used
+ * from one host thread at a time.
+ * ------------------------------------------------------------------------- */
+typedef struct ovro_pipeline ovro_pipeline;
+
+typedef struct {
+  int n_ant;                      /* dual-polarisation antennas (inputs = 2 n_ant) */
+  int n_coarse;
+  const int32_t* h_nfft;          /* [n_coarse] fine channels per coarse channel */
+  const double* h_coarse_hz;      /* [n_coarse] centre sky frequency of each coarse channel */
+  int64_t n_time;                 /* complex samples per coarse channel per integration */
+  const double* h_ant_enu_m;      /* [n_ant][3] antenna positions, metres */
+  int image_size;                 /* N */
+  double cell_dircos;             /* pixel size */
+  int xeng_mode;                  /* OVRO_XENG_TC or OVRO_XENG_FP32 */
+  ovro_detect_params detect;      /* threshold and filter parameters */
+  int use_graph;                  /* nonzero: replay the device work as a CUDA graph */
+} ovro_pipeline_config;
+
+/* Plans the pipeline (host only; the config's arrays are copied).  Fine
+ * channel k of coarse channel c is at h_coarse_hz[c] + (k - nfft/2) *
+ * coarse_bw_hz / nfft. */
+int ovro_pipeline_create(const ovro_pipeline_config* cfg, ovro_pipeline** out);
+size_t ovro_pipeline_workspace_size(const ovro_pipeline* pl);
+/* Binds the workspace and uploads the geometry tables (synchronises stream). */
+int ovro_pipeline_bind(ovro_pipeline* pl, void* d_ws, size_t ws_bytes, void* stream);
+/* One integration: d_volt uint8 [n_coarse][n_time][2 n_ant] packed 4+4-bit
+ * samples (as ovro_upchan).  Candidates as ovro_detect (synchronises stream).
+ * Returns OVRO_ERR_TIMEOUT if a tensor-core wait gave up in any coarse channel.
+ * While the autotuner is enabled, runs launch eagerly (no graph) and tune
+ * every site on first use; the graph is captured by the first run after it is
+ * disabled. */
+int ovro_pipeline_run(ovro_pipeline* pl, const uint8_t* d_volt, ovro_candidate* h_out, int max_out,
+                      int* n_out, void* stream);
+/* Fine channels in the integration and their sky frequencies (host array of
+ * that length, or NULL to query the count). */
+int ovro_pipeline_channels(const ovro_pipeline* pl, double* h_freq_or_null);
+/* Kernels the last run launched (graph replay, threshold and NMS included)
+ * and whether a graph is live. */
+int ovro_pipeline_stats(const ovro_pipeline* pl, long long* kernels_per_run, int* graph_live);
+void ovro_pipeline_destroy(ovro_pipeline* pl);
+
+/* -------------------------------------------------------------------------
+ * Autotuner: launch shapes (CTAs per SM of k_xeng_tc, k_rank and k_mf;
+ * channels per imaging launch) that give identical results are timed on first
+ * use while tuning is enabled (never inside a graph capture) and the fastest
+ * is cached per key "kernel/sm<SMs>/<shape...>".  Untuned keys use built-in
+ * defaults.  The cache is process-wide; save/load use a text file with one
+ * "key value" line per entry.
+ * ------------------------------------------------------------------------- */
+int ovro_autotune(int enable);
+int ovro_tune_get(const char* key, int* value);
+int ovro_tune_set(const char* key, int value);
+int ovro_tune_count(void);
+int ovro_tune_clear(void);
+int ovro_tune_save(const char* path);
+int ovro_tune_load(const char* path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,8 @@ static thread_local char g_last_error[256] = "";
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void sub_launches(unsigned long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 void set_last_error(const char* where, cudaError_t e) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));

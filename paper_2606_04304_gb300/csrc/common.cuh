@@ -21,12 +21,22 @@ void snprintf_last_error(const char* fmt, ...);
 // recorded on the launch stream around each traced kernel.
 bool profiling();
 void prof_mark(const char* name, cudaStream_t st, bool begin);
+// Adds n to the launch counter (kernels replayed by a CUDA graph launch).
+void add_launches(unsigned long long n);
+// Removes n from it (launches recorded into a graph capture, counted at replay).
+void sub_launches(unsigned long long n);
+
+// True while `st` is being captured into a CUDA graph (tracing is skipped then).
+inline bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
 
 struct ProfScope {
   const char* name;
   cudaStream_t st;
   bool on;
-  ProfScope(const char* n, cudaStream_t s) : name(n), st(s), on(profiling()) {
+  ProfScope(const char* n, cudaStream_t s) : name(n), st(s), on(profiling() && !capturing(s)) {
     if (on) prof_mark(name, st, true);
   }
   ~ProfScope() {

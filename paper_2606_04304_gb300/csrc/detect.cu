@@ -31,9 +31,12 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
+#include "stages.h"
+#include "tune.h"
 
 namespace ovro {
 namespace {
@@ -981,61 +984,104 @@ int validate(int n_chan, int n, double cell, int n_coarse, const int32_t* nfft) 
   return OVRO_OK;
 }
 
-int run_stats(const float* d_img, const DetectPlan& p, const DetectWs& w, cudaStream_t st) {
+// a8 for nc consecutive channel images starting at img; statistics to s64/s32.
+int run_stats_block(const float* img, int nc, double* s64, float* s32, const DetectPlan& p, const DetectWs& w,
+                    cudaStream_t st) {
   const size_t base = 2048 * 4 + 64 * 4 + 8 * 4 + 2048 * 8;
   const size_t sm = base + (p.stats_in_smem ? static_cast<size_t>(p.n_valid) * 4 : 0);
   OVRO_CUDA_TRY(cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
   OVRO_PROF("k_stats", st);
-  k_stats<<<p.n_chan, 1024, sm, st>>>(d_img, w.pix, p.n_valid, p.npix, p.stats_in_smem ? 1 : 0,
-                                      w.stats64, w.stats32);
+  k_stats<<<nc, 1024, sm, st>>>(img, w.pix, p.n_valid, p.npix, p.stats_in_smem ? 1 : 0, s64, s32);
   OVRO_LAUNCH_CHECK();
   return OVRO_OK;
 }
 
-// a9 + a10 for every coarse block: snr/width [coarse][pixel][k] in the workspace.
-int run_filter(const float* d_img, const DetectPlan& p, const DetectWs& w, uint32_t hist_key0,
-               int n_bins, float* d_zp_out, cudaStream_t st) {
+// a9 + a10 for coarse block c, whose nfft[c] images start at img_block:
+// snr/width [pixel][k] at vox0[c] in the workspace; the histogram accumulates.
+int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const DetectWs& w, uint32_t hist_key0,
+                      int n_bins, float* d_zp_out, cudaStream_t st) {
   const int nsm = num_sms();
-  for (int c = 0; c < p.n_coarse; ++c) {
-    const int nc = p.nfft[c];
-    {
-      dim3 g((p.n_valid + 31) / 32, (nc + 31) / 32);
-      OVRO_PROF("k_ztrans", st);
-      k_ztrans<<<g, 256, 0, st>>>(d_img, w.pix, p.n_valid, p.npix, p.chan0[c], nc, w.stats32, w.zbuf);
-      OVRO_LAUNCH_CHECK();
-    }
-    {
-      const int threads = 512, W = threads / 32;
-      const size_t sm = (256 * W + 32) * 4 + static_cast<size_t>(nc) * 12;
-      OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-      const int blocks = std::min(p.n_valid, 2 * nsm * 8);
+  const int nc = p.nfft[c];
+  {
+    dim3 g((p.n_valid + 31) / 32, (nc + 31) / 32);
+    OVRO_PROF("k_ztrans", st);
+    k_ztrans<<<g, 256, 0, st>>>(img_block, w.pix, p.n_valid, p.npix, 0, nc, w.stats32 + 2LL * p.chan0[c], w.zbuf);
+    OVRO_LAUNCH_CHECK();
+  }
+  {
+    const int threads = 512, W = threads / 32;
+    const size_t sm = (256 * W + 32) * 4 + static_cast<size_t>(nc) * 12;
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    // CTAs per SM (each CTA loops over pixels; the outputs do not depend on it)
+    auto rank = [&](int per_sm) -> int {
+      const int blocks = std::min(p.n_valid, per_sm * nsm);
       OVRO_PROF("k_rank", st);
       k_rank<<<blocks, threads, sm, st>>>(w.zbuf, p.n_valid, nc, p.half[c], w.sv, w.steps);
       OVRO_LAUNCH_CHECK();
-    }
-    {
-      const size_t sm = static_cast<size_t>((nc + 31) / 32) * kWalkThreads * 4;
-      OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-      OVRO_PROF("k_walk", st);
-      k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(
-          w.zbuf, w.sv, w.steps, p.n_valid, nc, p.half[c]);
-      OVRO_LAUNCH_CHECK();
-    }
-    if (d_zp_out) {
-      k_scatter<float><<<4 * nsm, 256, 0, st>>>(w.zbuf, w.pix, p.n_valid, nc, p.chan0[c], p.npix, d_zp_out);
-      OVRO_LAUNCH_CHECK();
-    }
-    {
-      const size_t sm = static_cast<size_t>(kMaxLo + nc + kMaxHi + kVox) * 4 + static_cast<size_t>(n_bins) * 4;
-      OVRO_CUDA_TRY(cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-      const int blocks = std::min(p.n_valid, 3 * nsm * 8);
+      return OVRO_OK;
+    };
+    const std::string key = tune_key("k_rank", {p.n_valid, nc});
+    int per_sm = tuned(key, 16);
+    if (tuning(st))
+      if (int e = tune_pick(key, {1, 2, 4, 16}, rank, st, &per_sm)) return e;
+    if (int e = rank(per_sm)) return e;
+  }
+  {
+    const size_t sm = static_cast<size_t>((nc + 31) / 32) * kWalkThreads * 4;
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    OVRO_PROF("k_walk", st);
+    k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(
+        w.zbuf, w.sv, w.steps, p.n_valid, nc, p.half[c]);
+    OVRO_LAUNCH_CHECK();
+  }
+  if (d_zp_out) {
+    k_scatter<float><<<4 * nsm, 256, 0, st>>>(w.zbuf, w.pix, p.n_valid, nc, p.chan0[c], p.npix, d_zp_out);
+    OVRO_LAUNCH_CHECK();
+  }
+  {
+    const size_t sm = static_cast<size_t>(kMaxLo + nc + kMaxHi + kVox) * 4 + static_cast<size_t>(n_bins) * 4;
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    // CTAs per SM; trial launches histogram into scratch (the real histogram
+    // accumulates over coarse channels and must count every voxel once)
+    auto mf = [&](int per_sm, unsigned long long* hist) -> int {
+      const int blocks = std::min(p.n_valid, per_sm * nsm);
       OVRO_PROF("k_mf", st);
       k_mf<<<blocks, 128, sm, st>>>(w.zbuf, p.n_valid, nc, w.snr + p.vox0[c], w.width + p.vox0[c],
-                                    hist_key0, n_bins, w.hist);
+                                    hist_key0, n_bins, hist);
       OVRO_LAUNCH_CHECK();
+      return OVRO_OK;
+    };
+    const std::string key = tune_key("k_mf", {p.n_valid, nc});
+    int per_sm = tuned(key, 24);
+    if (tuning(st)) {
+      unsigned long long* scratch = reinterpret_cast<unsigned long long*>(w.vals);
+      if (int e = tune_pick(key, {6, 12, 24, 48}, [&](int v) { return mf(v, scratch); }, st, &per_sm)) return e;
     }
+    if (int e = mf(per_sm, w.hist)) return e;
   }
   return OVRO_OK;
+}
+
+int run_filter(const float* d_img, const DetectPlan& p, const DetectWs& w, uint32_t hist_key0, int n_bins,
+               float* d_zp_out, cudaStream_t st) {
+  for (int c = 0; c < p.n_coarse; ++c)
+    if (int e = run_filter_coarse(c, d_img + static_cast<long long>(p.chan0[c]) * p.npix, p, w, hist_key0, n_bins,
+                                  d_zp_out, st))
+      return e;
+  return OVRO_OK;
+}
+
+// Device address of the detection status word (per device).
+int* detect_status_ptr() {
+  static int* cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cache[dev]) {
+    void* q = nullptr;
+    if (cudaGetSymbolAddress(&q, g_detect_status) != cudaSuccess) return nullptr;
+    cache[dev] = static_cast<int*>(q);
+  }
+  return cache[dev];
 }
 
 uint32_t host_f2key(float f) {
@@ -1145,7 +1191,7 @@ int ovro_detect_stats(const float* d_img, int n_chan, int image_size, double cel
   if (int e = check_workspace(d_ws, ws_bytes, need)) return e;
   cudaStream_t st = as_stream(stream);
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.pix, p.pix.data(), p.pix.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  if (int e = run_stats(d_img, p, w, st)) return e;
+  if (int e = run_stats_block(d_img, n_chan, w.stats64, w.stats32, p, w, st)) return e;
   OVRO_CUDA_TRY(cudaMemcpyAsync(d_stats, w.stats64, 2 * sizeof(double) * n_chan, cudaMemcpyDeviceToDevice, st));
   return OVRO_OK;
 }
@@ -1191,36 +1237,97 @@ int ovro_detect_filter(const float* d_img, const double* d_stats, int n_chan, in
   return OVRO_OK;
 }
 
-int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dircos, int n_coarse,
-                const int32_t* h_nfft, const double* h_chan_freq_hz, const ovro_detect_params* params,
-                ovro_candidate* h_out, int max_out, int* n_out, void* d_ws, size_t ws_bytes,
-                void* stream) {
-  using namespace ovro;
-  if (!d_img || !params || !n_out || (max_out > 0 && !h_out) || max_out < 0 || !h_chan_freq_hz)
-    return OVRO_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace ovro {
+
+struct DetectCtx {
+  DetectPlan p;
+  DetectWs w;
+  ovro_detect_params prm;
+  uint32_t key0 = 0;
+  int nb = 0;
+  int n_chan = 0, image_size = 0;
+};
+
+size_t detect_ctx_workspace(int n_chan, int image_size, int n_coarse, const int32_t* h_nfft) {
+  // the in-horizon pixel count depends on the cell; size for the largest (all pixels)
+  if (validate(n_chan, image_size, 1.0, n_coarse, h_nfft) != OVRO_OK) return 0;
+  DetectPlan p = make_plan(n_chan, image_size, 1e-9, n_coarse, h_nfft, 24000.0, 5000.0);
+  size_t need = 0;
+  carve_detect(nullptr, 0, p, &need);
+  return need;
+}
+
+int detect_ctx_init(DetectCtx** out, int n_chan, int image_size, double cell, int n_coarse, const int32_t* h_nfft,
+                    const ovro_detect_params* params, void* d_ws, size_t ws_bytes) {
+  if (!out || !params) return OVRO_ERR_INVALID_ARG;
+  *out = nullptr;
   if (params->mode != OVRO_DETECT_BH && params->mode != OVRO_DETECT_FIXED) return OVRO_ERR_INVALID_ARG;
   if (params->mode == OVRO_DETECT_BH && !(params->alpha > 0.0 && params->alpha <= 0.4))
     return OVRO_ERR_INVALID_ARG;
   if (!(params->highpass_hz > 0.0) || !(params->coarse_bw_hz > 0.0)) return OVRO_ERR_INVALID_ARG;
-  if (int e = validate(n_chan, image_size, cell_dircos, n_coarse, h_nfft)) return e;
-  DetectPlan p = make_plan(n_chan, image_size, cell_dircos, n_coarse, h_nfft, params->coarse_bw_hz,
-                           params->highpass_hz);
-  *n_out = 0;
-  if (p.n_valid == 0) return OVRO_OK;
+  if (int e = validate(n_chan, image_size, cell, n_coarse, h_nfft)) return e;
+  DetectCtx* d = new DetectCtx;
+  d->p = make_plan(n_chan, image_size, cell, n_coarse, h_nfft, params->coarse_bw_hz, params->highpass_hz);
   size_t need = 0;
-  DetectWs w = carve_detect(d_ws, ws_bytes, p, &need);
-  if (int e = check_workspace(d_ws, ws_bytes, need)) return e;
-  cudaStream_t st = as_stream(stream);
-  int zero = 0;
-  OVRO_CUDA_TRY(cudaMemcpyToSymbolAsync(g_detect_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
-  OVRO_CUDA_TRY(cudaMemcpyAsync(w.pix, p.pix.data(), p.pix.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  if (int e = run_stats(d_img, p, w, st)) return e;
-  uint32_t key0;
-  int nb;
-  hist_range(*params, &key0, &nb);
-  OVRO_CUDA_TRY(cudaMemsetAsync(w.hist, 0, kMaxBins * sizeof(unsigned long long), st));
-  if (int e = run_filter(d_img, p, w, key0, nb, nullptr, st)) return e;
+  d->w = carve_detect(d_ws, ws_bytes, d->p, &need);
+  if (d->p.n_valid > 0)
+    if (int e = check_workspace(d_ws, ws_bytes, need)) {
+      delete d;
+      return e;
+    }
+  d->prm = *params;
+  hist_range(*params, &d->key0, &d->nb);
+  d->n_chan = n_chan;
+  d->image_size = image_size;
+  *out = d;
+  return OVRO_OK;
+}
 
+int detect_ctx_valid_pixels(const DetectCtx* d) { return d ? d->p.n_valid : 0; }
+
+int detect_ctx_upload(DetectCtx* d, cudaStream_t st) {
+  if (!d) return OVRO_ERR_INVALID_ARG;
+  const DetectPlan& p = d->p;
+  if (p.n_valid == 0) return OVRO_OK;
+  OVRO_CUDA_TRY(cudaMemcpyAsync(d->w.pix, p.pix.data(), p.pix.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  OVRO_CUDA_TRY(cudaMemcpyAsync(d->w.vox0, p.vox0.data(), p.n_coarse * sizeof(long long), cudaMemcpyHostToDevice, st));
+  OVRO_CUDA_TRY(cudaMemcpyAsync(d->w.nfft, p.nfft.data(), p.n_coarse * sizeof(int), cudaMemcpyHostToDevice, st));
+  return OVRO_OK;
+}
+
+int detect_ctx_begin(DetectCtx* d, cudaStream_t st) {
+  if (!d) return OVRO_ERR_INVALID_ARG;
+  if (d->p.n_valid == 0) return OVRO_OK;
+  int* sp = detect_status_ptr();
+  if (!sp) return OVRO_ERR_CUDA;
+  OVRO_CUDA_TRY(cudaMemsetAsync(sp, 0, sizeof(int), st));
+  OVRO_CUDA_TRY(cudaMemsetAsync(d->w.hist, 0, kMaxBins * sizeof(unsigned long long), st));
+  return OVRO_OK;
+}
+
+int detect_ctx_coarse(DetectCtx* d, int c, const float* d_img_block, cudaStream_t st) {
+  if (!d || !d_img_block || c < 0 || c >= d->p.n_coarse) return OVRO_ERR_INVALID_ARG;
+  const DetectPlan& p = d->p;
+  if (p.n_valid == 0) return OVRO_OK;
+  const long long off = 2LL * p.chan0[c];
+  if (int e = run_stats_block(d_img_block, p.nfft[c], d->w.stats64 + off, d->w.stats32 + off, p, d->w, st))
+    return e;
+  return run_filter_coarse(c, d_img_block, p, d->w, d->key0, d->nb, nullptr, st);
+}
+
+int detect_ctx_finish(DetectCtx* d, const double* h_chan_freq_hz, ovro_candidate* h_out, int max_out, int* n_out,
+                      cudaStream_t st) {
+  if (!d || !n_out || (max_out > 0 && !h_out) || max_out < 0 || !h_chan_freq_hz) return OVRO_ERR_INVALID_ARG;
+  *n_out = 0;
+  const DetectPlan& p = d->p;
+  if (p.n_valid == 0) return OVRO_OK;
+  const DetectWs& w = d->w;
+  const ovro_detect_params& prm = d->prm;
+  const uint32_t key0 = d->key0;
+  const int nb = d->nb;
+  const int n_chan = d->n_chan, image_size = d->image_size;
   // ---- a11: threshold
   std::vector<unsigned long long> hist(nb);
   OVRO_CUDA_TRY(cudaMemcpyAsync(hist.data(), w.hist, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -1231,18 +1338,16 @@ int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dirc
   const double m = static_cast<double>(p.n_valid) * n_chan;
   const int nsm = num_sms();
   float cut;
-  if (params->mode == OVRO_DETECT_FIXED) {
-    cut = static_cast<float>(params->nsigma);
+  if (prm.mode == OVRO_DETECT_FIXED) {
+    cut = static_cast<float>(prm.nsigma);
   } else {
-    int e = bh_cut(hist, key0, nb, m, params->alpha, w, p, st, nsm, &cut);
+    int e = bh_cut(hist, key0, nb, m, prm.alpha, w, p, st, nsm, &cut);
     if (e == 1) return OVRO_OK;        // nothing is rejected
     if (e) return e;
   }
   // ---- a12: NMS on the device, candidates in (pixel, coarse, channel) order
   const long long np = n_pairs_of(p);
   if (np > 0x7fffffffLL / 2) return OVRO_ERR_UNSUPPORTED;
-  OVRO_CUDA_TRY(cudaMemcpyAsync(w.vox0, p.vox0.data(), p.n_coarse * sizeof(long long), cudaMemcpyHostToDevice, st));
-  OVRO_CUDA_TRY(cudaMemcpyAsync(w.nfft, p.nfft.data(), p.n_coarse * sizeof(int), cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, 4 * sizeof(int), st));
   const unsigned nms_blocks = static_cast<unsigned>((np + kNmsWarps - 1) / kNmsWarps);
   {
@@ -1309,6 +1414,33 @@ int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dirc
   }
   if (total > max_out) return OVRO_ERR_CAPACITY;
   return total > kCandCap ? OVRO_ERR_CAPACITY : OVRO_OK;
+}
+
+void detect_ctx_free(DetectCtx* d) { delete d; }
+
+}  // namespace ovro
+
+extern "C" {
+
+int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dircos, int n_coarse,
+                const int32_t* h_nfft, const double* h_chan_freq_hz, const ovro_detect_params* params,
+                ovro_candidate* h_out, int max_out, int* n_out, void* d_ws, size_t ws_bytes,
+                void* stream) {
+  using namespace ovro;
+  if (!d_img || !params || !n_out || (max_out > 0 && !h_out) || max_out < 0 || !h_chan_freq_hz)
+    return OVRO_ERR_INVALID_ARG;
+  *n_out = 0;
+  DetectCtx* d = nullptr;
+  if (int e = detect_ctx_init(&d, n_chan, image_size, cell_dircos, n_coarse, h_nfft, params, d_ws, ws_bytes))
+    return e;
+  cudaStream_t st = as_stream(stream);
+  int e = detect_ctx_upload(d, st);
+  if (!e) e = detect_ctx_begin(d, st);
+  for (int c = 0; c < n_coarse && !e; ++c)
+    e = detect_ctx_coarse(d, c, d_img + static_cast<long long>(d->p.chan0[c]) * d->p.npix, st);
+  if (!e) e = detect_ctx_finish(d, h_chan_freq_hz, h_out, max_out, n_out, st);
+  detect_ctx_free(d);
+  return e;
 }
 
 }  // extern "C"

@@ -31,11 +31,14 @@
 //      intermediate half-transformed grids L2-sized.
 #include <algorithm>
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
 #include "fft.cuh"
 #include "pswf.h"
+#include "stages.h"
+#include "tune.h"
 
 namespace ovro {
 namespace {
@@ -575,19 +578,87 @@ int validate(int n_ant, const double* h_ant, const double* h_freq, int n_chan, i
 }
 
 }  // namespace
+
+struct GridCtx {
+  ImgPlan p;
+  ImgWs w;
+  int n_ant = 0, n_chan = 0;
+  double cell = 0.0;
+};
+
+size_t grid_ctx_workspace(int n_ant, int n_chan, int image_size) {
+  if (n_ant <= 0 || n_chan <= 0 || !is_pow2(image_size) || image_size < 16 || image_size > 1024) return 0;
+  const ImgPlan p = make_plan(n_ant, n_chan, image_size);
+  size_t need = 0;
+  carve_img(nullptr, 0, p, n_ant, n_chan, &need);
+  return need;
+}
+
+int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double cell, void* d_ws, size_t ws_bytes) {
+  if (!out) return OVRO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n_ant <= 0 || n_chan <= 0 || !(cell > 0.0)) return OVRO_ERR_INVALID_ARG;
+  if (!is_pow2(image_size) || image_size < 16 || image_size > 1024 || n_ant > 4096) return OVRO_ERR_UNSUPPORTED;
+  GridCtx* g = new GridCtx;
+  g->p = make_plan(n_ant, n_chan, image_size);
+  size_t need = 0;
+  g->w = carve_img(d_ws, ws_bytes, g->p, n_ant, n_chan, &need);
+  if (int e = check_workspace(d_ws, ws_bytes, need)) {
+    delete g;
+    return e;
+  }
+  g->n_ant = n_ant;
+  g->n_chan = n_chan;
+  g->cell = cell;
+  *out = g;
+  return OVRO_OK;
+}
+
+int grid_ctx_upload(GridCtx* g, const double* h_ant_enu_m, const double* h_chan_freq_hz, cudaStream_t st) {
+  if (!g) return OVRO_ERR_INVALID_ARG;
+  if (int e = validate(g->n_ant, h_ant_enu_m, h_chan_freq_hz, g->n_chan, g->p.n, g->cell)) return e;
+  return upload_common(g->p, g->w, g->n_ant, h_ant_enu_m, h_chan_freq_hz, g->n_chan, g->cell, st);
+}
+
+int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_counts_or_null, cudaStream_t st) {
+  if (!g || !d_vis || !d_img) return OVRO_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_vis) % 16 != 0) return OVRO_ERR_INVALID_ARG;
+  const ImgPlan& p = g->p;
+  const long long n_bl = static_cast<long long>(g->n_ant) * (g->n_ant + 1) / 2;
+  // channels per launch pair (at most the workspace's batch): every choice
+  // gives the same images and counts
+  auto all = [&](int batch) -> int {
+    OVRO_CUDA_TRY(cudaMemsetAsync(g->w.kept, 0, g->n_chan * sizeof(int), st));
+    for (int ch0 = 0; ch0 < g->n_chan; ch0 += batch) {
+      const int nb = g->n_chan - ch0 < batch ? g->n_chan - ch0 : batch;
+      if (int e = run_bands(p, g->w, d_vis, n_bl, ch0, nb, d_img, st)) return e;
+    }
+    return OVRO_OK;
+  };
+  const std::string key = tune_key("grid_batch", {g->n_ant, g->n_chan, p.n});
+  int batch = std::min(p.batch, std::max(1, tuned(key, p.batch)));
+  if (tuning(st)) {
+    std::vector<int> cands;
+    for (int b = p.batch; b >= 1 && cands.size() < 4; b /= 2) cands.push_back(b);
+    if (int e = tune_pick(key, cands, all, st, &batch)) return e;
+  }
+  if (int e = all(batch)) return e;
+  if (d_counts_or_null) {
+    k_counts_out<<<(g->n_chan + 255) / 256, 256, 0, st>>>(g->w.kept, g->n_chan, d_counts_or_null);
+    OVRO_LAUNCH_CHECK();
+  }
+  return OVRO_OK;
+}
+
+void grid_ctx_free(GridCtx* g) { delete g; }
+
 }  // namespace ovro
 
 extern "C" {
 
 size_t ovro_grid_image_workspace_size(int n_ant, int n_chan, int image_size, int storage) {
-  using namespace ovro;
-  if (n_ant <= 0 || n_chan <= 0 || !is_pow2(image_size) || image_size < 16 || image_size > 1024)
-    return 0;
   (void)storage;
-  const ImgPlan p = make_plan(n_ant, n_chan, image_size);
-  size_t need = 0;
-  carve_img(nullptr, 0, p, n_ant, n_chan, &need);
-  return need;
+  return ovro::grid_ctx_workspace(n_ant, n_chan, image_size);
 }
 
 int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
@@ -601,23 +672,13 @@ int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
     return OVRO_ERR_INVALID_ARG;
   if (storage != OVRO_STORE_FP32) return OVRO_ERR_UNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(d_vis) % 16 != 0) return OVRO_ERR_INVALID_ARG;
-  const ImgPlan p = make_plan(n_ant, n_chan, image_size);
-  size_t need = 0;
-  ImgWs w = carve_img(d_ws, ws_bytes, p, n_ant, n_chan, &need);
-  if (int e = check_workspace(d_ws, ws_bytes, need)) return e;
+  GridCtx* g = nullptr;
+  if (int e = grid_ctx_init(&g, n_ant, n_chan, image_size, cell_dircos, d_ws, ws_bytes)) return e;
   cudaStream_t st = as_stream(stream);
-  if (int e = upload_common(p, w, n_ant, h_ant_enu_m, h_chan_freq_hz, n_chan, cell_dircos, st)) return e;
-  OVRO_CUDA_TRY(cudaMemsetAsync(w.kept, 0, n_chan * sizeof(int), st));
-  const long long n_bl = static_cast<long long>(n_ant) * (n_ant + 1) / 2;
-  for (int ch0 = 0; ch0 < n_chan; ch0 += p.batch) {
-    const int nb = n_chan - ch0 < p.batch ? n_chan - ch0 : p.batch;
-    if (int e = run_bands(p, w, d_vis, n_bl, ch0, nb, d_img, st)) return e;
-  }
-  if (d_n_gridded_or_null) {
-    k_counts_out<<<(n_chan + 255) / 256, 256, 0, st>>>(w.kept, n_chan, d_n_gridded_or_null);
-    OVRO_LAUNCH_CHECK();
-  }
-  return OVRO_OK;
+  int e = grid_ctx_upload(g, h_ant_enu_m, h_chan_freq_hz, st);
+  if (!e) e = grid_ctx_enqueue(g, d_vis, d_img, d_n_gridded_or_null, st);
+  grid_ctx_free(g);
+  return e;
 }
 
 // a5 alone: rounded uv positions p = rint(u Q), Q = 1024, of every cross

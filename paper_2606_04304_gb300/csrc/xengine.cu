@@ -23,6 +23,8 @@
 #include <cuda_fp16.h>
 
 #include "common.cuh"
+#include "stages.h"
+#include "tune.h"
 
 namespace ovro {
 namespace {
@@ -304,18 +306,36 @@ k_xeng_tc(const int8_t* __restrict__ q, int n_ant, int n_spec, int n_tiles, int 
 }  // namespace
 }  // namespace ovro
 
-extern "C" {
+namespace ovro {
 
-int ovro_correlate(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec, int mode,
-                   int32_t* d_vis, void* stream) {
-  using namespace ovro;
+// Device address of the timeout word (per device), for stream-ordered memsets.
+int* xeng_status_ptr() {
+  static int* cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cache[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_xeng_status) != cudaSuccess) return nullptr;
+    cache[dev] = static_cast<int*>(p);
+  }
+  return cache[dev];
+}
+
+int correlate_reset_status(cudaStream_t st) {
+  int* p = xeng_status_ptr();
+  if (!p) return OVRO_ERR_CUDA;
+  OVRO_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(int), st));
+  return OVRO_OK;
+}
+
+int correlate_enqueue(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec, int mode, int32_t* d_vis,
+                      cudaStream_t st, bool reset_status) {
   if (!d_fine_q || !d_vis || n_ant <= 0 || n_chan <= 0 || n_spec <= 0) return OVRO_ERR_INVALID_ARG;
   if (mode != OVRO_XENG_TC && mode != OVRO_XENG_FP32) return OVRO_ERR_INVALID_ARG;
   if (n_ant > 4096) return OVRO_ERR_UNSUPPORTED;
   if (2LL * 127 * 127 * n_spec >= (1LL << 24)) return OVRO_ERR_OVERFLOW;
   if (reinterpret_cast<uintptr_t>(d_vis) % 16 != 0 || reinterpret_cast<uintptr_t>(d_fine_q) % 2 != 0)
     return OVRO_ERR_INVALID_ARG;
-  cudaStream_t st = as_stream(stream);
   const int n_input = 2 * n_ant;
   if (mode == OVRO_XENG_FP32) {
     const int n_tiles = (n_input + kSimtTile - 1) / kSimtTile;
@@ -325,22 +345,38 @@ int ovro_correlate(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec, in
     OVRO_LAUNCH_CHECK();
     return OVRO_OK;
   }
-  int zero = 0;
-  OVRO_CUDA_TRY(cudaMemcpyToSymbolAsync(g_xeng_status, &zero, sizeof(int), 0,
-                                        cudaMemcpyHostToDevice, st));
+  if (reset_status)
+    if (int e = correlate_reset_status(st)) return e;
   const int n_tiles = (n_input + kTcM - 1) / kTcM;
   const int n_pairs = n_tiles * (n_tiles + 1) / 2;
   const long long n_items = static_cast<long long>(n_pairs) * n_chan;
   // 96 KB of dynamic shared memory keeps at most two CTAs (2 x 256 TMEM columns) per SM
   const int smem = 96 * 1024;
   OVRO_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  long long grid = 2LL * num_sms();
-  if (grid > n_items) grid = n_items;
-  OVRO_PROF("k_xeng_tc", st);
-  k_xeng_tc<<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(d_fine_q, n_ant, n_spec, n_tiles,
-                                                                  n_pairs, n_items, d_vis);
-  OVRO_LAUNCH_CHECK();
-  return OVRO_OK;
+  // persistent CTAs per SM (one or two fit: 256 TMEM columns each)
+  auto run = [&](int per_sm) -> int {
+    long long grid = static_cast<long long>(per_sm) * num_sms();
+    if (grid > n_items) grid = n_items;
+    OVRO_PROF("k_xeng_tc", st);
+    k_xeng_tc<<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(d_fine_q, n_ant, n_spec, n_tiles,
+                                                                    n_pairs, n_items, d_vis);
+    OVRO_LAUNCH_CHECK();
+    return OVRO_OK;
+  };
+  const std::string key = tune_key("k_xeng_tc", {n_ant, n_chan, n_spec});
+  int per_sm = tuned(key, 2);
+  if (tuning(st))
+    if (int e = tune_pick(key, {1, 2}, run, st, &per_sm)) return e;
+  return run(per_sm);
+}
+
+}  // namespace ovro
+
+extern "C" {
+
+int ovro_correlate(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec, int mode,
+                   int32_t* d_vis, void* stream) {
+  return ovro::correlate_enqueue(d_fine_q, n_ant, n_chan, n_spec, mode, d_vis, ovro::as_stream(stream), true);
 }
 
 // Device status of the last tensor-core correlation (nonzero: a bounded wait timed out).

@@ -79,6 +79,20 @@ def _load() -> ctypes.CDLL:
         "ovro_scorer_grad": (I, [P, I, P, P, I, P, P, P, S, P]),
         "ovro_scorer_adam": (I, [P, P, P, P, I, ctypes.c_float, P, P]),
         "ovro_scorer_to_bf16": (I, [P, P, P]),
+        "ovro_pipeline_create": (I, [P, P]),
+        "ovro_pipeline_workspace_size": (S, [P]),
+        "ovro_pipeline_bind": (I, [P, P, S, P]),
+        "ovro_pipeline_run": (I, [P, P, P, I, P, P]),
+        "ovro_pipeline_channels": (I, [P, P]),
+        "ovro_pipeline_stats": (I, [P, P, P]),
+        "ovro_pipeline_destroy": (None, [P]),
+        "ovro_autotune": (I, [I]),
+        "ovro_tune_get": (I, [ctypes.c_char_p, P]),
+        "ovro_tune_set": (I, [ctypes.c_char_p, I]),
+        "ovro_tune_count": (I, []),
+        "ovro_tune_clear": (I, []),
+        "ovro_tune_save": (I, [ctypes.c_char_p]),
+        "ovro_tune_load": (I, [ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -351,3 +365,94 @@ def scorer_adam(master: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: to
 
 def scorer_to_bf16(master: torch.Tensor, w_bf16: torch.Tensor, stream=None):
     _check("ovro_scorer_to_bf16", _lib.ovro_scorer_to_bf16(_ptr(master), _ptr(w_bf16), _stream(stream)))
+
+
+# ---------------------------------------------------------------------- a14
+class PipelineConfig(ctypes.Structure):
+    _fields_ = [("n_ant", ctypes.c_int), ("n_coarse", ctypes.c_int), ("h_nfft", ctypes.c_void_p),
+                ("h_coarse_hz", ctypes.c_void_p), ("n_time", ctypes.c_int64), ("h_ant_enu_m", ctypes.c_void_p),
+                ("image_size", ctypes.c_int), ("cell_dircos", ctypes.c_double), ("xeng_mode", ctypes.c_int),
+                ("detect", DetectParams), ("use_graph", ctypes.c_int)]
+
+
+class Pipeline:
+    """Batched driver (ovro_pipeline_*): streams the coarse channels of an
+    integration through fixed buffers and returns the candidates of the whole
+    integration.  Owns its device workspace (a torch tensor)."""
+
+    def __init__(self, n_ant: int, nfft: Sequence[int], coarse_hz: Sequence[float], n_time: int, ant_enu_m,
+                 image_size: int, cell: float, xeng_mode: int = XENG_TC, params: Optional[DetectParams] = None,
+                 use_graph: bool = True, device=None, stream=None):
+        self._nf = _host(nfft, np.int32)
+        self._hz = _host(coarse_hz, np.float64)
+        self._ant = _host(ant_enu_m, np.float64).reshape(-1, 3)
+        if self._hz.size != self._nf.size or self._ant.shape[0] != n_ant:
+            raise ValueError("nfft / coarse_hz / ant_enu_m sizes disagree")
+        cfg = PipelineConfig(n_ant, self._nf.size, self._nf.ctypes.data, self._hz.ctypes.data, int(n_time),
+                             self._ant.ctypes.data, image_size, float(cell), xeng_mode, params or detect_params(),
+                             1 if use_graph else 0)
+        h = ctypes.c_void_p()
+        _check("ovro_pipeline_create", _lib.ovro_pipeline_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.n_time, self.n_input, self.n_coarse = int(n_time), 2 * n_ant, int(self._nf.size)
+        self.ws = workspace(_lib.ovro_pipeline_workspace_size(h), device)
+        _check("ovro_pipeline_bind", _lib.ovro_pipeline_bind(h, _ptr(self.ws), self.ws.numel(), _stream(stream)))
+
+    def channels(self) -> np.ndarray:
+        n = _lib.ovro_pipeline_channels(self._h, None)
+        f = np.zeros(n, np.float64)
+        _lib.ovro_pipeline_channels(self._h, f.ctypes.data_as(ctypes.c_void_p))
+        return f
+
+    def run(self, volt: torch.Tensor, max_out: int = 1 << 20, stream=None) -> np.ndarray:
+        _cuda(volt, torch.uint8, "volt")
+        if volt.numel() != self.n_coarse * self.n_time * self.n_input:
+            raise ValueError("volt must be [n_coarse][n_time][2 n_ant] uint8")
+        out = np.zeros(max_out, CANDIDATE_DTYPE)
+        n_out = ctypes.c_int(0)
+        _check("ovro_pipeline_run", _lib.ovro_pipeline_run(self._h, _ptr(volt), out.ctypes.data_as(ctypes.c_void_p),
+                                                           max_out, ctypes.byref(n_out), _stream(stream)))
+        return out[: n_out.value]
+
+    def stats(self):
+        k = ctypes.c_longlong(0)
+        g = ctypes.c_int(0)
+        _check("ovro_pipeline_stats", _lib.ovro_pipeline_stats(self._h, ctypes.byref(k), ctypes.byref(g)))
+        return int(k.value), bool(g.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ovro_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def autotune(enable: bool) -> None:
+    _check("ovro_autotune", _lib.ovro_autotune(1 if enable else 0))
+
+
+def tune_get(key: str) -> Optional[int]:
+    v = ctypes.c_int(0)
+    return int(v.value) if _lib.ovro_tune_get(key.encode(), ctypes.byref(v)) == OVRO_OK else None
+
+
+def tune_set(key: str, value: int) -> None:
+    _check("ovro_tune_set", _lib.ovro_tune_set(key.encode(), int(value)))
+
+
+def tune_count() -> int:
+    return int(_lib.ovro_tune_count())
+
+
+def tune_clear() -> None:
+    _check("ovro_tune_clear", _lib.ovro_tune_clear())
+
+
+def tune_save(path: str) -> None:
+    _check("ovro_tune_save", _lib.ovro_tune_save(os.fspath(path).encode()))
+
+
+def tune_load(path: str) -> None:
+    _check("ovro_tune_load", _lib.ovro_tune_load(os.fspath(path).encode()))

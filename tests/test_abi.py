@@ -59,3 +59,68 @@ def test_host_validation_without_gpu(ov):
 def test_default_widths(ov):
     from oracle.detect import WIDTHS
     assert ov.default_widths().tolist() == list(WIDTHS)
+
+
+def _pipeline_cfg(ov, nfft, n_ant=8, **kw):
+    import numpy as np
+    keep = dict(nf=np.asarray(nfft, np.int32), hz=60e6 + 24e3 * np.arange(len(nfft), dtype=np.float64),
+                ant=np.zeros((n_ant, 3)))
+    cfg = ov.PipelineConfig(n_ant, len(nfft), keep["nf"].ctypes.data, keep["hz"].ctypes.data, kw.get("n_time", 4096),
+                            keep["ant"].ctypes.data, kw.get("image_size", 32), kw.get("cell", 2.0 / 32),
+                            kw.get("xeng", ov.XENG_TC), ov.detect_params(), 1)
+    return cfg, keep
+
+
+def test_pipeline_host_planning(ov):
+    import numpy as np
+    import synth
+    lib = ov.lib()
+    cfg, keep = _pipeline_cfg(ov, [256, 64, 1024])
+    h = ctypes.c_void_p()
+    assert lib.ovro_pipeline_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    try:
+        assert lib.ovro_pipeline_workspace_size(h) > 0
+        n = lib.ovro_pipeline_channels(h, None)
+        assert n == 256 + 64 + 1024
+        f = np.zeros(n)
+        lib.ovro_pipeline_channels(h, f.ctypes.data_as(ctypes.c_void_p))
+        # fine channel k of coarse c at nu_c + (k - N/2) f_c / N, as the synthetic generator
+        assert np.array_equal(f, synth.fine_freqs_hz([256, 64, 1024]))
+        out, n_out = (ov.Candidate * 1)(), ctypes.c_int(7)
+        # not bound: refused before any device access
+        assert lib.ovro_pipeline_run(h, ctypes.c_void_p(16), out, 1, ctypes.byref(n_out), None) == -5
+        assert n_out.value == 0
+        k, g = ctypes.c_longlong(-1), ctypes.c_int(-1)
+        assert lib.ovro_pipeline_stats(h, ctypes.byref(k), ctypes.byref(g)) == 0 and g.value == 0
+    finally:
+        lib.ovro_pipeline_destroy(h)
+
+
+def test_pipeline_rejects_bad_configs(ov):
+    lib = ov.lib()
+    h = ctypes.c_void_p()
+    assert lib.ovro_pipeline_create(None, ctypes.byref(h)) == -1
+    for kw, nfft, want in ((dict(n_time=100), [256], -1),       # fewer samples than one spectrum
+                           (dict(xeng=7), [256], -1),
+                           (dict(cell=0.0), [256], -1),
+                           (dict(image_size=48), [256], -2),   # not a power of two
+                           (dict(), [0], -1)):
+        cfg, keep = _pipeline_cfg(ov, nfft, **kw)
+        assert lib.ovro_pipeline_create(ctypes.byref(cfg), ctypes.byref(h)) == want, (kw, nfft)
+
+
+def test_tuner_cache_roundtrip(ov, tmp_path):
+    ov.tune_clear()
+    assert ov.tune_count() == 0 and ov.tune_get("k_rank/sm152/1/2") is None
+    ov.tune_set("k_rank/sm152/1/2", 4)
+    ov.tune_set("grid_batch/sm152/352/8192/256", 16)
+    p = tmp_path / "tune.txt"
+    ov.tune_save(p)
+    ov.tune_clear()
+    ov.tune_load(p)
+    assert ov.tune_count() == 2
+    assert ov.tune_get("k_rank/sm152/1/2") == 4 and ov.tune_get("grid_batch/sm152/352/8192/256") == 16
+    (tmp_path / "bad.txt").write_text("k 1 2 x\nk2 notanumber\n")
+    with pytest.raises(ov.OvroError):
+        ov.tune_load(tmp_path / "bad.txt")
+    ov.tune_clear()

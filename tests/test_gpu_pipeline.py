@@ -1,0 +1,117 @@
+"""GPU: the batched pipeline (a14) on a mixed-N_fft integration against the
+stage-by-stage public calls and the oracle's search, CUDA-graph replay and the
+autotuner."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import detect as OD, imaging as OI
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed():
+    # the batched recipe (mixed fine-channel counts per coarse channel, seeded
+    # tones) at a size the oracle's search finishes in seconds
+    return synth.make_config("batched", n_ant=16, n_coarse=4, nfft=[256, 1024, 64, 512], n_time=16384,
+                             image_size=32, core_ant=16, core_radius_m=30.0, n_tones=4)
+
+
+@pytest.fixture(scope="module")
+def case(lib):
+    cfg = _mixed()
+    volt = torch.from_numpy(synth.generate(cfg)).cuda()
+    pos = synth.antenna_positions(cfg)
+    freqs = synth.fine_freqs_hz(cfg.nfft)
+    q, _ = lib.upchan(volt, cfg.nfft)
+    vis = torch.empty((cfg.n_chan_total, lib.n_baselines(cfg.n_ant), 4, 2), dtype=torch.int32, device="cuda")
+    qoff = c0 = 0
+    for n, k in zip(cfg.nfft, cfg.n_spec):
+        m = n * k * cfg.n_input * 2
+        lib.correlate(q[qoff:qoff + m], cfg.n_ant, n, k, lib.XENG_TC, out=vis[c0:c0 + n])
+        qoff += m
+        c0 += n
+    img = lib.grid_image(vis, pos, freqs, cfg.image_size, cfg.cell)
+    ref = lib.detect(img, cfg.cell, cfg.nfft, freqs)
+    return cfg, volt, pos, img, ref
+
+
+def _pipeline(lib, cfg, pos, **kw):
+    centres = [synth.coarse_centre_hz(c) for c in range(cfg.n_coarse)]
+    return lib.Pipeline(cfg.n_ant, cfg.nfft, centres, cfg.n_time, pos, cfg.image_size, cfg.cell, **kw)
+
+
+def _same(a, b):
+    ka = {(int(c["chan"]), int(c["row"]), int(c["col"]), int(c["width"])): float(c["snr"]) for c in a}
+    kb = {(int(c["chan"]), int(c["row"]), int(c["col"]), int(c["width"])): float(c["snr"]) for c in b}
+    assert ka.keys() == kb.keys(), sorted(set(ka) ^ set(kb))[:10]
+    for k in ka:
+        assert abs(ka[k] - kb[k]) < 1e-4 * max(1.0, abs(kb[k])), (k, ka[k], kb[k])
+
+
+def test_pipeline_equals_stagewise_and_oracle(lib, case):
+    cfg, volt, pos, img, ref = case
+    pl = _pipeline(lib, cfg, pos)
+    assert np.array_equal(pl.channels(), synth.fine_freqs_hz(cfg.nfft))
+    got = pl.run(volt)
+    _same(got, ref)
+    # the oracle's search over the same images
+    mask = OI.horizon_mask(cfg.image_size, cfg.cell)
+    oref = OD.detect(img.cpu().numpy().astype(np.float64), mask, cfg.nfft)
+    assert {(int(c["chan"]), int(c["row"]), int(c["col"])) for c in got} == {(c.chan, c.row, c.col) for c in oref}
+    # every injected tone is found at its channel and pixel
+    found = {(int(c["chan"]), int(c["row"]), int(c["col"])) for c in got}
+    chan0 = np.concatenate([[0], np.cumsum(cfg.nfft)])
+    for t in cfg.tones:
+        assert any((chan0[t.coarse] + t.fine + d, t.row, t.col) in found for d in (-1, 0, 1)), t
+
+
+def test_graph_replay(lib, case):
+    cfg, volt, pos, img, ref = case
+    pl = _pipeline(lib, cfg, pos, use_graph=True)
+    first = pl.run(volt)
+    k, live = pl.stats()
+    assert live and k > 4 * cfg.n_coarse
+    l0 = lib.launch_count()
+    again = pl.run(volt)
+    assert lib.launch_count() - l0 == pl.stats()[0] == k   # replayed kernels are counted
+    _same(first, ref)
+    _same(again, ref)
+    # a different voltage buffer is captured anew
+    other = volt.clone()
+    _same(pl.run(other), ref)
+
+
+def test_eager_and_fp32_xengine(lib, case):
+    cfg, volt, pos, img, ref = case
+    pl = _pipeline(lib, cfg, pos, use_graph=False, xeng_mode=lib.XENG_FP32)
+    got = pl.run(volt)
+    _, live = pl.stats()
+    assert not live
+    _same(got, ref)
+
+
+def test_autotune_then_graph(lib, case, tmp_path):
+    cfg, volt, pos, img, ref = case
+    lib.tune_clear()
+    lib.autotune(True)
+    try:
+        pl = _pipeline(lib, cfg, pos, use_graph=True)
+        tuned = pl.run(volt)                      # eager: every site times its candidates
+        _, live = pl.stats()
+        assert not live
+    finally:
+        lib.autotune(False)
+    _same(tuned, ref)
+    # k_xeng_tc once per distinct (channels, spectra); imaging batch, k_rank, k_mf per coarse shape
+    assert lib.tune_count() >= 1 + 3 * len(set(cfg.nfft))
+    path = tmp_path / "tune.txt"
+    lib.tune_save(path)
+    n = lib.tune_count()
+    lib.tune_clear()
+    lib.tune_load(path)
+    assert lib.tune_count() == n
+    again = pl.run(volt)                          # captured with the tuned shapes
+    assert pl.stats()[1]
+    _same(again, ref)
