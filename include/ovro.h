@@ -169,6 +169,13 @@ int ovro_correlate_status(void* stream);
  *                 the horizon).
  * storage         OVRO_STORE_FP32, or OVRO_STORE_BF16 / OVRO_STORE_FP16 to keep
  *                 the intermediate uv grid in 16-bit storage (FP32 arithmetic).
+ *                 The grid lives in shared memory while it is gridded and row
+ *                 transformed; what crosses global memory is the half-transformed
+ *                 grid (G rows x N central columns per channel), and that is what
+ *                 is stored in 16 bits: BF16 as is, FP16 with a power-of-two
+ *                 scale per row (largest component in [2^13, 2^14)).  Measured
+ *                 errors vs the FP64 oracle: BF16 ~3e-3 of the image maximum
+ *                 (L2 ~1.4e-3), FP16 ~4e-4 (L2 ~1.7e-4), FP32 ~2e-7.
  * d_img           float output [n_chan][N][N].
  * d_n_gridded_or_null  optional int32 [n_chan]: gridded visibilities per
  *                 channel (mirrors included).

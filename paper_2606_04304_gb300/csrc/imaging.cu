@@ -34,6 +34,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "pswf.h"
@@ -49,6 +52,8 @@ constexpr int kHalfTab = kSupport * kOversample / 2;
 constexpr int kTabLen = 2 * kHalfTab + 1;
 constexpr int kHalfSup = kSupport / 2;
 constexpr int kPad = 2;              // uv grid cells per image pixel, per axis
+// storage of the half-transformed grid between the row and column passes
+constexpr int kStoreF32 = OVRO_STORE_FP32, kStoreBF16 = OVRO_STORE_BF16, kStoreF16 = OVRO_STORE_FP16;
 
 struct Baseline {
   double dx, dy;
@@ -174,13 +179,13 @@ __host__ __device__ constexpr int planar_pitch(int g) { return g + 4; }
 // band is held as two real planes during gridding (every atomic of a warp hits
 // its own bank) and in the interleaved, padded FFT layout afterwards; the
 // first FFT pass converts.
-template <int LOG2G>
+template <int LOG2G, int S>
 __global__ void __launch_bounds__(512)
 k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_off,
             const int32_t* __restrict__ vis, long long n_bl, const Baseline* __restrict__ base,
             const ChanScale* __restrict__ cs, const float* __restrict__ tab,
             const float2* __restrict__ tw_g, int ch0, int n_img, int band_h,
-            int* __restrict__ kept, float2* __restrict__ h) {
+            int* __restrict__ kept, void* __restrict__ h, float* __restrict__ hs) {
   constexpr int G = 1 << LOG2G;
   constexpr int LDP = band_pitch(G);
   constexpr int P = planar_pitch(G);
@@ -305,19 +310,64 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
   __syncthreads();
   if (threadIdx.x == 0 && n_home) atomicAdd(kept + chan, n_home);
   fft_rows_inplace<LOG2G>(band, LDP, tw, pre, pim, P);
-  // central N columns of each transformed row
+  // central N columns of each transformed row, in the storage format
   const int offc = G / 2 - n_img / 2;
-  float2* hb = h + (static_cast<long long>(cb) * G + row0) * n_img;
-  for (int i = threadIdx.x; i < band_h * n_img; i += blockDim.x) {
-    const int r = i / n_img, c = i - r * n_img;
-    hb[static_cast<long long>(r) * n_img + c] = band[r * LDP + pad16(offc + c)];
+  const long long hrow0 = static_cast<long long>(cb) * G + row0;
+  if constexpr (S == kStoreF32) {
+    float2* hb = static_cast<float2*>(h) + hrow0 * n_img;
+    for (int i = threadIdx.x; i < band_h * n_img; i += blockDim.x) {
+      const int r = i / n_img, c = i - r * n_img;
+      hb[static_cast<long long>(r) * n_img + c] = band[r * LDP + pad16(offc + c)];
+    }
+  } else if constexpr (S == kStoreBF16) {
+    __nv_bfloat162* hb = static_cast<__nv_bfloat162*>(h) + hrow0 * n_img;
+    for (int i = threadIdx.x; i < band_h * n_img; i += blockDim.x) {
+      const int r = i / n_img, c = i - r * n_img;
+      hb[static_cast<long long>(r) * n_img + c] = __float22bfloat162_rn(band[r * LDP + pad16(offc + c)]);
+    }
+  } else {
+    // FP16 with a power-of-two scale per row: the row's largest component
+    // lands in [2^13, 2^14), far from FP16 overflow; scaling is exact
+    __half2* hb = static_cast<__half2*>(h) + hrow0 * n_img;
+    const int lane = threadIdx.x & 31, n_w = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < band_h; r += n_w) {
+      float m = 0.f;
+      for (int c = lane; c < n_img; c += 32) {
+        const float2 v = band[r * LDP + pad16(offc + c)];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      int e = 0;
+      if (m > 0.f) frexpf(m, &e);
+      const float sc = m > 0.f ? ldexpf(1.0f, 14 - e) : 1.0f;
+      if (lane == 0) hs[hrow0 + r] = m > 0.f ? ldexpf(1.0f, e - 14) : 0.0f;
+      for (int c = lane; c < n_img; c += 32) {
+        const float2 v = band[r * LDP + pad16(offc + c)];
+        hb[static_cast<long long>(r) * n_img + c] = __float22half2_rn(make_float2(v.x * sc, v.y * sc));
+      }
+    }
+  }
+}
+
+// One complex value of the half-transformed grid in FP32.
+template <int S>
+__device__ __forceinline__ float2 load_h(const void* h, const float* hs, long long row, long long idx) {
+  if constexpr (S == kStoreF32) {
+    return static_cast<const float2*>(h)[idx];
+  } else if constexpr (S == kStoreBF16) {
+    return __bfloat1622float2(static_cast<const __nv_bfloat162*>(h)[idx]);
+  } else {
+    const float2 v = __half22float2(static_cast<const __half2*>(h)[idx]);
+    const float s = hs[row];
+    return make_float2(v.x * s, v.y * s);
   }
 }
 
 // Column transforms of the N central columns and the image itself.
-template <int LOG2G>
-__global__ void __launch_bounds__(512)
-k_fft_cols(const float2* __restrict__ h, int n_img, int cols_per_cta, int ch0,
+template <int LOG2G, int S>
+__global__ void __launch_bounds__(1024)
+k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, int cols_per_cta, int ch0,
            const float2* __restrict__ tw_g, const float* __restrict__ inv_corr,
            const uint8_t* __restrict__ mask, const int* __restrict__ kept, float* __restrict__ img) {
   constexpr int G = 1 << LOG2G;
@@ -328,11 +378,11 @@ k_fft_cols(const float2* __restrict__ h, int n_img, int cols_per_cta, int ch0,
   const int C = cols_per_cta;
   const int cb = blockIdx.y;
   const int c0 = blockIdx.x * C;
-  const float2* hc = h + static_cast<long long>(cb) * G * n_img;
+  const long long hrow0 = static_cast<long long>(cb) * G;
   for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
   for (int i = threadIdx.x; i < G * C; i += blockDim.x) {
     const int r = i / C, c = i - r * C;
-    A[c * LDP + pad16(r)] = hc[static_cast<long long>(r) * n_img + c0 + c];
+    A[c * LDP + pad16(r)] = load_h<S>(h, hs, hrow0 + r, (hrow0 + r) * n_img + c0 + c);
   }
   __syncthreads();
   fft_rows_inplace<LOG2G>(A, LDP, tw);
@@ -377,13 +427,14 @@ __global__ void k_counts_out(const int* __restrict__ kept, int n_chan, int32_t* 
 
 // ---------------------------------------------------------------- planning
 struct ImgPlan {
-  int n, g, log2g, band_h, n_bands, batch, cols_per_cta;
+  int n, g, log2g, band_h, n_bands, batch, cols_per_cta, storage;
   long long n_cross;
 };
 
-ImgPlan make_plan(int n_ant, int n_chan, int n) {
+ImgPlan make_plan(int n_ant, int n_chan, int n, int storage) {
   ImgPlan p;
   p.n = n;
+  p.storage = storage;
   p.g = kPad * n;
   p.log2g = ilog2(p.g);
   p.band_h = 8192 / p.g < p.g ? 8192 / p.g : p.g;    // 8192 complex values per band
@@ -396,6 +447,9 @@ ImgPlan make_plan(int n_ant, int n_chan, int n) {
   if (b > n_chan) b = n_chan;
   p.batch = static_cast<int>(b);
   int c = 8192 / p.g;
+  // 16-bit storage: at least 8 columns per CTA, so each row segment the
+  // column pass reads is a whole 32-byte sector
+  if (storage != kStoreF32 && c < 8 && 8 * p.g / 16 <= 1024) c = 8;
   if (c > n) c = n;
   p.cols_per_cta = c;
   return p;
@@ -413,7 +467,8 @@ struct ImgWs {
   int* kept;
   int* band_off;
   GridEntry* entries;
-  float2* h;
+  void* h;           // [batch][G][N] complex in the storage format
+  float* hs;         // [batch][G] row scales (FP16 storage)
 };
 
 // Candidate entries: each cross baseline once per band it can touch (at most
@@ -438,6 +493,7 @@ ImgWs carve_img(void* ws, size_t bytes, const ImgPlan& p, int n_ant, int n_chan,
   w.band_off = c.take<int>(p.n_bands + 1);
   w.entries = c.take<GridEntry>(entry_capacity(p));
   w.h = c.take<float2>(static_cast<size_t>(p.batch) * p.g * p.n);
+  w.hs = c.take<float>(static_cast<size_t>(p.batch) * p.g);
   *need = c.used;
   return w;
 }
@@ -486,7 +542,7 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
   off[p.n_bands] = static_cast<int>(out.size());
 }
 
-template <int L>
+template <int L, int S>
 int launch_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long n_bl, int ch0, int nb,
                  float* img, cudaStream_t st) {
   constexpr int G = 1 << L;
@@ -494,39 +550,50 @@ int launch_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long
   {
     const size_t sm = static_cast<size_t>(p.band_h) * LDP * sizeof(float2) + G * sizeof(float2) +
                       kRecMax * (sizeof(float4) + kWuStride * sizeof(float2) + kWvStride * sizeof(float));
-    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid_rows<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid_rows<L, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm)));
     const int threads = p.band_h * G / 16;
     dim3 grid(p.n_bands, nb);
     OVRO_PROF("k_grid_rows", st);
-    k_grid_rows<L><<<grid, threads, sm, st>>>(w.entries, w.band_off, vis, n_bl, w.base, w.cs, w.tab, w.tw, ch0,
-                                              p.n, p.band_h, w.kept, w.h);
+    k_grid_rows<L, S><<<grid, threads, sm, st>>>(w.entries, w.band_off, vis, n_bl, w.base, w.cs, w.tab, w.tw, ch0,
+                                                 p.n, p.band_h, w.kept, w.h, w.hs);
     OVRO_LAUNCH_CHECK();
   }
   {
     const size_t sm = static_cast<size_t>(p.cols_per_cta) * LDP * sizeof(float2) + G * sizeof(float2);
-    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<L, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm)));
     const int threads = p.cols_per_cta * G / 16;
     dim3 grid(p.n / p.cols_per_cta, nb);
     OVRO_PROF("k_fft_cols", st);
-    k_fft_cols<L><<<grid, threads, sm, st>>>(w.h, p.n, p.cols_per_cta, ch0, w.tw, w.inv_corr, w.mask, w.kept,
-                                             img);
+    k_fft_cols<L, S><<<grid, threads, sm, st>>>(w.h, w.hs, p.n, p.cols_per_cta, ch0, w.tw, w.inv_corr, w.mask,
+                                                w.kept, img);
     OVRO_LAUNCH_CHECK();
   }
   return OVRO_OK;
 }
 
+template <int L>
+int launch_storage(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long n_bl, int ch0, int nb,
+                   float* img, cudaStream_t st) {
+  switch (p.storage) {
+    case kStoreF32: return launch_bands<L, kStoreF32>(p, w, vis, n_bl, ch0, nb, img, st);
+    case kStoreBF16: return launch_bands<L, kStoreBF16>(p, w, vis, n_bl, ch0, nb, img, st);
+    case kStoreF16: return launch_bands<L, kStoreF16>(p, w, vis, n_bl, ch0, nb, img, st);
+    default: return OVRO_ERR_INVALID_ARG;
+  }
+}
+
 int run_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long n_bl, int ch0, int nb, float* img,
               cudaStream_t st) {
   switch (p.log2g) {
-    case 5: return launch_bands<5>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 6: return launch_bands<6>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 7: return launch_bands<7>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 8: return launch_bands<8>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 9: return launch_bands<9>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 10: return launch_bands<10>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 11: return launch_bands<11>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 5: return launch_storage<5>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 6: return launch_storage<6>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 7: return launch_storage<7>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 8: return launch_storage<8>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 9: return launch_storage<9>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 10: return launch_storage<10>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 11: return launch_storage<11>(p, w, vis, n_bl, ch0, nb, img, st);
     default: return OVRO_ERR_UNSUPPORTED;
   }
 }
@@ -586,21 +653,25 @@ struct GridCtx {
   double cell = 0.0;
 };
 
-size_t grid_ctx_workspace(int n_ant, int n_chan, int image_size) {
+size_t grid_ctx_workspace(int n_ant, int n_chan, int image_size, int storage) {
   if (n_ant <= 0 || n_chan <= 0 || !is_pow2(image_size) || image_size < 16 || image_size > 1024) return 0;
-  const ImgPlan p = make_plan(n_ant, n_chan, image_size);
+  if (storage != OVRO_STORE_FP32 && storage != OVRO_STORE_BF16 && storage != OVRO_STORE_FP16) return 0;
+  const ImgPlan p = make_plan(n_ant, n_chan, image_size, storage);
   size_t need = 0;
   carve_img(nullptr, 0, p, n_ant, n_chan, &need);
   return need;
 }
 
-int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double cell, void* d_ws, size_t ws_bytes) {
+int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double cell, int storage, void* d_ws,
+                  size_t ws_bytes) {
   if (!out) return OVRO_ERR_INVALID_ARG;
   *out = nullptr;
   if (n_ant <= 0 || n_chan <= 0 || !(cell > 0.0)) return OVRO_ERR_INVALID_ARG;
+  if (storage != OVRO_STORE_FP32 && storage != OVRO_STORE_BF16 && storage != OVRO_STORE_FP16)
+    return OVRO_ERR_INVALID_ARG;
   if (!is_pow2(image_size) || image_size < 16 || image_size > 1024 || n_ant > 4096) return OVRO_ERR_UNSUPPORTED;
   GridCtx* g = new GridCtx;
-  g->p = make_plan(n_ant, n_chan, image_size);
+  g->p = make_plan(n_ant, n_chan, image_size, storage);
   size_t need = 0;
   g->w = carve_img(d_ws, ws_bytes, g->p, n_ant, n_chan, &need);
   if (int e = check_workspace(d_ws, ws_bytes, need)) {
@@ -635,7 +706,7 @@ int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_
     }
     return OVRO_OK;
   };
-  const std::string key = tune_key("grid_batch", {g->n_ant, g->n_chan, p.n});
+  const std::string key = tune_key("grid_batch", {g->n_ant, g->n_chan, p.n, p.storage});
   int batch = std::min(p.batch, std::max(1, tuned(key, p.batch)));
   if (tuning(st)) {
     std::vector<int> cands;
@@ -657,8 +728,7 @@ void grid_ctx_free(GridCtx* g) { delete g; }
 extern "C" {
 
 size_t ovro_grid_image_workspace_size(int n_ant, int n_chan, int image_size, int storage) {
-  (void)storage;
-  return ovro::grid_ctx_workspace(n_ant, n_chan, image_size);
+  return ovro::grid_ctx_workspace(n_ant, n_chan, image_size, storage);
 }
 
 int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
@@ -670,10 +740,9 @@ int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
   if (int e = validate(n_ant, h_ant_enu_m, h_chan_freq_hz, n_chan, image_size, cell_dircos)) return e;
   if (storage != OVRO_STORE_FP32 && storage != OVRO_STORE_BF16 && storage != OVRO_STORE_FP16)
     return OVRO_ERR_INVALID_ARG;
-  if (storage != OVRO_STORE_FP32) return OVRO_ERR_UNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(d_vis) % 16 != 0) return OVRO_ERR_INVALID_ARG;
   GridCtx* g = nullptr;
-  if (int e = grid_ctx_init(&g, n_ant, n_chan, image_size, cell_dircos, d_ws, ws_bytes)) return e;
+  if (int e = grid_ctx_init(&g, n_ant, n_chan, image_size, cell_dircos, storage, d_ws, ws_bytes)) return e;
   cudaStream_t st = as_stream(stream);
   int e = grid_ctx_upload(g, h_ant_enu_m, h_chan_freq_hz, st);
   if (!e) e = grid_ctx_enqueue(g, d_vis, d_img, d_n_gridded_or_null, st);
@@ -690,7 +759,7 @@ int ovro_uvw(const double* h_ant_enu_m, int n_ant, const double* h_chan_freq_hz,
   using namespace ovro;
   if (!d_pu || !d_pv) return OVRO_ERR_INVALID_ARG;
   if (int e = validate(n_ant, h_ant_enu_m, h_chan_freq_hz, n_chan, image_size, cell_dircos)) return e;
-  const ImgPlan p = make_plan(n_ant, n_chan, image_size);
+  const ImgPlan p = make_plan(n_ant, n_chan, image_size, OVRO_STORE_FP32);
   size_t need = 0;
   ImgWs w = carve_img(d_ws, ws_bytes, p, n_ant, n_chan, &need);
   if (int e = check_workspace(d_ws, ws_bytes, need)) return e;

@@ -177,7 +177,7 @@ int ovro_pipeline_create(const ovro_pipeline_config* cfg, ovro_pipeline** out) {
   pl->off_up = take(pl->up_bytes);
   pl->off_det = take(pl->det_bytes);
   for (int c = 0; c < cfg->n_coarse; ++c) {
-    const size_t gb = grid_ctx_workspace(cfg->n_ant, pl->nfft[c], cfg->image_size);
+    const size_t gb = grid_ctx_workspace(cfg->n_ant, pl->nfft[c], cfg->image_size, OVRO_STORE_FP32);
     if (gb == 0) {
       delete pl;
       return OVRO_ERR_UNSUPPORTED;
@@ -212,8 +212,8 @@ int ovro_pipeline_bind(ovro_pipeline* pl, void* d_ws, size_t ws_bytes, void* str
   if (!pl->cap_stream) OVRO_CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
   for (int c = 0; c < pl->n_coarse; ++c) {
     GridCtx* g = nullptr;
-    if (int e = grid_ctx_init(&g, pl->n_ant, pl->nfft[c], pl->image_size, pl->cell, pl->ws + pl->off_grid[c],
-                              pl->grid_bytes[c]))
+    if (int e = grid_ctx_init(&g, pl->n_ant, pl->nfft[c], pl->image_size, pl->cell, OVRO_STORE_FP32,
+                              pl->ws + pl->off_grid[c], pl->grid_bytes[c]))
       return e;
     pl->grid.push_back(g);
     if (int e = grid_ctx_upload(g, pl->ant.data(), pl->freq.data() + pl->chan0[c], st)) return e;

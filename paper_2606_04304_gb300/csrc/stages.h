@@ -23,9 +23,11 @@ int correlate_reset_status(cudaStream_t st);
 
 // ---- a5-a7: gridding and imaging (imaging.cu)
 struct GridCtx;
-size_t grid_ctx_workspace(int n_ant, int n_chan, int image_size);
+size_t grid_ctx_workspace(int n_ant, int n_chan, int image_size, int storage);
 // Plans one call's worth of channels; the workspace must stay bound to the context.
-int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double cell, void* d_ws, size_t ws_bytes);
+// storage: OVRO_STORE_* format of the half-transformed grid between the passes.
+int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double cell, int storage, void* d_ws,
+                  size_t ws_bytes);
 // Host lists and tables (pageable copies): once per geometry and frequency axis.
 int grid_ctx_upload(GridCtx* g, const double* h_ant_enu_m, const double* h_chan_freq_hz, cudaStream_t st);
 int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_counts_or_null, cudaStream_t st);
