@@ -268,9 +268,22 @@ def run_ours(args):
     img = torch.empty((n_chan, N, N), dtype=torch.float32, device=dev)
     ws_u = ovro.workspace(ovro.lib().ovro_upchan_workspace_size(cfg.n_input, 1), dev)
     ws_i = ovro.workspace(ovro.grid_image_workspace_size(cfg.n_ant, n_chan, N), dev)
-    ws_d = ovro.workspace(ovro.detect_workspace_size(n_chan, N, cfg.nfft), dev)
+    ws_d = ovro.workspace(ovro.detect_workspace_size(n_chan, N, cfg.nfft), dev) if world == 1 else None
     prm = ovro.detect_params()
     stream = torch.cuda.current_stream()
+    if world > 1:
+        # one Benjamini-Hochberg family over every rank's coarse channel: the
+        # histograms and open-bin values are exchanged on the host (gloo)
+        from paper_2606_04304_gb300 import sharded
+        gloo = dist.new_group(backend="gloo")
+        search = ovro.Search(n_chan, N, cfg.cell, cfg.nfft, prm)
+
+    def detect_step():
+        if world == 1:
+            return ovro.detect(img, cfg.cell, cfg.nfft, freqs, prm, ws=ws_d)
+        search.reset()
+        search.add(0, img)
+        return sharded.sharded_detect(search, freqs, gloo)
 
     def step(ev=None):
         if ev: ev[0].record(stream)
@@ -280,7 +293,7 @@ def run_ours(args):
         if ev: ev[2].record(stream)
         ovro.grid_image(vis, pos, freqs, N, cfg.cell, out=img, ws=ws_i)
         if ev: ev[3].record(stream)
-        c = ovro.detect(img, cfg.cell, cfg.nfft, freqs, prm, ws=ws_d)
+        c = detect_step()
         if ev: ev[4].record(stream)
         return c
 

@@ -303,6 +303,55 @@ int ovro_scorer_adam(float* d_master, float* d_m, float* d_v, const float* d_gra
 int ovro_scorer_to_bf16(const float* d_master, void* d_w_bf16, void* stream);
 
 /* -------------------------------------------------------------------------
+ * Sharded search: the same Stage I search with coarse channels spread over
+ * several processes (one GPU each).  a8-a10 and a12 run per shard; a11's
+ * Benjamini-Hochberg family spans every shard (m = in-horizon pixels x all
+ * fine channels), so the shards' SNR histograms are summed on the host and
+ * the cut is decided bin by bin (ovro_bh_bin_verdict): a bin whose verdict the
+ * bin edges leave open is resolved from the values every shard holds in it
+ * (ovro_search_bin_values, then ovro_bh_resolve on their union, descending).
+ * Every shard then runs NMS at the common cut (ovro_search_candidates).
+ * With one shard this is exactly ovro_detect.
+ *
+ * The handle holds host memory only; the workspace (ovro_detect_workspace_size
+ * bytes) stays bound until ovro_search_destroy.
+ * ------------------------------------------------------------------------- */
+typedef struct ovro_search ovro_search;
+int ovro_search_create(int n_chan, int image_size, double cell_dircos, int n_coarse, const int32_t* h_nfft,
+                       const ovro_detect_params* params, void* d_ws, size_t ws_bytes, void* stream,
+                       ovro_search** out);
+/* Clears the histogram for a new integration. */
+int ovro_search_reset(ovro_search* s, void* stream);
+/* a8-a10 for coarse channel `coarse`: d_img_block holds its nfft images [nfft][N][N]. */
+int ovro_search_add(ovro_search* s, int coarse, const float* d_img_block, void* stream);
+/* Histogram floor key, bin count and this shard's number of tests. */
+int ovro_search_layout(const ovro_search* s, uint32_t* key0, int* n_bins, long long* n_tests);
+/* This shard's SNR histogram (synchronises). */
+int ovro_search_histogram(ovro_search* s, unsigned long long* h_hist, int n_bins, void* stream);
+/* SNR values of this shard in histogram bin `bin` (any order; synchronises).
+ * *n is the count; OVRO_ERR_CAPACITY if it exceeds cap. */
+int ovro_search_bin_values(ovro_search* s, int bin, float* h_vals, long long cap, long long* n, void* stream);
+/* NMS at SNR >= cut; candidates as ovro_detect (synchronises). */
+int ovro_search_candidates(ovro_search* s, float cut, const double* h_chan_freq_hz, ovro_candidate* h_out,
+                           int max_out, int* n_out, void* stream);
+void ovro_search_destroy(ovro_search* s);
+
+/* Host-only pieces of the threshold.  Bins are of the order-preserving 32-bit
+ * key of the FP32 SNR shifted right by 16 (ovro_snr_bin_key); bin b holds
+ * keys key0 + b, the last bin everything above.  ovro_bh_layout gives key0 and
+ * the bin count for the parameters.  The verdict of bin b given the summed
+ * histogram and the total number of tests: 0 no value in it can pass, 1 every
+ * value passes (the cut is *lo_edge), 2 open, 3 empty; *above_next = count of
+ * values above the bin.  ovro_bh_resolve: 1 and *cut = the lowest passing
+ * value of an open bin (values descending), or 0. */
+int ovro_bh_layout(const ovro_detect_params* params, uint32_t* key0, int* n_bins);
+int ovro_bh_bin_verdict(const unsigned long long* h_hist, int n_bins, uint32_t key0, double n_tests, double alpha,
+                        int bin, float* lo_edge, unsigned long long* above_next);
+int ovro_bh_resolve(const float* h_vals_desc, long long n, unsigned long long above_next, double n_tests,
+                    double alpha, float* cut);
+uint32_t ovro_snr_bin_key(float snr);
+
+/* -------------------------------------------------------------------------
  * a14  Batched pipeline: every coarse channel of an integration, one graph
  *
  * Section 2.1 processes the upchannelised data in batches because the

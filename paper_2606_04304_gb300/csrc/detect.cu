@@ -1116,43 +1116,74 @@ void hist_range(const ovro_detect_params& prm, uint32_t* key0, int* n_bins) {
 // surely cannot (no value passes), or is ambiguous -- then its values are
 // gathered and ranked exactly.  Bins are taken from the lowest one where a
 // rejection is possible upwards; the first passing value found is the cut
-// (the largest rank that passes).  Returns 0 with *cut set, 1 when nothing is
-// rejected, or an error status.
-int bh_cut(const std::vector<unsigned long long>& hist, uint32_t key0, int nb, double m, double alpha,
-           const DetectWs& w, const DetectPlan& p, cudaStream_t st, int nsm, float* cut) {
-  std::vector<unsigned long long> above(nb + 1, 0);     // count(SNR >= lower edge of bin b)
-  for (int b = nb - 1; b >= 0; --b) above[b] = above[b + 1] + hist[b];
-  auto edge = [&](int b) { return static_cast<double>(host_key2f((key0 + b) << kHistShift)); };
+// (the largest rank that passes).
+//
+// Verdict for bin b: 0 no value can pass, 1 every value passes (*lo_edge is
+// the cut), 2 ambiguous, 3 empty bin.
+int bh_bin_verdict(const unsigned long long* hist, int nb, uint32_t key0, double m, double alpha, int b,
+                   float* lo_edge, unsigned long long* above_next) {
+  unsigned long long above = 0;                    // count(SNR >= upper edge of bin b)
+  for (int x = nb - 1; x > b; --x) above += hist[x];
+  *above_next = above;
+  *lo_edge = host_key2f((key0 + b) << kHistShift);
+  if (hist[b] == 0) return 3;
   auto passes = [&](double s, unsigned long long rank) {
     return log_q(s) <= std::log(alpha * static_cast<double>(rank) / m);
   };
+  const bool top = b == nb - 1;
+  if (!top && !passes(static_cast<double>(host_key2f((key0 + b + 1) << kHistShift)), above + hist[b])) return 0;
+  if (passes(static_cast<double>(*lo_edge), above + 1)) return 1;
+  return 2;
+}
+
+// The lowest passing value among the values of one bin (descending order),
+// ranks above_next + 1, above_next + 2, ...; returns 1 and *cut, or 0.
+int bh_resolve(const float* v_desc, long long n, unsigned long long above_next, double m, double alpha,
+               float* cut) {
+  long long best = -1;
+  for (long long j = 0; j < n; ++j)
+    if (log_q(v_desc[j]) <= std::log(alpha * static_cast<double>(above_next + j + 1) / m)) best = j;
+  if (best < 0) return 0;
+  *cut = v_desc[best];
+  return 1;
+}
+
+// Values of bin b of this search (device gather; synchronises).
+int gather_bin(const DetectWs& w, const DetectPlan& p, uint32_t key0, int nb, int b, std::vector<float>& v,
+               cudaStream_t st) {
+  const int nsm = num_sms();
+  OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, sizeof(int), st));
+  k_gather_bin<<<8 * nsm, 256, 0, st>>>(w.snr, p.n_vox, key0 + b, b == nb - 1 ? 1 : 0, w.vals, kGatherCap,
+                                        w.count);
+  OVRO_LAUNCH_CHECK();
+  int nv = 0;
+  OVRO_CUDA_TRY(cudaMemcpyAsync(&nv, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (nv > kGatherCap) return OVRO_ERR_CAPACITY;
+  v.resize(nv);
+  if (nv) OVRO_CUDA_TRY(cudaMemcpy(v.data(), w.vals, nv * sizeof(float), cudaMemcpyDeviceToHost));
+  return OVRO_OK;
+}
+
+// Single-search cut.  Returns 0 with *cut set, 1 when nothing is rejected, or
+// an error status.
+int bh_cut(const std::vector<unsigned long long>& hist, uint32_t key0, int nb, double m, double alpha,
+           const DetectWs& w, const DetectPlan& p, cudaStream_t st, float* cut) {
   for (int b = 0; b < nb; ++b) {
-    if (hist[b] == 0) continue;
-    const unsigned long long hi_rank = above[b], lo_rank = above[b + 1] + 1;
-    const bool top = b == nb - 1;
-    if (!top && !passes(edge(b + 1), hi_rank)) continue;          // no value of the bin can pass
-    if (passes(edge(b), lo_rank)) {                               // every value passes
-      *cut = host_key2f((key0 + b) << kHistShift);
+    float lo;
+    unsigned long long above;
+    const int v = bh_bin_verdict(hist.data(), nb, key0, m, alpha, b, &lo, &above);
+    if (v == 0 || v == 3) continue;
+    if (v == 1) {
+      *cut = lo;
       return 0;
     }
     if (hist[b] > static_cast<unsigned long long>(kGatherCap)) return OVRO_ERR_CAPACITY;
-    OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, sizeof(int), st));
-    k_gather_bin<<<8 * nsm, 256, 0, st>>>(w.snr, p.n_vox, key0 + b, top ? 1 : 0, w.vals, kGatherCap, w.count);
-    OVRO_LAUNCH_CHECK();
-    int nv = 0;
-    OVRO_CUDA_TRY(cudaMemcpyAsync(&nv, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
-    OVRO_CUDA_TRY(cudaStreamSynchronize(st));
-    if (static_cast<unsigned long long>(nv) != hist[b]) return OVRO_ERR_CAPACITY;
-    std::vector<float> v(nv);
-    OVRO_CUDA_TRY(cudaMemcpy(v.data(), w.vals, nv * sizeof(float), cudaMemcpyDeviceToHost));
-    std::sort(v.begin(), v.end(), std::greater<float>());
-    int best = -1;
-    for (int j = 0; j < nv; ++j)
-      if (passes(v[j], above[b + 1] + j + 1)) best = j;
-    if (best >= 0) {
-      *cut = v[best];
-      return 0;
-    }
+    std::vector<float> vals;
+    if (int e = gather_bin(w, p, key0, nb, b, vals, st)) return e;
+    if (static_cast<unsigned long long>(vals.size()) != hist[b]) return OVRO_ERR_CAPACITY;
+    std::sort(vals.begin(), vals.end(), std::greater<float>());
+    if (bh_resolve(vals.data(), static_cast<long long>(vals.size()), above, m, alpha, cut)) return 0;
   }
   return 1;
 }
@@ -1317,35 +1348,48 @@ int detect_ctx_coarse(DetectCtx* d, int c, const float* d_img_block, cudaStream_
   return run_filter_coarse(c, d_img_block, p, d->w, d->key0, d->nb, nullptr, st);
 }
 
+// The search's SNR histogram (synchronises; checks the device status word).
+int detect_ctx_histogram(DetectCtx* d, std::vector<unsigned long long>& hist, cudaStream_t st) {
+  hist.assign(d->nb, 0ull);
+  if (d->p.n_valid == 0) return OVRO_OK;
+  OVRO_CUDA_TRY(cudaMemcpyAsync(hist.data(), d->w.hist, d->nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                st));
+  int status = 0;
+  OVRO_CUDA_TRY(cudaMemcpyFromSymbolAsync(&status, g_detect_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+  return status ? OVRO_ERR_CAPACITY : OVRO_OK;
+}
+
 int detect_ctx_finish(DetectCtx* d, const double* h_chan_freq_hz, ovro_candidate* h_out, int max_out, int* n_out,
                       cudaStream_t st) {
+  if (!d || !n_out || (max_out > 0 && !h_out) || max_out < 0 || !h_chan_freq_hz) return OVRO_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (d->p.n_valid == 0) return OVRO_OK;
+  // ---- a11: threshold
+  std::vector<unsigned long long> hist;
+  if (int e = detect_ctx_histogram(d, hist, st)) return e;
+  const double m = static_cast<double>(d->p.n_valid) * d->n_chan;
+  float cut;
+  if (d->prm.mode == OVRO_DETECT_FIXED) {
+    cut = static_cast<float>(d->prm.nsigma);
+  } else {
+    int e = bh_cut(hist, d->key0, d->nb, m, d->prm.alpha, d->w, d->p, st, &cut);
+    if (e == 1) return OVRO_OK;        // nothing is rejected
+    if (e) return e;
+  }
+  return detect_ctx_candidates(d, cut, h_chan_freq_hz, h_out, max_out, n_out, st);
+}
+
+// ---- a12: NMS on the device at a given cut, candidates in (pixel, coarse,
+// channel) order (synchronises).
+int detect_ctx_candidates(DetectCtx* d, float cut, const double* h_chan_freq_hz, ovro_candidate* h_out, int max_out,
+                          int* n_out, cudaStream_t st) {
   if (!d || !n_out || (max_out > 0 && !h_out) || max_out < 0 || !h_chan_freq_hz) return OVRO_ERR_INVALID_ARG;
   *n_out = 0;
   const DetectPlan& p = d->p;
   if (p.n_valid == 0) return OVRO_OK;
   const DetectWs& w = d->w;
-  const ovro_detect_params& prm = d->prm;
-  const uint32_t key0 = d->key0;
-  const int nb = d->nb;
-  const int n_chan = d->n_chan, image_size = d->image_size;
-  // ---- a11: threshold
-  std::vector<unsigned long long> hist(nb);
-  OVRO_CUDA_TRY(cudaMemcpyAsync(hist.data(), w.hist, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  int status = 0;
-  OVRO_CUDA_TRY(cudaMemcpyFromSymbolAsync(&status, g_detect_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
-  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
-  if (status) return OVRO_ERR_CAPACITY;
-  const double m = static_cast<double>(p.n_valid) * n_chan;
-  const int nsm = num_sms();
-  float cut;
-  if (prm.mode == OVRO_DETECT_FIXED) {
-    cut = static_cast<float>(prm.nsigma);
-  } else {
-    int e = bh_cut(hist, key0, nb, m, prm.alpha, w, p, st, nsm, &cut);
-    if (e == 1) return OVRO_OK;        // nothing is rejected
-    if (e) return e;
-  }
-  // ---- a12: NMS on the device, candidates in (pixel, coarse, channel) order
+  const int image_size = d->image_size;
   const long long np = n_pairs_of(p);
   if (np > 0x7fffffffLL / 2) return OVRO_ERR_UNSUPPORTED;
   OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, 4 * sizeof(int), st));
@@ -1416,6 +1460,19 @@ int detect_ctx_finish(DetectCtx* d, const double* h_chan_freq_hz, ovro_candidate
   return total > kCandCap ? OVRO_ERR_CAPACITY : OVRO_OK;
 }
 
+int detect_ctx_bin_values(DetectCtx* d, int b, std::vector<float>& v, cudaStream_t st) {
+  if (!d || b < 0 || b >= d->nb) return OVRO_ERR_INVALID_ARG;
+  v.clear();
+  if (d->p.n_valid == 0) return OVRO_OK;
+  return gather_bin(d->w, d->p, d->key0, d->nb, b, v, st);
+}
+
+void detect_ctx_layout(const DetectCtx* d, uint32_t* key0, int* n_bins, long long* n_tests) {
+  *key0 = d->key0;
+  *n_bins = d->nb;
+  *n_tests = static_cast<long long>(d->p.n_valid) * d->n_chan;
+}
+
 void detect_ctx_free(DetectCtx* d) { delete d; }
 
 }  // namespace ovro
@@ -1442,5 +1499,102 @@ int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dirc
   detect_ctx_free(d);
   return e;
 }
+
+// ---- sharded search (Section 2.4 threshold over several shards)
+struct ovro_search {
+  ovro::DetectCtx* d = nullptr;
+};
+
+int ovro_search_create(int n_chan, int image_size, double cell_dircos, int n_coarse, const int32_t* h_nfft,
+                       const ovro_detect_params* params, void* d_ws, size_t ws_bytes, void* stream,
+                       ovro_search** out) {
+  using namespace ovro;
+  if (!out) return OVRO_ERR_INVALID_ARG;
+  *out = nullptr;
+  DetectCtx* d = nullptr;
+  if (int e = detect_ctx_init(&d, n_chan, image_size, cell_dircos, n_coarse, h_nfft, params, d_ws, ws_bytes))
+    return e;
+  cudaStream_t st = as_stream(stream);
+  int e = detect_ctx_upload(d, st);
+  if (!e) e = detect_ctx_begin(d, st);
+  if (e) {
+    detect_ctx_free(d);
+    return e;
+  }
+  *out = new ovro_search{d};
+  return OVRO_OK;
+}
+
+int ovro_search_reset(ovro_search* s, void* stream) {
+  if (!s) return OVRO_ERR_INVALID_ARG;
+  return ovro::detect_ctx_begin(s->d, ovro::as_stream(stream));
+}
+
+int ovro_bh_layout(const ovro_detect_params* params, uint32_t* key0, int* n_bins) {
+  if (!params || !key0 || !n_bins) return OVRO_ERR_INVALID_ARG;
+  ovro::hist_range(*params, key0, n_bins);
+  return OVRO_OK;
+}
+
+int ovro_search_add(ovro_search* s, int coarse, const float* d_img_block, void* stream) {
+  if (!s) return OVRO_ERR_INVALID_ARG;
+  return ovro::detect_ctx_coarse(s->d, coarse, d_img_block, ovro::as_stream(stream));
+}
+
+int ovro_search_layout(const ovro_search* s, uint32_t* key0, int* n_bins, long long* n_tests) {
+  if (!s || !key0 || !n_bins || !n_tests) return OVRO_ERR_INVALID_ARG;
+  ovro::detect_ctx_layout(s->d, key0, n_bins, n_tests);
+  return OVRO_OK;
+}
+
+int ovro_search_histogram(ovro_search* s, unsigned long long* h_hist, int n_bins, void* stream) {
+  if (!s || !h_hist) return OVRO_ERR_INVALID_ARG;
+  uint32_t k0;
+  int nb;
+  long long nt;
+  ovro::detect_ctx_layout(s->d, &k0, &nb, &nt);
+  if (n_bins != nb) return OVRO_ERR_INVALID_ARG;
+  std::vector<unsigned long long> h;
+  if (int e = ovro::detect_ctx_histogram(s->d, h, ovro::as_stream(stream))) return e;
+  std::memcpy(h_hist, h.data(), nb * sizeof(unsigned long long));
+  return OVRO_OK;
+}
+
+int ovro_search_bin_values(ovro_search* s, int bin, float* h_vals, long long cap, long long* n, void* stream) {
+  if (!s || !n || (cap > 0 && !h_vals)) return OVRO_ERR_INVALID_ARG;
+  std::vector<float> v;
+  if (int e = ovro::detect_ctx_bin_values(s->d, bin, v, ovro::as_stream(stream))) return e;
+  *n = static_cast<long long>(v.size());
+  if (static_cast<long long>(v.size()) > cap) return OVRO_ERR_CAPACITY;
+  if (!v.empty()) std::memcpy(h_vals, v.data(), v.size() * sizeof(float));
+  return OVRO_OK;
+}
+
+int ovro_search_candidates(ovro_search* s, float cut, const double* h_chan_freq_hz, ovro_candidate* h_out,
+                           int max_out, int* n_out, void* stream) {
+  if (!s) return OVRO_ERR_INVALID_ARG;
+  return ovro::detect_ctx_candidates(s->d, cut, h_chan_freq_hz, h_out, max_out, n_out, ovro::as_stream(stream));
+}
+
+void ovro_search_destroy(ovro_search* s) {
+  if (!s) return;
+  ovro::detect_ctx_free(s->d);
+  delete s;
+}
+
+int ovro_bh_bin_verdict(const unsigned long long* h_hist, int n_bins, uint32_t key0, double n_tests, double alpha,
+                        int bin, float* lo_edge, unsigned long long* above_next) {
+  if (!h_hist || !lo_edge || !above_next || bin < 0 || bin >= n_bins || !(n_tests > 0.0) || !(alpha > 0.0))
+    return OVRO_ERR_INVALID_ARG;
+  return ovro::bh_bin_verdict(h_hist, n_bins, key0, n_tests, alpha, bin, lo_edge, above_next);
+}
+
+int ovro_bh_resolve(const float* h_vals_desc, long long n, unsigned long long above_next, double n_tests,
+                    double alpha, float* cut) {
+  if ((n > 0 && !h_vals_desc) || n < 0 || !cut || !(n_tests > 0.0) || !(alpha > 0.0)) return OVRO_ERR_INVALID_ARG;
+  return ovro::bh_resolve(h_vals_desc, n, above_next, n_tests, alpha, cut);
+}
+
+uint32_t ovro_snr_bin_key(float snr) { return ovro::host_f2key(snr) >> ovro::kHistShift; }
 
 }  // extern "C"

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/ovro.h"
 
@@ -47,6 +48,13 @@ int detect_ctx_coarse(DetectCtx* d, int c, const float* d_img_block, cudaStream_
 // a11-a12 (synchronises): candidates in (pixel, coarse, channel) order.
 int detect_ctx_finish(DetectCtx* d, const double* h_chan_freq_hz, ovro_candidate* h_out, int max_out, int* n_out,
                       cudaStream_t st);
+// The pieces of finish, for a threshold decided across several searches:
+// the SNR histogram (synchronises), the values of one bin, and NMS at a cut.
+int detect_ctx_histogram(DetectCtx* d, std::vector<unsigned long long>& hist, cudaStream_t st);
+int detect_ctx_bin_values(DetectCtx* d, int b, std::vector<float>& v, cudaStream_t st);
+int detect_ctx_candidates(DetectCtx* d, float cut, const double* h_chan_freq_hz, ovro_candidate* h_out, int max_out,
+                          int* n_out, cudaStream_t st);
+void detect_ctx_layout(const DetectCtx* d, uint32_t* key0, int* n_bins, long long* n_tests);
 void detect_ctx_free(DetectCtx* d);
 
 }  // namespace ovro

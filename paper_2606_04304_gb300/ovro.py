@@ -86,6 +86,18 @@ def _load() -> ctypes.CDLL:
         "ovro_pipeline_channels": (I, [P, P]),
         "ovro_pipeline_stats": (I, [P, P, P]),
         "ovro_pipeline_destroy": (None, [P]),
+        "ovro_search_create": (I, [I, I, D, I, P, P, P, S, P, P]),
+        "ovro_search_reset": (I, [P, P]),
+        "ovro_search_add": (I, [P, I, P, P]),
+        "ovro_search_layout": (I, [P, P, P, P]),
+        "ovro_search_histogram": (I, [P, P, I, P]),
+        "ovro_search_bin_values": (I, [P, I, P, ctypes.c_longlong, P, P]),
+        "ovro_search_candidates": (I, [P, ctypes.c_float, P, P, I, P, P]),
+        "ovro_search_destroy": (None, [P]),
+        "ovro_bh_layout": (I, [P, P, P]),
+        "ovro_bh_bin_verdict": (I, [P, I, ctypes.c_uint32, D, D, I, P, P]),
+        "ovro_bh_resolve": (I, [P, ctypes.c_longlong, ctypes.c_ulonglong, D, D, P]),
+        "ovro_snr_bin_key": (ctypes.c_uint32, [ctypes.c_float]),
         "ovro_autotune": (I, [I]),
         "ovro_tune_get": (I, [ctypes.c_char_p, P]),
         "ovro_tune_set": (I, [ctypes.c_char_p, I]),
@@ -456,3 +468,95 @@ def tune_save(path: str) -> None:
 
 def tune_load(path: str) -> None:
     _check("ovro_tune_load", _lib.ovro_tune_load(os.fspath(path).encode()))
+
+
+# ------------------------------------------------------- sharded search (a11)
+class Search:
+    """One shard of a Stage I search (ovro_search_*): add coarse-channel image
+    blocks, read the SNR histogram and bin values, then NMS at a given cut."""
+
+    def __init__(self, n_chan: int, image_size: int, cell: float, nfft: Sequence[int],
+                 params: Optional[DetectParams] = None, device=None, stream=None):
+        self._nf = _host(nfft, np.int32)
+        self.params = params or detect_params()
+        self.ws = workspace(detect_workspace_size(n_chan, image_size, self._nf), device)
+        h = ctypes.c_void_p()
+        _check("ovro_search_create", _lib.ovro_search_create(
+            n_chan, image_size, float(cell), self._nf.size, self._nf.ctypes.data_as(ctypes.c_void_p),
+            ctypes.byref(self.params), _ptr(self.ws), self.ws.numel(), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        k0, nb, nt = ctypes.c_uint32(0), ctypes.c_int(0), ctypes.c_longlong(0)
+        _check("ovro_search_layout", _lib.ovro_search_layout(h, ctypes.byref(k0), ctypes.byref(nb), ctypes.byref(nt)))
+        self.key0, self.n_bins, self.n_tests = int(k0.value), int(nb.value), int(nt.value)
+
+    def reset(self, stream=None):
+        _check("ovro_search_reset", _lib.ovro_search_reset(self._h, _stream(stream)))
+
+    def add(self, coarse: int, img_block: torch.Tensor, stream=None):
+        _cuda(img_block, torch.float32, "img_block")
+        _check("ovro_search_add", _lib.ovro_search_add(self._h, coarse, _ptr(img_block), _stream(stream)))
+
+    def histogram(self, stream=None) -> np.ndarray:
+        h = np.zeros(self.n_bins, np.uint64)
+        _check("ovro_search_histogram", _lib.ovro_search_histogram(self._h, h.ctypes.data_as(ctypes.c_void_p),
+                                                                   self.n_bins, _stream(stream)))
+        return h
+
+    def bin_values(self, b: int, stream=None) -> np.ndarray:
+        n = ctypes.c_longlong(0)
+        st = _lib.ovro_search_bin_values(self._h, b, None, 0, ctypes.byref(n), _stream(stream))
+        if st not in (OVRO_OK, -7):
+            _check("ovro_search_bin_values", st)
+        v = np.zeros(n.value, np.float32)
+        if n.value:
+            _check("ovro_search_bin_values", _lib.ovro_search_bin_values(
+                self._h, b, v.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n), _stream(stream)))
+        return v
+
+    def candidates(self, cut: float, freqs_hz, max_out: int = 1 << 20, stream=None) -> np.ndarray:
+        fr = _host(freqs_hz, np.float64)
+        out = np.zeros(max_out, CANDIDATE_DTYPE)
+        n_out = ctypes.c_int(0)
+        _check("ovro_search_candidates", _lib.ovro_search_candidates(
+            self._h, ctypes.c_float(cut), fr.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+            max_out, ctypes.byref(n_out), _stream(stream)))
+        return out[: n_out.value]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ovro_search_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def bh_layout(params: Optional[DetectParams] = None):
+    k0, nb = ctypes.c_uint32(0), ctypes.c_int(0)
+    _check("ovro_bh_layout", _lib.ovro_bh_layout(ctypes.byref(params or detect_params()), ctypes.byref(k0),
+                                                 ctypes.byref(nb)))
+    return int(k0.value), int(nb.value)
+
+
+def bh_bin_verdict(hist: np.ndarray, key0: int, n_tests: float, alpha: float, b: int):
+    h = np.ascontiguousarray(hist, np.uint64)
+    lo, above = ctypes.c_float(0), ctypes.c_ulonglong(0)
+    v = _lib.ovro_bh_bin_verdict(h.ctypes.data_as(ctypes.c_void_p), h.size, key0, float(n_tests), float(alpha), b,
+                                 ctypes.byref(lo), ctypes.byref(above))
+    if v < 0:
+        _check("ovro_bh_bin_verdict", v)
+    return v, float(lo.value), int(above.value)
+
+
+def bh_resolve(vals_desc: np.ndarray, above_next: int, n_tests: float, alpha: float) -> Optional[float]:
+    v = np.ascontiguousarray(vals_desc, np.float32)
+    cut = ctypes.c_float(0)
+    r = _lib.ovro_bh_resolve(v.ctypes.data_as(ctypes.c_void_p), v.size, above_next, float(n_tests), float(alpha),
+                             ctypes.byref(cut))
+    if r < 0:
+        _check("ovro_bh_resolve", r)
+    return float(cut.value) if r == 1 else None
+
+
+def snr_bin_key(snr: float) -> int:
+    return int(_lib.ovro_snr_bin_key(ctypes.c_float(snr)))

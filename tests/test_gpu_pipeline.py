@@ -115,3 +115,32 @@ def test_autotune_then_graph(lib, case, tmp_path):
     again = pl.run(volt)                          # captured with the tuned shapes
     assert pl.stats()[1]
     _same(again, ref)
+
+
+def test_two_shards_equal_one_search(lib, case):
+    # coarse channels 0-1 and 2-3 searched as two shards; the common threshold
+    # (summed histograms, open bins resolved from both shards' values) and each
+    # shard's NMS reproduce one search over all four
+    from paper_2606_04304_gb300 import sharded
+    cfg, volt, pos, img, ref = case
+    freqs = synth.fine_freqs_hz(cfg.nfft)
+    c0 = int(sum(cfg.nfft[:2]))
+    prm = lib.detect_params()
+    shards = [(lib.Search(c0, cfg.image_size, cfg.cell, cfg.nfft[:2], prm), img[:c0], freqs[:c0], 0),
+              (lib.Search(cfg.n_chan_total - c0, cfg.image_size, cfg.cell, cfg.nfft[2:], prm), img[c0:], freqs[c0:], c0)]
+    for s, im, _, _ in shards:
+        off = 0
+        for c, n in enumerate(s._nf):
+            s.add(c, im[off:off + n].contiguous())
+            off += int(n)
+    hist = sum(s.histogram().astype(np.int64) for s, *_ in shards)
+    n_tests = sum(s.n_tests for s, *_ in shards)
+    trace = []
+    cut = sharded.global_cut(hist, shards[0][0].key0, n_tests, prm,
+                             lambda b: np.concatenate([s.bin_values(b) for s, *_ in shards]), trace=trace)
+    got = []
+    for i, (s, _, fr, ch0) in enumerate(shards):
+        cands = s.candidates(cut, fr)
+        got += [(int(c["chan"]) + ch0, int(c["row"]), int(c["col"]), int(c["width"]), float(c["snr"])) for c in cands]
+    want = [(int(c["chan"]), int(c["row"]), int(c["col"]), int(c["width"]), float(c["snr"])) for c in ref]
+    assert sorted(got) == sorted(want)
