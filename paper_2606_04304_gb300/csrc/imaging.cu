@@ -351,22 +351,30 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
 }
 
 // One complex value of the half-transformed grid in FP32.
+// (read-only path: h is not written while the column pass runs)
 template <int S>
 __device__ __forceinline__ float2 load_h(const void* h, const float* hs, long long row, long long idx) {
   if constexpr (S == kStoreF32) {
-    return static_cast<const float2*>(h)[idx];
+    return __ldg(static_cast<const float2*>(h) + idx);
   } else if constexpr (S == kStoreBF16) {
-    return __bfloat1622float2(static_cast<const __nv_bfloat162*>(h)[idx]);
+    const unsigned raw = __ldg(static_cast<const unsigned*>(h) + idx);
+    __nv_bfloat162 b;
+    memcpy(&b, &raw, sizeof(b));
+    return __bfloat1622float2(b);
   } else {
-    const float2 v = __half22float2(static_cast<const __half2*>(h)[idx]);
-    const float s = hs[row];
+    const unsigned raw = __ldg(static_cast<const unsigned*>(h) + idx);
+    __half2 b;
+    memcpy(&b, &raw, sizeof(b));
+    const float2 v = __half22float2(b);
+    const float s = __ldg(hs + row);
     return make_float2(v.x * s, v.y * s);
   }
 }
 
 // Column transforms of the N central columns and the image itself.
+// 1024 threads only for 16-bit storage at G = 2048 (8 columns per CTA)
 template <int LOG2G, int S>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__((S != kStoreF32 && LOG2G == 11) ? 1024 : 512)
 k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, int cols_per_cta, int ch0,
            const float2* __restrict__ tw_g, const float* __restrict__ inv_corr,
            const uint8_t* __restrict__ mask, const int* __restrict__ kept, float* __restrict__ img) {
