@@ -101,8 +101,10 @@ def roofline_models(cfg, n_kept_vis, peaks):
         "k_ztrans": ("hbm", vox * 8, "B", n_chan),
         # sort: read z, write sorted values and the step stream
         "k_rank": ("hbm", vox * 12, "B", n_chan),
-        # walk: read steps, z and gathered sorted values, write z'
-        "k_walk": ("hbm", vox * 16, "B", n_chan),
+        # walk: read the step stream, write the median ranks over it
+        "k_walk": ("hbm", vox * 8, "B", n_chan),
+        # z' = z - median: read ranks and z, write z' (sorted-value gathers hit L1/L2)
+        "k_median_sub": ("hbm", vox * 12, "B", n_chan),
         # boxcars: read z', write SNR and width
         "k_mf": ("hbm", vox * 9, "B", n_chan),
         # NMS: a count pass and a write pass, each reading the SNR cube

@@ -287,8 +287,9 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restric
        uint32_t* __restrict__ steps) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = blockDim.x >> 5;
-  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);           // 256 * W
-  uint32_t* tot = hist + 256 * W;                                // 32
+  const int HP = W + 1;                                          // histogram pitch: digit-major, padded
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);           // 256 * HP
+  uint32_t* tot = hist + 256 * HP;                               // 32
   uint32_t* ka = tot + 32;
   uint32_t* kb = ka + nc;
   uint16_t* ia = reinterpret_cast<uint16_t*>(kb + nc);
@@ -307,14 +308,14 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restric
     __syncthreads();
     for (int pass = 0; pass < 4; ++pass) {
       const int sh = 8 * pass;
-      for (int i = threadIdx.x; i < 256 * W; i += blockDim.x) hist[i] = 0;
+      for (int i = threadIdx.x; i < 256 * HP; i += blockDim.x) hist[i] = 0;
       __syncthreads();
       for (int i = lane; i < seg; i += 32) {
         const int k = warp * seg + i;
-        if (k < nc) atomicAdd(&hist[((ks[k] >> sh) & 255u) * W + warp], 1u);
+        if (k < nc) atomicAdd(&hist[((ks[k] >> sh) & 255u) * HP + warp], 1u);
       }
       __syncthreads();
-      block_exclusive_scan(hist, 256 * W, tot);
+      block_exclusive_scan(hist, 256 * HP, tot);
       for (int b = 0; b < seg; b += 32) {
         const int k = warp * seg + b + lane;
         const bool valid = k < nc;
@@ -322,12 +323,12 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restric
         const uint32_t d = valid ? ((key >> sh) & 255u) : 256u + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         if (valid) {
-          const uint32_t pos = hist[d * W + warp] + __popc(peers & lt_mask);
+          const uint32_t pos = hist[d * HP + warp] + __popc(peers & lt_mask);
           kd[pos] = key;
           id[pos] = is[k];
         }
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) hist[d * W + warp] += __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) hist[d * HP + warp] += __popc(peers);
         __syncwarp();
       }
       __syncthreads();
@@ -408,11 +409,13 @@ __device__ __forceinline__ bool walk_step(uint32_t* bits, int nwords, uint32_t w
   return cur >= 0;
 }
 
-// zbuf holds z on entry and z - running median on exit ([pixel][channel]).
-// steps: the stream written by k_rank (walk_stride words per pixel).
+// One thread per pixel walks its step stream (written by k_rank) and
+// overwrites each consumed step word with the window's median ranks
+// (lower | upper << 16; equal for odd windows).  The loop touches only the
+// bitset in shared memory and the thread's own stream, read two chunks ahead;
+// k_median_sub then applies the medians with all threads.
 __global__ void __launch_bounds__(kWalkThreads)
-k_walk(float* __restrict__ zbuf, const float* __restrict__ sv, const uint32_t* __restrict__ steps,
-       int n_valid, int nc, int h) {
+k_walk(uint32_t* __restrict__ steps, int n_valid, int nc, int h) {
   extern __shared__ uint32_t bits_all[];
   const int t = threadIdx.x;
   const int p = blockIdx.x * kWalkThreads + t;
@@ -421,94 +424,138 @@ k_walk(float* __restrict__ zbuf, const float* __restrict__ sv, const uint32_t* _
   for (int w = 0; w < nwords; ++w) bits[w * kWalkThreads] = 0u;
   if (p >= n_valid) return;
   const int H = (h + 3) & ~3;
-  float* zp = zbuf + static_cast<long long>(p) * nc;
-  const float* svp = sv + static_cast<long long>(p) * nc;
-  const uint32_t* st = steps + static_cast<long long>(p) * walk_stride(nc, h);
+  const int n_total = H + ((nc + 3) & ~3);               // stream words, a multiple of 4
+  uint32_t* st = steps + static_cast<long long>(p) * walk_stride(nc, h);
+  const uint4* st4 = reinterpret_cast<const uint4*>(st);
   int size = 0, cur = -1, lt = 0;
-  for (int i = 0; i < H; ++i)
-    if (!walk_step(bits, nwords, st[i], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
-  const bool vec_ok = (nc & 3) == 0;
-  for (int k0 = 0; k0 < nc; k0 += 4) {
-    const uint4 sw = *reinterpret_cast<const uint4*>(st + H + k0);
-    const uint32_t swa[4] = {sw.x, sw.y, sw.z, sw.w};
-    int lower[4], upper[4];
+  const int n4 = n_total >> 2;
+  uint4 a = st4[0];
+  uint4 b = n4 > 1 ? st4[1] : make_uint4(0u, 0u, 0u, 0u);
+  for (int c = 0; c < n4; ++c) {
+    const uint4 nx = c + 2 < n4 ? st4[c + 2] : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t sw[4] = {a.x, a.y, a.z, a.w};
+    const int i0 = c << 2;
+    if (i0 < H) {
+      // steps building the first window (H is a multiple of 4)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      lower[q] = upper[q] = 0;
-      if (k0 + q >= nc) continue;
-      if (!walk_step(bits, nwords, swa[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
-      lower[q] = cur;
-      upper[q] = (size & 1) ? cur : next_set(bits, cur + 1, nwords);
-      if (upper[q] < 0) { atomicExch(&g_detect_status, 3); return; }
-    }
-    float med[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) med[q] = 0.5f * (svp[lower[q]] + svp[upper[q]]);
-    if (vec_ok) {
-      float4 zz = *reinterpret_cast<const float4*>(zp + k0);
-      zz.x -= med[0];
-      zz.y -= med[1];
-      zz.z -= med[2];
-      zz.w -= med[3];
-      *reinterpret_cast<float4*>(zp + k0) = zz;
+      for (int q = 0; q < 4; ++q)
+        if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
     } else {
-      for (int q = 0; q < 4 && k0 + q < nc; ++q) zp[k0 + q] -= med[q];
+      uint32_t r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        r[q] = 0u;
+        if (i0 - H + q >= nc) continue;
+        if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
+        const int upper = (size & 1) ? cur : next_set(bits, cur + 1, nwords);
+        if (upper < 0) { atomicExch(&g_detect_status, 3); return; }
+        r[q] = static_cast<uint32_t>(cur) | (static_cast<uint32_t>(upper) << 16);
+      }
+      reinterpret_cast<uint4*>(st)[c] = make_uint4(r[0], r[1], r[2], r[3]);
     }
+    a = b;
+    b = nx;
+  }
+}
+
+// z' = z - (v[lower] + v[upper]) / 2 for every voxel, v the pixel's sorted
+// values and the ranks those k_walk left in the step stream.
+__global__ void k_median_sub(float* __restrict__ zbuf, const float* __restrict__ sv,
+                             const uint32_t* __restrict__ steps, int n_valid, int nc, int h) {
+  const int H = (h + 3) & ~3;
+  const int S = walk_stride(nc, h);
+  const long long n = static_cast<long long>(n_valid) * nc;
+  for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < n;
+       v += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int p = static_cast<int>(v / nc), k = static_cast<int>(v - static_cast<long long>(p) * nc);
+    const uint32_t r = __ldg(steps + static_cast<long long>(p) * S + H + k);
+    const float* svp = sv + static_cast<long long>(p) * nc;
+    const float med = 0.5f * (__ldg(svp + (r & 0xffffu)) + __ldg(svp + (r >> 16)));
+    zbuf[v] -= med;
   }
 }
 
 // -------------------------------------------------------- a10 matched filter
+// Shared-memory slot of staged spectrum index i: one pad word after every 8,
+// so thread t's window (starting at index 8t, slot 9t) lies in its own banks
+// and every load of the window is the thread's base slot plus a constant.
+__host__ __device__ constexpr int mf_slot(int i) { return i + (i >> 3); }
+
+// Boxcars for kVox consecutive channels from the register prefix P; BOUNDS
+// keeps only widths that fit inside the coarse channel (edge chunks).
+template <bool BOUNDS>
+__device__ __forceinline__ void mf_chunk(const float (&P)[kWin + 1], int k0, int nc, float (&best)[kVox],
+                                         int (&bw)[kVox]) {
+#pragma unroll
+  for (int j = 0; j < kVox; ++j) { best[j] = -INFINITY; bw[j] = 0; }
+#pragma unroll
+  for (int wi = 0; wi < kNW; ++wi) {
+    const int w = width_of(wi);
+    const int lo = (w - 1) / 2, hi = w - 1 - lo;
+#pragma unroll
+    for (int j = 0; j < kVox; ++j) {
+      if (!BOUNDS || (k0 + j - lo >= 0 && k0 + j + hi <= nc - 1)) {
+        const float S = P[j + kMaxLo + hi + 1] - P[j + kMaxLo - lo];
+        const float v = S * rsqrt_width(wi);
+        if (v > best[j]) { best[j] = v; bw[j] = w; }
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128)
 k_mf(const float* __restrict__ zbuf, int n_valid, int nc, float* __restrict__ snr,
      uint8_t* __restrict__ width, uint32_t hist_key0, int n_bins, unsigned long long* __restrict__ ghist) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* s = reinterpret_cast<float*>(smem);                 // [kMaxLo + nc + kMaxHi + kVox]
-  uint32_t* hist = reinterpret_cast<uint32_t*>(s + kMaxLo + nc + kMaxHi + kVox);
+  const int n_s = kMaxLo + nc + kMaxHi + kVox;
+  float* s = reinterpret_cast<float*>(smem);                 // [mf_slot(n_s)]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(s + mf_slot(n_s) + 1);
   for (int i = threadIdx.x; i < n_bins; i += blockDim.x) hist[i] = 0;
   const float floor_snr = key2f(hist_key0 << kHistShift);
   for (int p = blockIdx.x; p < n_valid; p += gridDim.x) {
     const float* zp = zbuf + static_cast<long long>(p) * nc;
     __syncthreads();
-    for (int i = threadIdx.x; i < kMaxLo + nc + kMaxHi + kVox; i += blockDim.x) {
+    for (int i = threadIdx.x; i < n_s; i += blockDim.x) {
       const int k = i - kMaxLo;
-      s[i] = (k >= 0 && k < nc) ? zp[k] : 0.f;
+      s[mf_slot(i)] = (k >= 0 && k < nc) ? zp[k] : 0.f;
     }
     __syncthreads();
     for (int k0 = threadIdx.x * kVox; k0 < nc; k0 += blockDim.x * kVox) {
+      const float* sw = s + mf_slot(k0);                     // k0 is a multiple of 8
       float P[kWin + 1];
       P[0] = 0.f;
 #pragma unroll
-      for (int i = 0; i < kWin; ++i) P[i + 1] = P[i] + s[k0 + i];     // s index k0 + i <-> channel k0 - 49 + i
+      for (int i = 0; i < kWin; ++i) P[i + 1] = P[i] + sw[mf_slot(i)];   // channel k0 - 49 + i
       float best[kVox];
       int bw[kVox];
-#pragma unroll
-      for (int j = 0; j < kVox; ++j) { best[j] = -INFINITY; bw[j] = 0; }
-#pragma unroll
-      for (int wi = 0; wi < kNW; ++wi) {
-        const int w = width_of(wi);
-        const int lo = (w - 1) / 2, hi = w - 1 - lo;
-#pragma unroll
-        for (int j = 0; j < kVox; ++j) {
-          const int k = k0 + j;
-          if (k - lo >= 0 && k + hi <= nc - 1) {
-            const float S = P[j + kMaxLo + hi + 1] - P[j + kMaxLo - lo];
-            const float v = S * rsqrt_width(wi);
-            if (v > best[j]) { best[j] = v; bw[j] = w; }
-          }
-        }
-      }
+      if (k0 >= kMaxLo && k0 + kVox - 1 + kMaxHi <= nc - 1) mf_chunk<false>(P, k0, nc, best, bw);
+      else mf_chunk<true>(P, k0, nc, best, bw);
       float* so = snr + static_cast<long long>(p) * nc + k0;
       uint8_t* wo = width + static_cast<long long>(p) * nc + k0;
+      if (k0 + kVox <= nc && (reinterpret_cast<uintptr_t>(so) & 15) == 0 &&
+          (reinterpret_cast<uintptr_t>(wo) & 7) == 0) {
+        reinterpret_cast<float4*>(so)[0] = make_float4(best[0], best[1], best[2], best[3]);
+        reinterpret_cast<float4*>(so)[1] = make_float4(best[4], best[5], best[6], best[7]);
+        uint2 wb;
+        wb.x = static_cast<uint32_t>(bw[0]) | (static_cast<uint32_t>(bw[1]) << 8) |
+               (static_cast<uint32_t>(bw[2]) << 16) | (static_cast<uint32_t>(bw[3]) << 24);
+        wb.y = static_cast<uint32_t>(bw[4]) | (static_cast<uint32_t>(bw[5]) << 8) |
+               (static_cast<uint32_t>(bw[6]) << 16) | (static_cast<uint32_t>(bw[7]) << 24);
+        *reinterpret_cast<uint2*>(wo) = wb;
+      } else {
+#pragma unroll
+        for (int j = 0; j < kVox; ++j)
+          if (k0 + j < nc) {
+            so[j] = best[j];
+            wo[j] = static_cast<uint8_t>(bw[j]);
+          }
+      }
 #pragma unroll
       for (int j = 0; j < kVox; ++j) {
-        if (k0 + j < nc) {
-          so[j] = best[j];
-          wo[j] = static_cast<uint8_t>(bw[j]);
-          if (best[j] >= floor_snr) {
-            int b = static_cast<int>((f2key(best[j]) >> kHistShift) - hist_key0);
-            if (b >= n_bins) b = n_bins - 1;
-            atomicAdd(&hist[b], 1u);
-          }
+        if (k0 + j < nc && best[j] >= floor_snr) {
+          int b = static_cast<int>((f2key(best[j]) >> kHistShift) - hist_key0);
+          if (b >= n_bins) b = n_bins - 1;
+          atomicAdd(&hist[b], 1u);
         }
       }
     }
@@ -1010,7 +1057,7 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
   }
   {
     const int threads = 512, W = threads / 32;
-    const size_t sm = (256 * W + 32) * 4 + static_cast<size_t>(nc) * 12;
+    const size_t sm = (256 * (W + 1) + 32) * 4 + static_cast<size_t>(nc) * 12;
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
     // CTAs per SM (each CTA loops over pixels; the outputs do not depend on it)
     auto rank = [&](int per_sm) -> int {
@@ -1029,9 +1076,14 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
   {
     const size_t sm = static_cast<size_t>((nc + 31) / 32) * kWalkThreads * 4;
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-    OVRO_PROF("k_walk", st);
-    k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(
-        w.zbuf, w.sv, w.steps, p.n_valid, nc, p.half[c]);
+    {
+      OVRO_PROF("k_walk", st);
+      k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(w.steps, p.n_valid, nc,
+                                                                                   p.half[c]);
+      OVRO_LAUNCH_CHECK();
+    }
+    OVRO_PROF("k_median_sub", st);
+    k_median_sub<<<8 * nsm, 256, 0, st>>>(w.zbuf, w.sv, w.steps, p.n_valid, nc, p.half[c]);
     OVRO_LAUNCH_CHECK();
   }
   if (d_zp_out) {
@@ -1039,7 +1091,8 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
     OVRO_LAUNCH_CHECK();
   }
   {
-    const size_t sm = static_cast<size_t>(kMaxLo + nc + kMaxHi + kVox) * 4 + static_cast<size_t>(n_bins) * 4;
+    const size_t sm = static_cast<size_t>(mf_slot(kMaxLo + nc + kMaxHi + kVox) + 1) * 4 +
+                      static_cast<size_t>(n_bins) * 4;
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
     // CTAs per SM; trial launches histogram into scratch (the real histogram
     // accumulates over coarse channels and must count every voxel once)

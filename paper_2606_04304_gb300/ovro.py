@@ -138,7 +138,7 @@ def profile_query(kernel: str):
 
 
 TRACED_KERNELS = ("k_upchan", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
-                  "k_rank", "k_walk", "k_mf", "k_nms_warp")
+                  "k_rank", "k_walk", "k_median_sub", "k_mf", "k_nms_warp")
 
 
 def _check(fn: str, status: int) -> int:
