@@ -265,39 +265,36 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     volt_pin = torch.from_numpy(volt_h).pin_memory()
     volt = volt_pin.to(dev)
-    q = torch.empty(ovro.fine_elements(cfg.nfft, cfg.n_time, cfg.n_input), dtype=torch.int8, device=dev)
-    vis = torch.empty((n_chan, ovro.n_baselines(cfg.n_ant), 4, 2), dtype=torch.int32, device=dev)
-    img = torch.empty((n_chan, N, N), dtype=torch.float32, device=dev)
-    ws_u = ovro.workspace(ovro.lib().ovro_upchan_workspace_size(cfg.n_input, 1), dev)
-    ws_i = ovro.workspace(ovro.grid_image_workspace_size(cfg.n_ant, n_chan, N), dev)
-    ws_d = ovro.workspace(ovro.detect_workspace_size(n_chan, N, cfg.nfft), dev) if world == 1 else None
     prm = ovro.detect_params()
     stream = torch.cuda.current_stream()
-    if world > 1:
-        # one Benjamini-Hochberg family over every rank's coarse channel: the
-        # histograms and open-bin values are exchanged on the host (gloo)
+    # one integration = one step: at N = 1 through the batched pipeline (plan
+    # and tables uploaded once, the device work replayed as one CUDA graph);
+    # at N > 1 stage by stage with one Benjamini-Hochberg family over all ranks
+    use_pipeline = world == 1
+    if use_pipeline:
+        centres = [synth.coarse_centre_hz(c) for c in range(cfg.n_coarse)]
+        pl = ovro.Pipeline(cfg.n_ant, cfg.nfft, centres, cfg.n_time, pos, N, cfg.cell, xeng_mode=mode,
+                           params=prm, use_graph=True, device=dev)
+
+        def step():
+            return pl.run(volt)
+    else:
         from paper_2606_04304_gb300 import sharded
+        q = torch.empty(ovro.fine_elements(cfg.nfft, cfg.n_time, cfg.n_input), dtype=torch.int8, device=dev)
+        vis = torch.empty((n_chan, ovro.n_baselines(cfg.n_ant), 4, 2), dtype=torch.int32, device=dev)
+        img = torch.empty((n_chan, N, N), dtype=torch.float32, device=dev)
+        ws_u = ovro.workspace(ovro.lib().ovro_upchan_workspace_size(cfg.n_input, 1), dev)
+        ws_i = ovro.workspace(ovro.grid_image_workspace_size(cfg.n_ant, n_chan, N), dev)
         gloo = dist.new_group(backend="gloo")
         search = ovro.Search(n_chan, N, cfg.cell, cfg.nfft, prm)
 
-    def detect_step():
-        if world == 1:
-            return ovro.detect(img, cfg.cell, cfg.nfft, freqs, prm, ws=ws_d)
-        search.reset()
-        search.add(0, img)
-        return sharded.sharded_detect(search, freqs, gloo)
-
-    def step(ev=None):
-        if ev: ev[0].record(stream)
-        ovro.upchan(volt, cfg.nfft, out_q=q, ws=ws_u)
-        if ev: ev[1].record(stream)
-        ovro.correlate(q, cfg.n_ant, n_chan, K, mode, out=vis)
-        if ev: ev[2].record(stream)
-        ovro.grid_image(vis, pos, freqs, N, cfg.cell, out=img, ws=ws_i)
-        if ev: ev[3].record(stream)
-        c = detect_step()
-        if ev: ev[4].record(stream)
-        return c
+        def step():
+            ovro.upchan(volt, cfg.nfft, out_q=q, ws=ws_u)
+            ovro.correlate(q, cfg.n_ant, n_chan, K, mode, out=vis)
+            ovro.grid_image(vis, pos, freqs, N, cfg.cell, out=img, ws=ws_i)
+            search.reset()
+            search.add(0, img)
+            return sharded.sharded_detect(search, freqs, gloo)
 
     for _ in range(args.warmup):
         step()
@@ -309,12 +306,20 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    # ---- device-resident timed region
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    _, n_grid = ovro.grid_image(vis, pos, freqs, N, cfg.cell, out=img, ws=ws_i, want_counts=True)
-    n_kept_vis = int(n_grid.sum().item()) // 2
-    l0 = ovro.launch_count()
+    if use_pipeline:
+        n_kept_vis = pl.gridded()
+    else:
+        _, n_grid = ovro.grid_image(vis, pos, freqs, N, cfg.cell, out=img, ws=ws_i, want_counts=True)
+        n_kept_vis = int(n_grid.sum().item()) // 2
+
+    # ---- device-resident timed region (per-kernel CUDA events: stream events
+    # when eager, event nodes inside the graph when replayed)
     ovro.profile(True)
+    if use_pipeline:
+        step()                                   # capture the graph with its timing nodes (untimed)
+        torch.cuda.synchronize()
+        ovro.profile(True)                       # clear the trace of that untimed run
+    l0 = ovro.launch_count()
     barrier()
     torch.cuda.synchronize()
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -322,18 +327,23 @@ def run_ours(args):
         t_wall = time.perf_counter()
         e_start.record(stream)
         for i in range(args.steps):
-            cands = step(evs[i])
+            cands = step()
         e_end.record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
-    ovro.profile(False)
-    barrier()
     launches = ovro.launch_count() - l0
     kern = {k: ovro.profile_query(k) for k in ovro.TRACED_KERNELS}
     kern = {k: v for k, v in kern.items() if v[1] > 0}
+    ovro.profile(False)
+    if use_pipeline:
+        step()                                   # recapture without timing nodes (untimed)
+        torch.cuda.synchronize()
+    barrier()
     ms = e_start.elapsed_time(e_end) / args.steps
-    stage_ms = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)]
-                         for i in range(args.steps)]).mean(axis=0)
+    stages = {"upchan": ("k_upchan",), "correlate": ("k_xeng_tc", "k_xeng_simt"),
+              "grid_image": ("k_grid_rows", "k_fft_cols"),
+              "detect": ("k_stats", "k_ztrans", "k_rank", "k_walk", "k_median_sub", "k_mf", "k_nms_warp")}
+    stage_ms = {st: sum(kern[k][0] for k in ks if k in kern) / args.steps for st, ks in stages.items()}
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -394,8 +404,8 @@ def run_ours(args):
                        "l2": "inputs larger than L2: 169 MB voltages and 16.3 GB visibilities per step",
                        "parallelism": f"{world} independent coarse channels"},
             "images_per_s": world * n_chan / (ms * 1e-3),
-            "stage_ms": {"upchan": float(stage_ms[0]), "correlate": float(stage_ms[1]),
-                         "grid_image": float(stage_ms[2]), "detect": float(stage_ms[3])},
+            "stage_kernel_ms": {k: float(v) for k, v in stage_ms.items()},
+            "path": "ovro_pipeline (CUDA graph)" if use_pipeline else "stage calls + sharded threshold",
             "roofline": roof,
             "rooflines": roofs,
             "kept_visibilities_per_step": n_kept_vis,

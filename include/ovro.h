@@ -411,6 +411,9 @@ int ovro_pipeline_channels(const ovro_pipeline* pl, double* h_freq_or_null);
 /* Kernels the last run launched (graph replay, threshold and NMS included)
  * and whether a graph is live. */
 int ovro_pipeline_stats(const ovro_pipeline* pl, long long* kernels_per_run, int* graph_live);
+/* Cross visibilities the last run gridded, summed over channels (each
+ * baseline once, mirrors not counted; synchronises). */
+int ovro_pipeline_gridded(ovro_pipeline* pl, long long* n_gridded, void* stream);
 void ovro_pipeline_destroy(ovro_pipeline* pl);
 
 /* -------------------------------------------------------------------------

@@ -28,8 +28,56 @@ struct ProfRec {
   std::vector<cudaEvent_t> begin, end;
 };
 static std::map<std::string, ProfRec> g_prof;
+// times collected from graph event nodes: name -> (ms, launches)
+static std::map<std::string, std::pair<double, int>> g_prof_graph;
+static thread_local std::vector<GraphTraceEntry>* g_capture_trace = nullptr;
 
 bool profiling() { return g_prof_on.load(std::memory_order_relaxed); }
+
+void set_capture_trace(std::vector<GraphTraceEntry>* list) { g_capture_trace = list; }
+bool graph_tracing() { return g_capture_trace != nullptr; }
+
+void graph_mark(const char* name, cudaStream_t st, bool begin) {
+  if (!g_capture_trace) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  if (cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) != cudaSuccess) {
+    cudaEventDestroy(e);
+    return;
+  }
+  if (begin) {
+    g_capture_trace->push_back(GraphTraceEntry{name, e, nullptr});
+  } else {
+    // pair with the latest open entry of this name
+    for (auto it = g_capture_trace->rbegin(); it != g_capture_trace->rend(); ++it)
+      if (it->end == nullptr && std::strcmp(it->name, name) == 0) {
+        it->end = e;
+        return;
+      }
+    cudaEventDestroy(e);
+  }
+}
+
+void graph_trace_collect(const std::vector<GraphTraceEntry>& list) {
+  if (!profiling()) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (const GraphTraceEntry& t : list) {
+    if (!t.end) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.begin, t.end) != cudaSuccess) continue;
+    auto& a = g_prof_graph[t.name];
+    a.first += ms;
+    a.second += 1;
+  }
+}
+
+void graph_trace_free(std::vector<GraphTraceEntry>& list) {
+  for (GraphTraceEntry& t : list) {
+    if (t.begin) cudaEventDestroy(t.begin);
+    if (t.end) cudaEventDestroy(t.end);
+  }
+  list.clear();
+}
 
 void prof_mark(const char* name, cudaStream_t st, bool begin) {
   cudaEvent_t e;
@@ -47,6 +95,7 @@ static void prof_clear() {
     for (cudaEvent_t e : kv.second.end) cudaEventDestroy(e);
   }
   g_prof.clear();
+  g_prof_graph.clear();
 }
 
 void snprintf_last_error(const char* fmt, ...) {
@@ -90,6 +139,11 @@ int ovro_profile_query(const char* kernel, double* total_ms, int* launches) {
   std::lock_guard<std::mutex> lk(ovro::g_prof_mu);
   *total_ms = 0.0;
   *launches = 0;
+  auto g = ovro::g_prof_graph.find(kernel);
+  if (g != ovro::g_prof_graph.end()) {
+    *total_ms += g->second.first;
+    *launches += g->second.second;
+  }
   auto it = ovro::g_prof.find(kernel);
   if (it == ovro::g_prof.end()) return OVRO_OK;
   const auto& r = it->second;
@@ -100,7 +154,7 @@ int ovro_profile_query(const char* kernel, double* total_ms, int* launches) {
     if (cudaEventElapsedTime(&ms, r.begin[i], r.end[i]) != cudaSuccess) return OVRO_ERR_CUDA;
     *total_ms += ms;
   }
-  *launches = static_cast<int>(n);
+  *launches += static_cast<int>(n);
   return OVRO_OK;
 }
 

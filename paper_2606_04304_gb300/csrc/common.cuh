@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "../../include/ovro.h"
 
@@ -32,15 +33,34 @@ inline bool capturing(cudaStream_t st) {
   return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
 }
 
+// Tracing inside a CUDA graph: while a trace list is installed for the
+// capturing thread, traced launches record external event nodes into the
+// graph (begin/end per launch); graph_trace_collect adds their elapsed times
+// to the trace after the graph has run.
+struct GraphTraceEntry {
+  const char* name;
+  cudaEvent_t begin, end;
+};
+void set_capture_trace(std::vector<GraphTraceEntry>* list);   // nullptr: none
+void graph_mark(const char* name, cudaStream_t st, bool begin);
+bool graph_tracing();
+void graph_trace_collect(const std::vector<GraphTraceEntry>& list);
+void graph_trace_free(std::vector<GraphTraceEntry>& list);
+
 struct ProfScope {
   const char* name;
   cudaStream_t st;
-  bool on;
-  ProfScope(const char* n, cudaStream_t s) : name(n), st(s), on(profiling() && !capturing(s)) {
-    if (on) prof_mark(name, st, true);
+  int mode;          // 0 off, 1 stream events, 2 graph event nodes
+  ProfScope(const char* n, cudaStream_t s) : name(n), st(s), mode(0) {
+    if (!profiling()) return;
+    if (!capturing(s)) mode = 1;
+    else if (graph_tracing()) mode = 2;
+    if (mode == 1) prof_mark(name, st, true);
+    if (mode == 2) graph_mark(name, st, true);
   }
   ~ProfScope() {
-    if (on) prof_mark(name, st, false);
+    if (mode == 1) prof_mark(name, st, false);
+    if (mode == 2) graph_mark(name, st, false);
   }
 };
 #define OVRO_PROF(name, st) ::ovro::ProfScope ovro_prof_scope_(name, st)

@@ -729,6 +729,17 @@ int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_
   return OVRO_OK;
 }
 
+int grid_ctx_gridded(GridCtx* g, long long* total, cudaStream_t st) {
+  if (!g || !total) return OVRO_ERR_INVALID_ARG;
+  std::vector<int> k(g->n_chan);
+  OVRO_CUDA_TRY(cudaMemcpyAsync(k.data(), g->w.kept, g->n_chan * sizeof(int), cudaMemcpyDeviceToHost, st));
+  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+  long long s = 0;
+  for (int v : k) s += v;
+  *total = s;
+  return OVRO_OK;
+}
+
 void grid_ctx_free(GridCtx* g) { delete g; }
 
 }  // namespace ovro

@@ -42,6 +42,8 @@ struct ovro_pipeline {
   const uint8_t* graph_volt = nullptr;
   cudaStream_t cap_stream = nullptr;     // private stream for capture (the legacy stream cannot be captured)
   unsigned long long graph_kernels = 0;   // kernel nodes of the captured graph
+  std::vector<ovro::GraphTraceEntry> trace;   // event nodes of traced kernels (captured while tracing)
+  bool graph_traced = false;
   unsigned long long kernels_per_run = 0;  // kernels of the last run (graph + threshold/NMS)
 };
 
@@ -78,6 +80,8 @@ void drop_graph(ovro_pipeline* pl) {
   pl->exec = nullptr;
   pl->graph = nullptr;
   pl->graph_volt = nullptr;
+  graph_trace_free(pl->trace);
+  pl->graph_traced = false;
 }
 
 // Records the device work on the private capture stream (nothing executes);
@@ -86,8 +90,11 @@ int capture(ovro_pipeline* pl, const uint8_t* d_volt) {
   drop_graph(pl);
   cudaStream_t st = pl->cap_stream;
   const unsigned long long l0 = ovro_launch_count();
+  const bool traced = profiling();
   OVRO_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  if (traced) set_capture_trace(&pl->trace);
   const int e = enqueue_device(pl, d_volt, st);
+  set_capture_trace(nullptr);
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(st, &g);
   const unsigned long long n = ovro_launch_count() - l0;
@@ -108,6 +115,7 @@ int capture(ovro_pipeline* pl, const uint8_t* d_volt) {
   }
   pl->graph = g;
   pl->graph_volt = d_volt;
+  pl->graph_traced = traced;
   pl->graph_kernels = n;
   return OVRO_OK;
 }
@@ -238,7 +246,8 @@ int ovro_pipeline_run(ovro_pipeline* pl, const uint8_t* d_volt, ovro_candidate* 
   cudaStream_t st = as_stream(stream);
   unsigned long long n_dev = 0;
   if (pl->use_graph && !tuning(st)) {
-    if (!pl->exec || pl->graph_volt != d_volt)
+    // (re)capture for a new buffer, or when tracing was switched since
+    if (!pl->exec || pl->graph_volt != d_volt || pl->graph_traced != profiling())
       if (int e = capture(pl, d_volt)) return e;
     OVRO_CUDA_TRY(cudaGraphLaunch(pl->exec, st));
     add_launches(pl->graph_kernels);
@@ -251,6 +260,10 @@ int ovro_pipeline_run(ovro_pipeline* pl, const uint8_t* d_volt, ovro_candidate* 
   const unsigned long long l1 = ovro_launch_count();
   const int e = detect_ctx_finish(pl->det, pl->freq.data(), h_out, max_out, n_out, st);
   pl->kernels_per_run = n_dev + (ovro_launch_count() - l1);
+  if (pl->exec && pl->graph_traced && pl->use_graph && !tuning(st)) {
+    OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+    graph_trace_collect(pl->trace);              // per-kernel times of this replay
+  }
   if (pl->xeng_mode == OVRO_XENG_TC) {
     const int s = ovro_correlate_status(st);
     if (s) return s;
@@ -262,6 +275,17 @@ int ovro_pipeline_stats(const ovro_pipeline* pl, long long* kernels_per_run, int
   if (!pl) return OVRO_ERR_INVALID_ARG;
   if (kernels_per_run) *kernels_per_run = static_cast<long long>(pl->kernels_per_run);
   if (graph_live) *graph_live = pl->exec ? 1 : 0;
+  return OVRO_OK;
+}
+
+int ovro_pipeline_gridded(ovro_pipeline* pl, long long* n_gridded, void* stream) {
+  if (!pl || !n_gridded) return OVRO_ERR_INVALID_ARG;
+  *n_gridded = 0;
+  for (ovro::GridCtx* g : pl->grid) {
+    long long n = 0;
+    if (int e = ovro::grid_ctx_gridded(g, &n, ovro::as_stream(stream))) return e;
+    *n_gridded += n;
+  }
   return OVRO_OK;
 }
 

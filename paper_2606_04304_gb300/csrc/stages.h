@@ -32,6 +32,8 @@ int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double c
 // Host lists and tables (pageable copies): once per geometry and frequency axis.
 int grid_ctx_upload(GridCtx* g, const double* h_ant_enu_m, const double* h_chan_freq_hz, cudaStream_t st);
 int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_counts_or_null, cudaStream_t st);
+// Cross visibilities gridded by the last enqueue (mirrors not counted; synchronises).
+int grid_ctx_gridded(GridCtx* g, long long* total, cudaStream_t st);
 void grid_ctx_free(GridCtx* g);
 
 // ---- a8-a12: detection (detect.cu)

@@ -22,6 +22,8 @@
 //    drain their TMEM lane quarter with tcgen05.ld and store int32 records.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "stages.h"
 #include "tune.h"
@@ -303,6 +305,192 @@ k_xeng_tc(const int8_t* __restrict__ q, int n_ant, int n_spec, int n_tiles, int 
   }
 }
 
+// ---------------------------------------------- tcgen05 path, channel-major
+// For arrays of at most 768 inputs and at most 32 spectra per integration, a
+// persistent CTA per SM takes whole channels: the channel's int8 spectra are
+// converted once into FP16 operand tiles in shared memory -- per tile of 128
+// inputs, rows 0..127 hold X = (re, im) per spectrum and rows 128..255 hold
+// Z = (-im, re) -- so tile J as a 256-row B operand yields Re in TMEM columns
+// 0..127 and Im in 128..255 against A = X rows of tile I.  Two 256-column
+// accumulators alternate: the MMAs of tile pair t+1 run while the epilogue
+// drains pair t.  The next channel's spectra are prefetched into L2.
+constexpr int kV2Threads = 256;
+constexpr int kV2MaxTiles = 6;
+constexpr int kV2TileBytes = 2 * kTcM * kTcKc * 2;        // 32 KB: X rows then Z rows
+constexpr uint32_t kV2TmemCols = 512;
+
+__global__ void __launch_bounds__(kV2Threads, 1)
+k_xeng_tc2(const int8_t* __restrict__ q, int n_ant, int n_spec, int n_tiles, int n_chan, int prefetch,
+           int32_t* __restrict__ vis) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int n_input = 2 * n_ant;
+  const long long n_bl = static_cast<long long>(n_ant) * (n_ant + 1) / 2;
+  const int n_pairs = n_tiles * (n_tiles + 1) / 2;
+  const int NI = n_tiles * kTcM;
+  const long long chan_bytes = static_cast<long long>(n_spec) * n_input * 2;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base_sh)), "r"(kV2TmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_sh = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+  uint32_t par[2] = {0u, 0u};          // next phase parity to wait for, per accumulator
+  int inflight[2] = {0, 0};            // a commit on that accumulator's barrier not yet waited for
+
+  // tile pair t -> (I, J), I <= J, row-major over the upper triangle
+  auto pair_of = [&](int t, int& I, int& J) {
+    I = 0;
+    while (t >= n_tiles - I) { t -= n_tiles - I; ++I; }
+    J = I + t;
+  };
+  auto issue = [&](int t) {
+    inflight[t & 1] = 1;
+    if (tid != 0) return;
+    int I, J;
+    pair_of(t, I, J);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t a0 = smem_u32(smem + I * kV2TileBytes), b0 = smem_u32(smem + J * kV2TileBytes);
+    const uint32_t d = tmem + static_cast<uint32_t>((t & 1) * 256);
+#pragma unroll
+    for (int kk = 0; kk < kTcKc / 16; ++kk) {
+      const uint64_t ad = make_sdesc(a0 + kk * 2 * kLBO);
+      const uint64_t bd = make_sdesc(b0 + kk * 2 * kLBO);
+      const uint32_t acc = kk > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+          :: "r"(d), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc) : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(&mbar[t & 1])) : "memory");
+  };
+
+  for (int ch = blockIdx.x; ch < n_chan; ch += gridDim.x) {
+    const int8_t* qc = q + static_cast<long long>(ch) * chan_bytes;
+    if (prefetch && tid == 0 && ch + static_cast<int>(gridDim.x) < n_chan) {
+      const int8_t* nx = qc + static_cast<long long>(gridDim.x) * chan_bytes;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                   :: "l"(nx), "r"(static_cast<uint32_t>(chan_bytes)) : "memory");
+    }
+    // ---- operands: task = (spectrum group of 4, input), inputs fastest
+    for (int task = tid; task < NI * (kTcKc / 8); task += kV2Threads) {
+      const int i = task % NI, sg = task / NI;
+      uint32_t xw[4], zw[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int sp = 4 * sg + j;
+        char2 v = make_char2(0, 0);
+        if (sp < n_spec && i < n_input)
+          v = reinterpret_cast<const char2*>(qc + static_cast<long long>(sp) * n_input * 2)[i];
+        const __half2 hx = __halves2half2(__short2half_rn(v.x), __short2half_rn(v.y));
+        const __half2 hz = __halves2half2(__short2half_rn(static_cast<short>(-v.y)), __short2half_rn(v.x));
+        xw[j] = *reinterpret_cast<const uint32_t*>(&hx);
+        zw[j] = *reinterpret_cast<const uint32_t*>(&hz);
+      }
+      const int t = i / kTcM, r = i - t * kTcM;
+      unsigned char* base = smem + t * kV2TileBytes + op_offset(r, 8 * sg);
+      *reinterpret_cast<uint4*>(base) = make_uint4(xw[0], xw[1], xw[2], xw[3]);
+      *reinterpret_cast<uint4*>(base + 16 * kSBO) = make_uint4(zw[0], zw[1], zw[2], zw[3]);   // rows 128 + r
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    issue(0);
+    for (int t = 0; t < n_pairs; ++t) {
+      if (t + 1 < n_pairs) issue(t + 1);        // its accumulator was drained in step t - 1
+      const bool ok = mbar_wait(smem_u32(&mbar[t & 1]), par[t & 1]);
+      if (ok) {
+        par[t & 1] ^= 1u;
+        inflight[t & 1] = 0;
+      } else {
+        atomicExch(&g_xeng_status, 1);
+        abort_sh = 1;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ok) {
+        int I, J;
+        pair_of(t, I, J);
+        const int q4 = warp & 3, wg = warp >> 2;
+        const int gi = I * kTcM + q4 * 32 + lane;
+        const int a = gi >> 1, pa = gi & 1;
+        int4* out = reinterpret_cast<int4*>(vis + static_cast<long long>(ch) * n_bl * 8);
+        const uint32_t cb = static_cast<uint32_t>((t & 1) * 256);
+#pragma unroll 1
+        for (int hh = 0; hh < 2; ++hh) {
+          const int cin0 = wg * 64 + hh * 32;     // column inputs cin0 .. cin0 + 31
+          uint32_t re[32], im[32];
+          const uint32_t tl = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + cb + cin0;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+              "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]),
+                "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]),
+                "=r"(re[13]), "=r"(re[14]), "=r"(re[15]), "=r"(re[16]), "=r"(re[17]), "=r"(re[18]),
+                "=r"(re[19]), "=r"(re[20]), "=r"(re[21]), "=r"(re[22]), "=r"(re[23]), "=r"(re[24]),
+                "=r"(re[25]), "=r"(re[26]), "=r"(re[27]), "=r"(re[28]), "=r"(re[29]), "=r"(re[30]),
+                "=r"(re[31])
+              : "r"(tl));
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+              "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]),
+                "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]),
+                "=r"(im[13]), "=r"(im[14]), "=r"(im[15]), "=r"(im[16]), "=r"(im[17]), "=r"(im[18]),
+                "=r"(im[19]), "=r"(im[20]), "=r"(im[21]), "=r"(im[22]), "=r"(im[23]), "=r"(im[24]),
+                "=r"(im[25]), "=r"(im[26]), "=r"(im[27]), "=r"(im[28]), "=r"(im[29]), "=r"(im[30]),
+                "=r"(im[31])
+              : "r"(tl + 128u));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (a < n_ant) {
+            const int b0 = (J * kTcInputsN + cin0) >> 1;
+#pragma unroll
+            for (int bb = 0; bb < 16; ++bb) {
+              const int b = b0 + bb;
+              if (b >= n_ant || b < a) continue;
+              int4 v;
+              v.x = __float2int_rn(__uint_as_float(re[2 * bb]));
+              v.y = __float2int_rn(__uint_as_float(im[2 * bb]));
+              v.z = __float2int_rn(__uint_as_float(re[2 * bb + 1]));
+              v.w = __float2int_rn(__uint_as_float(im[2 * bb + 1]));
+              __stcs(out + bl_index(a, b, n_ant) * 2 + pa, v);
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (abort_sh) break;
+    }
+    if (abort_sh) break;
+  }
+  // after a timeout: wait (bounded) for the MMAs still in flight before the
+  // accumulators are released
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+    if (inflight[b]) (void)mbar_wait(smem_u32(&mbar[b]), par[b]);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tmem), "r"(kV2TmemCols) : "memory");
+  }
+}
+
 }  // namespace
 }  // namespace ovro
 
@@ -348,6 +536,19 @@ int correlate_enqueue(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec,
   if (reset_status)
     if (int e = correlate_reset_status(st)) return e;
   const int n_tiles = (n_input + kTcM - 1) / kTcM;
+  if (n_tiles <= kV2MaxTiles && n_spec <= kTcSpecPerChunk) {
+    // channel-major kernel; at least 116 KB of shared memory keeps one CTA
+    // (and so one 512-column TMEM allocation) per SM
+    const int smem = std::max(n_tiles * kV2TileBytes, 116 * 1024);
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const long long cb = static_cast<long long>(n_spec) * n_input * 2;
+    const int prefetch = (cb % 16 == 0 && reinterpret_cast<uintptr_t>(d_fine_q) % 16 == 0) ? 1 : 0;
+    const int grid = std::min(n_chan, num_sms());
+    OVRO_PROF("k_xeng_tc", st);
+    k_xeng_tc2<<<grid, kV2Threads, smem, st>>>(d_fine_q, n_ant, n_spec, n_tiles, n_chan, prefetch, d_vis);
+    OVRO_LAUNCH_CHECK();
+    return OVRO_OK;
+  }
   const int n_pairs = n_tiles * (n_tiles + 1) / 2;
   const long long n_items = static_cast<long long>(n_pairs) * n_chan;
   // 96 KB of dynamic shared memory keeps at most two CTAs (2 x 256 TMEM columns) per SM

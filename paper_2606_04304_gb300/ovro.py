@@ -86,6 +86,7 @@ def _load() -> ctypes.CDLL:
         "ovro_pipeline_channels": (I, [P, P]),
         "ovro_pipeline_stats": (I, [P, P, P]),
         "ovro_pipeline_destroy": (None, [P]),
+        "ovro_pipeline_gridded": (I, [P, P, P]),
         "ovro_search_create": (I, [I, I, D, I, P, P, P, S, P, P]),
         "ovro_search_reset": (I, [P, P]),
         "ovro_search_add": (I, [P, I, P, P]),
@@ -431,6 +432,12 @@ class Pipeline:
         g = ctypes.c_int(0)
         _check("ovro_pipeline_stats", _lib.ovro_pipeline_stats(self._h, ctypes.byref(k), ctypes.byref(g)))
         return int(k.value), bool(g.value)
+
+    def gridded(self, stream=None) -> int:
+        """Cross visibilities the last run gridded (summed over channels)."""
+        n = ctypes.c_longlong(0)
+        _check("ovro_pipeline_gridded", _lib.ovro_pipeline_gridded(self._h, ctypes.byref(n), _stream(stream)))
+        return int(n.value)
 
     def close(self):
         if getattr(self, "_h", None):
