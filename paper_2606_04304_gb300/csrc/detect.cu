@@ -8,7 +8,7 @@
 //      k_ztrans      standardises (z = (x - med) / (1.4826 MAD)) and turns the
 //                    cube into per-pixel spectra [coarse][pixel][channel].
 //  a9  k_rank        per pixel spectrum: stable LSD radix sort (4 x 8-bit
-//                    digits, warp match for in-warp ranks) -> sorted values and
+//                    digits, ballot multisplit for in-warp ranks) -> sorted values and
 //                    the rank of every channel.
 //      k_walk        one thread per pixel walks the channels keeping the
 //                    window's ranks in a bitset (shared memory, interleaved per
@@ -282,7 +282,7 @@ __host__ __device__ __forceinline__ int walk_stride(int nc, int h) {
   return (nc + ((h + 3) & ~3) + 3) & ~3;
 }
 // Stable LSD radix sort of one pixel spectrum per CTA iteration.
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restrict__ sv,
        uint32_t* __restrict__ steps) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -320,8 +320,15 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restric
         const int k = warp * seg + b + lane;
         const bool valid = k < nc;
         const uint32_t key = valid ? ks[k] : 0u;
-        const uint32_t d = valid ? ((key >> sh) & 255u) : 256u + lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = (key >> sh) & 255u;
+        // lanes holding the same digit: one ballot per digit bit
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+          const bool x = (d >> bit) & 1u;
+          const unsigned bb = __ballot_sync(0xffffffffu, x);
+          peers &= x ? bb : ~bb;
+        }
         if (valid) {
           const uint32_t pos = hist[d * HP + warp] + __popc(peers & lt_mask);
           kd[pos] = key;
@@ -358,6 +365,7 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restric
 
 // --------------------------------------------------------- a9 running median
 constexpr int kWalkThreads = 64;
+constexpr int kWalkQ = 1;        // 16-byte step words per walk iteration
 
 __device__ __forceinline__ int next_set(const uint32_t* bits, int p, int nwords) {
   int w = p >> 5;
@@ -428,33 +436,50 @@ k_walk(uint32_t* __restrict__ steps, int n_valid, int nc, int h) {
   uint32_t* st = steps + static_cast<long long>(p) * walk_stride(nc, h);
   const uint4* st4 = reinterpret_cast<const uint4*>(st);
   int size = 0, cur = -1, lt = 0;
+  // the stream is read kWalkQ 16-byte words (4 kWalkQ steps) per iteration,
+  // two iterations ahead of the walk
   const int n4 = n_total >> 2;
-  uint4 a = st4[0];
-  uint4 b = n4 > 1 ? st4[1] : make_uint4(0u, 0u, 0u, 0u);
-  for (int c = 0; c < n4; ++c) {
-    const uint4 nx = c + 2 < n4 ? st4[c + 2] : make_uint4(0u, 0u, 0u, 0u);
-    const uint32_t sw[4] = {a.x, a.y, a.z, a.w};
-    const int i0 = c << 2;
-    if (i0 < H) {
-      // steps building the first window (H is a multiple of 4)
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  uint4 a[kWalkQ], b[kWalkQ];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
-    } else {
-      uint32_t r[4];
+  for (int u = 0; u < kWalkQ; ++u) {
+    a[u] = u < n4 ? st4[u] : zero4;
+    b[u] = kWalkQ + u < n4 ? st4[kWalkQ + u] : zero4;
+  }
+  for (int c0 = 0; c0 < n4; c0 += kWalkQ) {
+    uint4 nx[kWalkQ];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        r[q] = 0u;
-        if (i0 - H + q >= nc) continue;
-        if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
-        const int upper = (size & 1) ? cur : next_set(bits, cur + 1, nwords);
-        if (upper < 0) { atomicExch(&g_detect_status, 3); return; }
-        r[q] = static_cast<uint32_t>(cur) | (static_cast<uint32_t>(upper) << 16);
+    for (int u = 0; u < kWalkQ; ++u) nx[u] = c0 + 2 * kWalkQ + u < n4 ? st4[c0 + 2 * kWalkQ + u] : zero4;
+#pragma unroll
+    for (int u = 0; u < kWalkQ; ++u) {
+      const int c = c0 + u;
+      if (c >= n4) break;
+      const uint32_t sw[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
+      const int i0 = c << 2;
+      if (i0 < H) {
+        // steps building the first window (H is a multiple of 4)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
+      } else {
+        uint32_t r[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          r[q] = 0u;
+          if (i0 - H + q >= nc) continue;
+          if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
+          const int upper = (size & 1) ? cur : next_set(bits, cur + 1, nwords);
+          if (upper < 0) { atomicExch(&g_detect_status, 3); return; }
+          r[q] = static_cast<uint32_t>(cur) | (static_cast<uint32_t>(upper) << 16);
+        }
+        reinterpret_cast<uint4*>(st)[c] = make_uint4(r[0], r[1], r[2], r[3]);
       }
-      reinterpret_cast<uint4*>(st)[c] = make_uint4(r[0], r[1], r[2], r[3]);
     }
-    a = b;
-    b = nx;
+#pragma unroll
+    for (int u = 0; u < kWalkQ; ++u) {
+      a[u] = b[u];
+      b[u] = nx[u];
+    }
   }
 }
 
@@ -1056,7 +1081,7 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
     OVRO_LAUNCH_CHECK();
   }
   {
-    const int threads = 512, W = threads / 32;
+    const int threads = 1024, W = threads / 32;      // one CTA per SM (shared memory): all 32 warps
     const size_t sm = (256 * (W + 1) + 32) * 4 + static_cast<size_t>(nc) * 12;
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
     // CTAs per SM (each CTA loops over pixels; the outputs do not depend on it)

@@ -201,7 +201,8 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
   __shared__ int n_home, n_rec;
   const int b = blockIdx.x, cb = blockIdx.y;
   const long long chan = ch0 + cb;
-  for (int i = threadIdx.x; i < 2 * band_h * P; i += blockDim.x) pre[i] = 0.0f;
+  for (int i = threadIdx.x; i < (2 * band_h * P) / 4; i += blockDim.x)
+    reinterpret_cast<float4*>(pre)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
   if (threadIdx.x == 0) n_home = 0;
   const ChanScale s = cs[chan];
@@ -221,11 +222,11 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
     // ---- prepare: one visibility per thread pair
     const int e = c0 + (threadIdx.x >> 1);
     const bool valid = e < e1;
-    int bl = 0, cc = 0, off = 0;
+    GridEntry en{};
+    if (valid) en = entries[e];
+    int cc = 0, off = 0;
     bool in = false;
     if (valid) {
-      const GridEntry en = entries[e];
-      bl = en.bl;
       long long pc;
       if (!fast_rint_prod(axis ? en.dyh : en.dxh, axis ? en.dyl : en.dxl, s, &pc)) {
         const Baseline B = base[en.cross];           // FP64 product of the definition
@@ -248,7 +249,7 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
     // Stokes I = (XX + YY) / 2: XX on the even thread, YY on the odd one
     int sr = 0, si = 0;
     if (use) {
-      const int4 q = __ldg(vis4 + (chan * n_bl + bl) * 2 + axis);
+      const int4 q = __ldg(vis4 + (chan * n_bl + en.bl) * 2 + axis);
       sr = axis ? q.z : q.x;
       si = axis ? q.w : q.y;
     }
