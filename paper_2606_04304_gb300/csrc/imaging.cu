@@ -161,7 +161,7 @@ struct GridEntry {
 __host__ __device__ constexpr int band_pitch(int g) { return (g + g / 16) + ((7 - (g + g / 16) % 16) + 16) % 16; }
 
 // Gridding records per chunk (one per prepared visibility).
-constexpr int kRecMax = 256;
+constexpr int kRecMax = 512;
 constexpr int kWuStride = 5;       // float2 per record: (w_t, w_{t+4}), t < 4; odd word stride
 constexpr int kWvStride = 9;       // floats per record: w_t, t < 8 (w_7 = 0)
 
@@ -180,7 +180,7 @@ __host__ __device__ constexpr int planar_pitch(int g) { return g + 4; }
 // its own bank) and in the interleaved, padded FFT layout afterwards; the
 // first FFT pass converts.
 template <int LOG2G, int S>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_off,
             const int32_t* __restrict__ vis, long long n_bl, const Baseline* __restrict__ base,
             const ChanScale* __restrict__ cs, const float* __restrict__ tab,
@@ -446,7 +446,9 @@ ImgPlan make_plan(int n_ant, int n_chan, int n, int storage) {
   p.storage = storage;
   p.g = kPad * n;
   p.log2g = ilog2(p.g);
-  p.band_h = 8192 / p.g < p.g ? 8192 / p.g : p.g;    // 8192 complex values per band
+  // 16384 complex values per band: one CTA of 1024 threads per SM, and each
+  // 7-row footprint spills into a second band only (7 - 1) / band_h of the time
+  p.band_h = 16384 / p.g < p.g ? 16384 / p.g : p.g;
   p.n_bands = p.g / p.band_h;
   p.n_cross = static_cast<long long>(n_ant) * (n_ant - 1) / 2;
   const long long h_bytes = 8LL * p.g * n;           // half-transformed grid of one channel
