@@ -123,6 +123,26 @@ __device__ __forceinline__ long long exact_rint_prod(double x, float xh, float x
   return __double2ll_rn(__dmul_rn(x, s.s));
 }
 
+// The same decision in 32-bit integers (|x s| < 2^21 is required anyway).
+__device__ __forceinline__ bool fast_rint_prod32(float xh, float xl, const ChanScale& s, int* p) {
+  const float hi = __fmul_rn(xh, s.sh);
+  if (!(fabsf(hi) < 2097152.0f)) return false;
+  const float e = __fmaf_rn(xh, s.sh, -hi);
+  const float t = __fmaf_rn(xh, s.sl, __fmaf_rn(xl, s.sh, e));
+  const float n = rintf(hi);
+  const float f = __fadd_rn(hi - n, t);
+  if (fabsf(fabsf(f) - 0.5f) <= 2.5e-7f) return false;
+  *p = __float2int_rn(n) + (f > 0.5f ? 1 : 0) - (f < -0.5f ? 1 : 0);   // n is integral, |n| < 2^21
+  return true;
+}
+
+static_assert(kQ == 1024, "centre_cell32 divides by shifting");
+__device__ __forceinline__ void centre_cell32(int p, int& c0, int& off) {
+  const int c = (abs(p) + kQ / 2) >> 10;
+  c0 = p < 0 ? -c : c;
+  off = p - c0 * kQ;
+}
+
 __device__ __forceinline__ void centre_cell(long long p, int& c0, int& off) {
   const long long ap = p < 0 ? -p : p;
   long long c = (ap + kQ / 2) / kQ;
@@ -208,7 +228,7 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
   const ChanScale s = cs[chan];
   const int row0 = b * band_h;
   const int cmax = G / 2 - kHalfSup - 1;
-  const long long lim = static_cast<long long>(cmax + 1) * kQ;
+  const int lim = (cmax + 1) * kQ;                     // < 2^21
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
   const int axis = threadIdx.x & 1;                  // 0: u, 1: v
   const int chunk = blockDim.x >> 1;
@@ -227,13 +247,14 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
     int cc = 0, off = 0;
     bool in = false;
     if (valid) {
-      long long pc;
-      if (!fast_rint_prod(axis ? en.dyh : en.dxh, axis ? en.dyl : en.dxl, s, &pc)) {
+      int pc;
+      if (!fast_rint_prod32(axis ? en.dyh : en.dxh, axis ? en.dyl : en.dxl, s, &pc)) {
         const Baseline B = base[en.cross];           // FP64 product of the definition
-        pc = __double2ll_rn(__dmul_rn(axis ? B.dy : B.dx, s.s));
+        const long long pl = __double2ll_rn(__dmul_rn(axis ? B.dy : B.dx, s.s));
+        pc = static_cast<int>(pl > lim ? lim : (pl < -lim ? -lim : pl));
       }
       if (pc > -lim && pc < lim) {
-        centre_cell(pc, cc, off);
+        centre_cell32(pc, cc, off);
         in = cc <= cmax && cc >= -cmax;
       }
     }
