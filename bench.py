@@ -368,6 +368,31 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e = float(t.item())
     h2d = volt_h.nbytes
+
+    # ---- the same X-engine contraction on the plain FP32 path (same int8
+    # spectra, same visibilities): device time per step of each path
+    xeng_cmp = None
+    if world == 1:
+        qx = torch.empty(ovro.fine_elements(cfg.nfft, cfg.n_time, cfg.n_input), dtype=torch.int8, device=dev)
+        ovro.upchan(volt, cfg.nfft, out_q=qx)
+        outs, times = {}, {}
+        for name, md in (("int8_tc", ovro.XENG_TC), ("fp32_simt", ovro.XENG_FP32)):
+            outs[name] = ovro.correlate(qx, cfg.n_ant, n_chan, K, md)
+            ovro.correlate(qx, cfg.n_ant, n_chan, K, md, out=outs[name])
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                ovro.correlate(qx, cfg.n_ant, n_chan, K, md, out=outs[name])
+            b.record(stream)
+            torch.cuda.synchronize()
+            times[name] = a.elapsed_time(b) / 3
+        same = bool(torch.equal(outs["int8_tc"], outs["fp32_simt"]))
+        xeng_cmp = {"workload": "one step's int8 spectra (8192 channels, K = 29, 352 antennas)",
+                    "int8_tc_ms": times["int8_tc"], "fp32_simt_ms": times["fp32_simt"],
+                    "int8_tc_vis_per_s": vis_per_step / (times["int8_tc"] * 1e-3),
+                    "fp32_simt_vis_per_s": vis_per_step / (times["fp32_simt"] * 1e-3),
+                    "speedup": times["fp32_simt"] / times["int8_tc"], "bit_identical": same}
+        del qx, outs
     d2h = int(len(c2)) * ovro.CANDIDATE_DTYPE.itemsize
 
     if rank == 0:
@@ -414,6 +439,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "candidates_per_step": int(len(cands)),
+            "xeng_int8_tc_vs_fp32": xeng_cmp,
             "wall_s_timed": t_wall,
         }
         if world == 1 and not args.no_cpu_baseline:
