@@ -123,18 +123,41 @@ def _taps(p: np.ndarray, n: int, q: int):
     return c0, off, inside
 
 
-def grid_channel(vis_chan, pos, nu_hz, n, cell, table, q=OVERSAMPLE):
+def uv_length_wavelengths(pos, a, b, nu_hz):
+    """Baseline length in wavelengths, L * (nu / c) with L = sqrt(dx^2 + dy^2)
+    (planar array, zenith phase centre)."""
+    dx = pos[a, 0] - pos[b, 0]
+    dy = pos[a, 1] - pos[b, 1]
+    return np.sqrt(dx * dx + dy * dy) * (float(nu_hz) / C_LIGHT)
+
+
+def grid_channel(vis_chan, pos, nu_hz, n, cell, table, q=OVERSAMPLE, gains_chan=None, uv_range=None):
     """FP64 uv grid G[kv][ku] (n = G cells a side) of one channel, plus the number
-    of gridded visibilities (mirrors included) and of dropped baselines."""
+    of gridded visibilities (mirrors included) and of dropped baselines.
+
+    gains_chan: optional complex [2 n_ant] corrections applied per polarisation
+    before Stokes I; uv_range: optional (uv_min, uv_max) in wavelengths, keeping
+    baselines with uv_min <= length < uv_max (the baseline cuts of the near-field
+    test, Section 2.5.1); baselines outside it are dropped like baselines off the grid."""
     n_ant = pos.shape[0]
     a, b, idx = _cross_pairs(n_ant)
-    vi = stokes_i(vis_chan)[idx]
+    if gains_chan is None:
+        vi = stokes_i(vis_chan)[idx]
+    else:
+        g = np.asarray(gains_chan, dtype=np.complex128)
+        xx = vis_chan[idx, 0, 0] + 1j * vis_chan[idx, 0, 1].astype(np.float64)
+        yy = vis_chan[idx, 3, 0] + 1j * vis_chan[idx, 3, 1].astype(np.float64)
+        vi = (g[2 * a] * np.conj(g[2 * b]) * xx + g[2 * a + 1] * np.conj(g[2 * b + 1]) * yy) / 2.0
     s = cells_per_metre(nu_hz, n, cell)
     u = (pos[a, 0] - pos[b, 0]) * s
     v = (pos[a, 1] - pos[b, 1]) * s
     pu = np.rint(u * q).astype(np.int64)
     pv = np.rint(v * q).astype(np.int64)
     keep = np.ones(a.size, dtype=bool)
+    if uv_range is not None:
+        lam = uv_length_wavelengths(pos, a, b, nu_hz)
+        lo, hi = uv_range
+        keep &= (lam >= lo) & (lam < hi)
     sides = []
     for sign in (1, -1):
         cu, ou, iu = _taps(sign * pu, n, q)
@@ -175,14 +198,17 @@ def image_from_grid(G, n_grid, n, cell, corr):
     return img
 
 
-def dirty_images(vis, pos, freqs_hz, n, cell, channels=None):
-    """vis: [n_chan][n_bl][4][2] int -> FP64 images [n_sel][N][N] and stats."""
+def dirty_images(vis, pos, freqs_hz, n, cell, channels=None, gains=None, uv_range=None):
+    """vis: [n_chan][n_bl][4][2] int -> FP64 images [n_sel][N][N] and stats.
+    gains: optional complex [n_chan][2 n_ant] corrections; uv_range: optional
+    (uv_min, uv_max) in wavelengths (see grid_channel)."""
     table = kernel_table()
     corr = grid_correction(table, n)
     chans = range(vis.shape[0]) if channels is None else channels
     imgs, ngrid, ndrop = [], [], []
     for c in chans:
-        G, ng, nd = grid_channel(vis[c], pos, freqs_hz[c], PAD * n, cell, table)
+        G, ng, nd = grid_channel(vis[c], pos, freqs_hz[c], PAD * n, cell, table,
+                                 gains_chan=None if gains is None else gains[c], uv_range=uv_range)
         imgs.append(image_from_grid(G, ng, n, cell, corr))
         ngrid.append(ng)
         ndrop.append(nd)

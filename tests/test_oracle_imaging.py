@@ -147,3 +147,87 @@ def test_horizon_mask():
     m = I.horizon_mask(64, 2.0 / 64)
     assert m[32, 32] and not m[0, 0] and not m[32, 0]
     assert abs(m.sum() / 64 ** 2 - math.pi / 4) < 0.02
+
+
+# ---- calibration corrections and uv-range selection (Sections 2.2, 2.5.1)
+def _rand_vis(g, pos, n_chan=1, scale=100.0):
+    return g.normal(size=(n_chan, X.n_baselines(pos.shape[0]), 4, 2)) * scale
+
+
+def test_unit_gains_and_open_uv_range_change_nothing():
+    pos = _small_array(10, 50.0, 9)
+    n, cell, nu = 64, 0.02, np.array([60e6])
+    vis = _rand_vis(np.random.default_rng(1), pos)
+    ref, ng, nd = I.dirty_images(vis, pos, nu, n, cell)
+    ones = np.ones((1, 2 * pos.shape[0]), np.complex128)
+    got, ng2, nd2 = I.dirty_images(vis, pos, nu, n, cell, gains=ones, uv_range=(0.0, np.inf))
+    assert np.array_equal(got, ref) and np.array_equal(ng, ng2) and np.array_equal(nd, nd2)
+
+
+def test_common_gain_scales_image_by_its_power():
+    # V' = g conj(g) V = |g|^2 V for every baseline
+    pos = _small_array(10, 50.0, 9)
+    n, cell, nu = 64, 0.02, np.array([60e6])
+    vis = _rand_vis(np.random.default_rng(2), pos)
+    gval = 0.6 - 1.3j
+    ref, _, _ = I.dirty_images(vis, pos, nu, n, cell)
+    got, _, _ = I.dirty_images(vis, pos, nu, n, cell, gains=np.full((1, 2 * pos.shape[0]), gval))
+    assert np.allclose(got, abs(gval) ** 2 * ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_gains_act_per_polarisation():
+    # corrections of 2 on every X input and 1 on every Y input: I' = (4 XX + YY) / 2,
+    # the image of the visibilities with XX scaled by 4
+    pos = _small_array(10, 50.0, 9)
+    n, cell, nu = 64, 0.02, np.array([60e6])
+    vis = _rand_vis(np.random.default_rng(3), pos)
+    gains = np.ones((1, 2 * pos.shape[0]), np.complex128)
+    gains[0, 0::2] = 2.0
+    got, _, _ = I.dirty_images(vis, pos, nu, n, cell, gains=gains)
+    v4 = vis.copy()
+    v4[:, :, 0, :] *= 4.0
+    ref, _, _ = I.dirty_images(v4, pos, nu, n, cell)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_phase_gains_move_a_source_to_its_pixel():
+    # a source at the phase centre with corrections c_i = exp(-2 pi i (x_i l0 + y_i m0) / lambda)
+    # has V'_ab = exp(-2 pi i (u l0 + v m0)): the image peaks at (l0, m0) with value 1
+    pos = _small_array()
+    n, cell, nu = 64, 0.02, 60e6
+    r0, c0 = n // 2 + 7, n // 2 - 4
+    l0, m0 = (c0 - n // 2) * cell, (r0 - n // 2) * cell
+    vis = _point_source_vis(pos, nu, 0.0, 0.0)[None]
+    lam = I.C_LIGHT / nu
+    ph = np.exp(-2j * np.pi * (pos[:, 0] * l0 + pos[:, 1] * m0) / lam)
+    gains = np.repeat(ph, 2)[None]                       # inputs 2a (X) and 2a+1 (Y)
+    img, _, _ = I.dirty_images(vis, pos, np.array([nu]), n, cell, gains=gains)
+    assert np.unravel_index(np.argmax(img[0]), img[0].shape) == (r0, c0)
+    assert abs(img[0][r0, c0] - 1.0) < 2e-3
+
+
+def test_uv_length_closed_form():
+    pos = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])
+    nu = I.C_LIGHT / 2.5                                 # lambda = 2.5 m: 5 m = 2 wavelengths
+    assert I.uv_length_wavelengths(pos, np.array([0]), np.array([1]), nu)[0] == pytest.approx(2.0, rel=1e-15)
+
+
+def test_uv_range_keeps_exactly_the_selected_baselines():
+    # the cut image equals brute-force DFT imaging of the baselines whose length
+    # lies in [uv_min, uv_max), and the counts follow
+    pos = _small_array(10, 50.0, 9)
+    n, cell, nu = 64, 0.02, 60e6
+    vis = _rand_vis(np.random.default_rng(5), pos)
+    a, b, idx = I._cross_pairs(pos.shape[0])
+    lam = I.uv_length_wavelengths(pos, a, b, nu)
+    srt = np.sort(lam)
+    lo, hi = (srt[10] + srt[11]) / 2, (srt[30] + srt[31]) / 2          # between baseline lengths
+    sel = np.nonzero((lam >= lo) & (lam < hi))[0]
+    assert sel.size == 20
+    img, ng, nd = I.dirty_images(vis, pos, np.array([nu]), n, cell, uv_range=(lo, hi))
+    assert ng[0] == 2 * sel.size and nd[0] == a.size - sel.size
+    ref = I.dft_image(vis[0], pos, nu, n, cell, baselines=sel)
+    assert np.max(np.abs(img[0] - ref)) < 1e-3 * np.max(np.abs(ref))
+    # an empty range grids nothing
+    img0, ng0, _ = I.dirty_images(vis, pos, np.array([nu]), n, cell, uv_range=(hi, lo))
+    assert ng0[0] == 0 and not img0.any()
