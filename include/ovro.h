@@ -188,6 +188,30 @@ int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
                     double cell_dircos, int storage, float* d_img,
                     int32_t* d_n_gridded_or_null, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Imaging with calibration corrections and a baseline (uv-range) selection.
+ *
+ * Section 2.2 calibrates the visibilities (per-antenna gains and a bandpass)
+ * before imaging, and Section 2.5.1 re-images with baseline-length cuts to
+ * test for near-field emitters.  d_gains_or_null: complex64 (float2, 8-byte
+ * aligned) [n_chan][2 n_ant] multiplicative corrections c per input and
+ * channel (so a bandpass is included): XX' = c_{2a} conj(c_{2b}) XX,
+ * YY' = c_{2a+1} conj(c_{2b+1}) YY, Stokes I = (XX' + YY') / 2, in FP32 on the
+ * device (NULL: the exact integer Stokes I of ovro_grid_image).  Baselines are
+ * kept when uv_min_lambda <= L nu / c < uv_max_lambda, L = sqrt(dx^2 + dy^2)
+ * metres, decided in FP64 per channel (uv_max_lambda <= 0: no upper cut);
+ * baselines outside are dropped and not counted.  Otherwise as ovro_grid_image
+ * (same workspace size). */
+typedef struct {
+  int storage;                    /* OVRO_STORE_* */
+  const void* d_gains_or_null;    /* complex64 [n_chan][2 n_ant] or NULL */
+  double uv_min_lambda;           /* >= 0 */
+  double uv_max_lambda;           /* <= 0: none */
+} ovro_grid_options;
+int ovro_grid_image_ex(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
+                       const double* h_chan_freq_hz, int n_chan, int image_size, double cell_dircos,
+                       const ovro_grid_options* options, float* d_img, int32_t* d_n_gridded_or_null,
+                       void* d_ws, size_t ws_bytes, void* stream);
+
 /* a5 on its own: p = rint(u Q), Q = 1024, the rounded uv position in 1/1024
  * cell of the padded (2 image_size) grid of every cross baseline (a < b, row-major order) in every channel,
  * int32 [n_chan][n_cross] (saturated at +-2^30).  The FP64 product of the

@@ -63,6 +63,7 @@ struct Baseline {
 
 struct ChanScale {
   double s;          // s_nu * Q
+  double nu_c;       // nu / c (wavelengths per metre)
   float sh, sl;      // float-float split of s
 };
 
@@ -94,6 +95,7 @@ __global__ void k_chan_scale(const double* __restrict__ freq, int n_chan, int n,
   const double s = freq[f] / (kCLight * du);
   ChanScale c;
   c.s = s * static_cast<double>(kQ);          // exact: Q is a power of two
+  c.nu_c = freq[f] / kCLight;
   c.sh = static_cast<float>(c.s);
   c.sl = static_cast<float>(c.s - static_cast<double>(c.sh));
   out[f] = c;
@@ -143,14 +145,6 @@ __device__ __forceinline__ void centre_cell32(int p, int& c0, int& off) {
   off = p - c0 * kQ;
 }
 
-__device__ __forceinline__ void centre_cell(long long p, int& c0, int& off) {
-  const long long ap = p < 0 ? -p : p;
-  long long c = (ap + kQ / 2) / kQ;
-  if (p < 0) c = -c;
-  c0 = static_cast<int>(c);
-  off = static_cast<int>(p - c * kQ);
-}
-
 // a5 on its own: rounded positions p_u, p_v (1/Q cells) of every cross baseline.
 __global__ void k_uvw(const Baseline* __restrict__ base, int n_cross, const ChanScale* __restrict__ cs,
                       int32_t* __restrict__ pu, int32_t* __restrict__ pv) {
@@ -169,9 +163,19 @@ __global__ void k_uvw(const Baseline* __restrict__ base, int n_cross, const Chan
 
 struct GridEntry {
   int bl;            // baseline index in the visibility record
-  int cross;         // cross-baseline index (for the FP64 fallback)
-  int pad0, pad1;
+  int cross;         // cross-baseline index (FP64 fallback, baseline length)
+  int a;             // antennas a < b
+  int bf;            // b | kCheckUv when the uv range must be decided per channel
   float dxh, dxl, dyh, dyl;
+};
+constexpr int kCheckUv = 1 << 16;
+
+// Calibration and baseline-selection options of one gridding call.
+struct GridOpts {
+  const float2* gains;      // [n_chan][n_input] corrections or nullptr
+  int n_input;
+  const double* blen;       // [n_cross] baseline lengths, metres (FP64)
+  double uv_min, uv_max;    // wavelengths, [uv_min, uv_max)
 };
 
 // Row pitch of a shared-memory grid band: G + G/16 pad slots, rounded so the
@@ -199,13 +203,13 @@ __host__ __device__ constexpr int planar_pitch(int g) { return g + 4; }
 // band is held as two real planes during gridding (every atomic of a warp hits
 // its own bank) and in the interleaved, padded FFT layout afterwards; the
 // first FFT pass converts.
-template <int LOG2G, int S>
+template <int LOG2G, int S, bool CAL>
 __global__ void __launch_bounds__(1024)
 k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_off,
             const int32_t* __restrict__ vis, long long n_bl, const Baseline* __restrict__ base,
             const ChanScale* __restrict__ cs, const float* __restrict__ tab,
             const float2* __restrict__ tw_g, int ch0, int n_img, int band_h,
-            int* __restrict__ kept, void* __restrict__ h, float* __restrict__ hs) {
+            int* __restrict__ kept, void* __restrict__ h, float* __restrict__ hs, GridOpts opt) {
   constexpr int G = 1 << LOG2G;
   constexpr int LDP = band_pitch(G);
   constexpr int P = planar_pitch(G);
@@ -257,6 +261,11 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
         centre_cell32(pc, cc, off);
         in = cc <= cmax && cc >= -cmax;
       }
+      // baselines straddling an edge of the uv range: decide in FP64, L * (nu / c)
+      if (CAL && axis == 0 && (en.bf & kCheckUv)) {
+        const double lam = __dmul_rn(opt.blen[en.cross], s.nu_c);
+        in = in && lam >= opt.uv_min && lam < opt.uv_max;
+      }
     }
     const int cc_o = __shfl_xor_sync(full, cc, 1);
     const int in_o = __shfl_xor_sync(full, in ? 1 : 0, 1);   // every lane takes part
@@ -267,15 +276,35 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
     const int ku0 = G / 2 + cu - kHalfSup;
     if (keep && axis && kv_home >= row0 && kv_home < row0 + band_h) ++my_home;
     const bool use = keep && kv_rel + kSupport > 0 && kv_rel < band_h;
-    // Stokes I = (XX + YY) / 2: XX on the even thread, YY on the odd one
-    int sr = 0, si = 0;
-    if (use) {
-      const int4 q = __ldg(vis4 + (chan * n_bl + en.bl) * 2 + axis);
-      sr = axis ? q.z : q.x;
-      si = axis ? q.w : q.y;
+    // Stokes I = (XX + YY) / 2: XX on the even thread, YY on the odd one;
+    // exact integer sums, or with the calibration corrections c_a conj(c_b)
+    // applied per polarisation in FP32
+    float fr, fi;
+    if (!CAL || opt.gains == nullptr) {
+      int sr = 0, si = 0;
+      if (use) {
+        const int4 q = __ldg(vis4 + (chan * n_bl + en.bl) * 2 + axis);
+        sr = axis ? q.z : q.x;
+        si = axis ? q.w : q.y;
+      }
+      sr += __shfl_xor_sync(full, sr, 1);
+      si += __shfl_xor_sync(full, si, 1);
+      fr = static_cast<float>(sr);
+      fi = static_cast<float>(si);
+    } else {
+      float pr = 0.f, pi = 0.f;
+      if (use) {
+        const int4 q = __ldg(vis4 + (chan * n_bl + en.bl) * 2 + axis);
+        const float vr = static_cast<float>(axis ? q.z : q.x), vi = static_cast<float>(axis ? q.w : q.y);
+        const float2* gc = opt.gains + chan * opt.n_input;
+        const float2 ca = __ldg(gc + 2 * en.a + axis), cbb = __ldg(gc + 2 * (en.bf & 0xffff) + axis);
+        const float gr = ca.x * cbb.x + ca.y * cbb.y, gi = ca.y * cbb.x - ca.x * cbb.y;
+        pr = gr * vr - gi * vi;
+        pi = gr * vi + gi * vr;
+      }
+      fr = pr + __shfl_xor_sync(full, pr, 1);
+      fi = pi + __shfl_xor_sync(full, pi, 1);
     }
-    sr += __shfl_xor_sync(full, sr, 1);
-    si += __shfl_xor_sync(full, si, 1);
     const unsigned m = __ballot_sync(full, use) & 0x55555555u;
     int base_slot = 0;
     if (lane == 0 && m) base_slot = atomicAdd(&n_rec, __popc(m));
@@ -292,8 +321,7 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
 #pragma unroll
         for (int t = 0; t < kSupport; ++t)
           if ((ku0 + t) & 1) w[t] = -w[t];
-        r_hdr[slot] = make_float4(0.5f * static_cast<float>(sr), -0.5f * static_cast<float>(si),
-                                  __int_as_float(kv_rel * P + ku0), __int_as_float(kv_rel));
+        r_hdr[slot] = make_float4(0.5f * fr, -0.5f * fi, __int_as_float(kv_rel * P + ku0), __int_as_float(kv_rel));
 #pragma unroll
         for (int t = 0; t < 4; ++t) r_wu[slot * kWuStride + t] = make_float2(w[t], w[t + 4]);
       } else {
@@ -499,6 +527,7 @@ struct ImgWs {
   int* kept;
   int* band_off;
   GridEntry* entries;
+  double* blen;      // [n_cross] baseline lengths (metres)
   void* h;           // [batch][G][N] complex in the storage format
   float* hs;         // [batch][G] row scales (FP16 storage)
 };
@@ -524,6 +553,7 @@ ImgWs carve_img(void* ws, size_t bytes, const ImgPlan& p, int n_ant, int n_chan,
   w.kept = c.take<int>(n_chan);
   w.band_off = c.take<int>(p.n_bands + 1);
   w.entries = c.take<GridEntry>(entry_capacity(p));
+  w.blen = c.take<double>(p.n_cross > 0 ? p.n_cross : 1);
   w.h = c.take<float2>(static_cast<size_t>(p.batch) * p.g * p.n);
   w.hs = c.take<float>(static_cast<size_t>(p.batch) * p.g);
   *need = c.used;
@@ -532,8 +562,16 @@ ImgWs carve_img(void* ws, size_t bytes, const ImgPlan& p, int n_ant, int n_chan,
 
 // Host: which baselines can touch which band of grid rows for any channel of
 // the call (u, v scale linearly with frequency; one cell of margin).
+// Baseline length in metres, sqrt(dx^2 + dy^2) in FP64 (host code is built
+// without FMA contraction, so this rounds like the definition).
+double baseline_length(const double* ant, int a, int b) {
+  const double dx = ant[3 * a] - ant[3 * b], dy = ant[3 * a + 1] - ant[3 * b + 1];
+  const double x2 = dx * dx, y2 = dy * dy;
+  return std::sqrt(x2 + y2);
+}
+
 void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double* freq, int n_chan,
-                   double cell, std::vector<GridEntry>& out, std::vector<int>& off) {
+                   double cell, double uv_min, double uv_max, std::vector<GridEntry>& out, std::vector<int>& off) {
   const double du = 1.0 / (static_cast<double>(p.g) * cell);
   double fmin = freq[0], fmax = freq[0];
   for (int f = 1; f < n_chan; ++f) {
@@ -541,6 +579,8 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
     fmax = std::max(fmax, freq[f]);
   }
   const double s_lo = fmin / (kCLight * du), s_hi = fmax / (kCLight * du);   // cells per metre
+  const bool uv_cut = uv_min > 0.0 || std::isfinite(uv_max);
+  const double w_lo = fmin / kCLight, w_hi = fmax / kCLight;                  // wavelengths per metre
   const int cmax = p.g / 2 - kHalfSup - 1;
   std::vector<std::vector<GridEntry>> bands(p.n_bands);
   long long cross = 0;
@@ -551,6 +591,15 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
       const double v0 = std::min(dy * s_lo, dy * s_hi), v1 = std::max(dy * s_lo, dy * s_hi);
       // can the centre cell ever satisfy |c0| <= cmax?
       if (u0 > cmax + 1.5 || u1 < -cmax - 1.5 || v0 > cmax + 1.5 || v1 < -cmax - 1.5) continue;
+      // uv range: decided here when every channel of the call agrees (with a
+      // relative margin), per channel on the device otherwise
+      bool check = false;
+      if (uv_cut) {
+        const double L = baseline_length(ant, a, b);
+        const double l0 = L * w_lo, l1 = L * w_hi, eps = 1e-9;
+        if (l1 < uv_min * (1.0 - eps) || l0 >= uv_max * (1.0 + eps)) continue;      // always outside
+        check = !(l0 >= uv_min * (1.0 + eps) && l1 < uv_max * (1.0 - eps));       // not always inside
+      }
       int r_lo = p.g / 2 + static_cast<int>(std::floor(v0)) - 1 - kHalfSup;
       int r_hi = p.g / 2 + static_cast<int>(std::ceil(v1)) + 1 + kHalfSup;
       r_lo = std::max(r_lo, 0);
@@ -558,7 +607,8 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
       GridEntry e;
       e.bl = static_cast<int>(a * static_cast<long long>(n_ant) - static_cast<long long>(a) * (a - 1) / 2 + (b - a));
       e.cross = static_cast<int>(cross);
-      e.pad0 = e.pad1 = 0;
+      e.a = a;
+      e.bf = b | (check ? kCheckUv : 0);
       e.dxh = static_cast<float>(dx);
       e.dxl = static_cast<float>(dx - static_cast<double>(e.dxh));
       e.dyh = static_cast<float>(dy);
@@ -575,20 +625,22 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
 }
 
 template <int L, int S>
-int launch_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long n_bl, int ch0, int nb,
-                 float* img, cudaStream_t st) {
+int launch_bands(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int32_t* vis, long long n_bl, int ch0,
+                 int nb, float* img, cudaStream_t st) {
   constexpr int G = 1 << L;
   constexpr int LDP = band_pitch(G);
   {
     const size_t sm = static_cast<size_t>(p.band_h) * LDP * sizeof(float2) + G * sizeof(float2) +
                       kRecMax * (sizeof(float4) + kWuStride * sizeof(float2) + kWvStride * sizeof(float));
-    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid_rows<L, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sm)));
+    // calibration corrections or a uv range select the variant that applies them
+    const bool cal = o.gains != nullptr || o.uv_min > 0.0 || std::isfinite(o.uv_max);
+    auto kern = cal ? k_grid_rows<L, S, true> : k_grid_rows<L, S, false>;
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
     const int threads = p.band_h * G / 16;
     dim3 grid(p.n_bands, nb);
     OVRO_PROF("k_grid_rows", st);
-    k_grid_rows<L, S><<<grid, threads, sm, st>>>(w.entries, w.band_off, vis, n_bl, w.base, w.cs, w.tab, w.tw, ch0,
-                                                 p.n, p.band_h, w.kept, w.h, w.hs);
+    kern<<<grid, threads, sm, st>>>(w.entries, w.band_off, vis, n_bl, w.base, w.cs, w.tab, w.tw, ch0, p.n, p.band_h,
+                                    w.kept, w.h, w.hs, o);
     OVRO_LAUNCH_CHECK();
   }
   {
@@ -606,32 +658,33 @@ int launch_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long
 }
 
 template <int L>
-int launch_storage(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long n_bl, int ch0, int nb,
-                   float* img, cudaStream_t st) {
+int launch_storage(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int32_t* vis, long long n_bl, int ch0,
+                   int nb, float* img, cudaStream_t st) {
   switch (p.storage) {
-    case kStoreF32: return launch_bands<L, kStoreF32>(p, w, vis, n_bl, ch0, nb, img, st);
-    case kStoreBF16: return launch_bands<L, kStoreBF16>(p, w, vis, n_bl, ch0, nb, img, st);
-    case kStoreF16: return launch_bands<L, kStoreF16>(p, w, vis, n_bl, ch0, nb, img, st);
+    case kStoreF32: return launch_bands<L, kStoreF32>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case kStoreBF16: return launch_bands<L, kStoreBF16>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case kStoreF16: return launch_bands<L, kStoreF16>(p, w, o, vis, n_bl, ch0, nb, img, st);
     default: return OVRO_ERR_INVALID_ARG;
   }
 }
 
-int run_bands(const ImgPlan& p, const ImgWs& w, const int32_t* vis, long long n_bl, int ch0, int nb, float* img,
-              cudaStream_t st) {
+int run_bands(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int32_t* vis, long long n_bl, int ch0,
+              int nb, float* img, cudaStream_t st) {
   switch (p.log2g) {
-    case 5: return launch_storage<5>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 6: return launch_storage<6>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 7: return launch_storage<7>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 8: return launch_storage<8>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 9: return launch_storage<9>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 10: return launch_storage<10>(p, w, vis, n_bl, ch0, nb, img, st);
-    case 11: return launch_storage<11>(p, w, vis, n_bl, ch0, nb, img, st);
+    case 5: return launch_storage<5>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case 6: return launch_storage<6>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case 7: return launch_storage<7>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case 8: return launch_storage<8>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case 9: return launch_storage<9>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case 10: return launch_storage<10>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case 11: return launch_storage<11>(p, w, o, vis, n_bl, ch0, nb, img, st);
     default: return OVRO_ERR_UNSUPPORTED;
   }
 }
 
 int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_ant,
-                  const double* h_freq, int n_chan, double cell, cudaStream_t st) {
+                  const double* h_freq, int n_chan, double cell, cudaStream_t st,
+                  double uv_min = 0.0, double uv_max = HUGE_VAL) {
   const KernelTables& kt = kernel_tables();
   std::vector<double> corr;
   grid_correction(p.n, p.g, corr);
@@ -639,8 +692,15 @@ int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_a
   for (int i = 0; i < p.n; ++i) inv[i] = static_cast<float>(1.0 / corr[i]);
   std::vector<GridEntry> entries;
   std::vector<int> off;
-  build_entries(p, n_ant, h_ant, h_freq, n_chan, cell, entries, off);
+  build_entries(p, n_ant, h_ant, h_freq, n_chan, cell, uv_min, uv_max, entries, off);
   if (static_cast<long long>(entries.size()) > entry_capacity(p)) return OVRO_ERR_CAPACITY;
+  std::vector<double> blen(p.n_cross > 0 ? p.n_cross : 1, 0.0);
+  {
+    long long x = 0;
+    for (int a = 0; a < n_ant; ++a)
+      for (int b = a + 1; b < n_ant; ++b) blen[x++] = baseline_length(h_ant, a, b);
+  }
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.blen, blen.data(), blen.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.tab, kt.table32.data(), kTabLen * sizeof(float),
                                 cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.inv_corr, inv.data(), p.n * sizeof(float), cudaMemcpyHostToDevice, st));
@@ -683,6 +743,8 @@ struct GridCtx {
   ImgWs w;
   int n_ant = 0, n_chan = 0;
   double cell = 0.0;
+  const float2* gains = nullptr;      // calibration corrections [n_chan][2 n_ant]
+  double uv_min = 0.0, uv_max = HUGE_VAL;
 };
 
 size_t grid_ctx_workspace(int n_ant, int n_chan, int image_size, int storage) {
@@ -695,7 +757,7 @@ size_t grid_ctx_workspace(int n_ant, int n_chan, int image_size, int storage) {
 }
 
 int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double cell, int storage, void* d_ws,
-                  size_t ws_bytes) {
+                  size_t ws_bytes, const void* d_gains, double uv_min, double uv_max) {
   if (!out) return OVRO_ERR_INVALID_ARG;
   *out = nullptr;
   if (n_ant <= 0 || n_chan <= 0 || !(cell > 0.0)) return OVRO_ERR_INVALID_ARG;
@@ -713,6 +775,9 @@ int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double c
   g->n_ant = n_ant;
   g->n_chan = n_chan;
   g->cell = cell;
+  g->gains = static_cast<const float2*>(d_gains);
+  g->uv_min = uv_min;
+  g->uv_max = uv_max;
   *out = g;
   return OVRO_OK;
 }
@@ -720,7 +785,8 @@ int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double c
 int grid_ctx_upload(GridCtx* g, const double* h_ant_enu_m, const double* h_chan_freq_hz, cudaStream_t st) {
   if (!g) return OVRO_ERR_INVALID_ARG;
   if (int e = validate(g->n_ant, h_ant_enu_m, h_chan_freq_hz, g->n_chan, g->p.n, g->cell)) return e;
-  return upload_common(g->p, g->w, g->n_ant, h_ant_enu_m, h_chan_freq_hz, g->n_chan, g->cell, st);
+  return upload_common(g->p, g->w, g->n_ant, h_ant_enu_m, h_chan_freq_hz, g->n_chan, g->cell, st, g->uv_min,
+                       g->uv_max);
 }
 
 int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_counts_or_null, cudaStream_t st) {
@@ -728,13 +794,19 @@ int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_
   if (reinterpret_cast<uintptr_t>(d_vis) % 16 != 0) return OVRO_ERR_INVALID_ARG;
   const ImgPlan& p = g->p;
   const long long n_bl = static_cast<long long>(g->n_ant) * (g->n_ant + 1) / 2;
+  GridOpts o;
+  o.gains = g->gains;
+  o.n_input = 2 * g->n_ant;
+  o.blen = g->w.blen;
+  o.uv_min = g->uv_min;
+  o.uv_max = g->uv_max;
   // channels per launch pair (at most the workspace's batch): every choice
   // gives the same images and counts
   auto all = [&](int batch) -> int {
     OVRO_CUDA_TRY(cudaMemsetAsync(g->w.kept, 0, g->n_chan * sizeof(int), st));
     for (int ch0 = 0; ch0 < g->n_chan; ch0 += batch) {
       const int nb = g->n_chan - ch0 < batch ? g->n_chan - ch0 : batch;
-      if (int e = run_bands(p, g->w, d_vis, n_bl, ch0, nb, d_img, st)) return e;
+      if (int e = run_bands(p, g->w, o, d_vis, n_bl, ch0, nb, d_img, st)) return e;
     }
     return OVRO_OK;
   };
@@ -778,14 +850,32 @@ int ovro_grid_image(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m,
                     const double* h_chan_freq_hz, int n_chan, int image_size, double cell_dircos,
                     int storage, float* d_img, int32_t* d_n_gridded_or_null, void* d_ws,
                     size_t ws_bytes, void* stream) {
+  ovro_grid_options o;
+  o.storage = storage;
+  o.d_gains_or_null = nullptr;
+  o.uv_min_lambda = 0.0;
+  o.uv_max_lambda = 0.0;
+  return ovro_grid_image_ex(d_vis, n_ant, h_ant_enu_m, h_chan_freq_hz, n_chan, image_size, cell_dircos, &o, d_img,
+                            d_n_gridded_or_null, d_ws, ws_bytes, stream);
+}
+
+int ovro_grid_image_ex(const int32_t* d_vis, int n_ant, const double* h_ant_enu_m, const double* h_chan_freq_hz,
+                       int n_chan, int image_size, double cell_dircos, const ovro_grid_options* opt, float* d_img,
+                       int32_t* d_n_gridded_or_null, void* d_ws, size_t ws_bytes, void* stream) {
   using namespace ovro;
-  if (!d_vis || !d_img) return OVRO_ERR_INVALID_ARG;
+  if (!d_vis || !d_img || !opt) return OVRO_ERR_INVALID_ARG;
   if (int e = validate(n_ant, h_ant_enu_m, h_chan_freq_hz, n_chan, image_size, cell_dircos)) return e;
+  const int storage = opt->storage;
   if (storage != OVRO_STORE_FP32 && storage != OVRO_STORE_BF16 && storage != OVRO_STORE_FP16)
     return OVRO_ERR_INVALID_ARG;
+  if (!(opt->uv_min_lambda >= 0.0) || std::isnan(opt->uv_max_lambda)) return OVRO_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_vis) % 16 != 0) return OVRO_ERR_INVALID_ARG;
+  if (opt->d_gains_or_null && reinterpret_cast<uintptr_t>(opt->d_gains_or_null) % 8 != 0) return OVRO_ERR_INVALID_ARG;
+  const double uv_max = opt->uv_max_lambda > 0.0 ? opt->uv_max_lambda : HUGE_VAL;
   GridCtx* g = nullptr;
-  if (int e = grid_ctx_init(&g, n_ant, n_chan, image_size, cell_dircos, storage, d_ws, ws_bytes)) return e;
+  if (int e = grid_ctx_init(&g, n_ant, n_chan, image_size, cell_dircos, storage, d_ws, ws_bytes,
+                            opt->d_gains_or_null, opt->uv_min_lambda, uv_max))
+    return e;
   cudaStream_t st = as_stream(stream);
   int e = grid_ctx_upload(g, h_ant_enu_m, h_chan_freq_hz, st);
   if (!e) e = grid_ctx_enqueue(g, d_vis, d_img, d_n_gridded_or_null, st);

@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -27,8 +28,11 @@ struct GridCtx;
 size_t grid_ctx_workspace(int n_ant, int n_chan, int image_size, int storage);
 // Plans one call's worth of channels; the workspace must stay bound to the context.
 // storage: OVRO_STORE_* format of the half-transformed grid between the passes.
+// d_gains: calibration corrections [n_chan][2 n_ant] (complex64) or nullptr;
+// baselines kept when uv_min <= length (wavelengths) < uv_max.
 int grid_ctx_init(GridCtx** out, int n_ant, int n_chan, int image_size, double cell, int storage, void* d_ws,
-                  size_t ws_bytes);
+                  size_t ws_bytes, const void* d_gains = nullptr, double uv_min = 0.0,
+                  double uv_max = HUGE_VAL);
 // Host lists and tables (pageable copies): once per geometry and frequency axis.
 int grid_ctx_upload(GridCtx* g, const double* h_ant_enu_m, const double* h_chan_freq_hz, cudaStream_t st);
 int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_counts_or_null, cudaStream_t st);

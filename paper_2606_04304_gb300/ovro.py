@@ -67,6 +67,7 @@ def _load() -> ctypes.CDLL:
         "ovro_grid_image_workspace_size": (S, [I, I, I, I]),
         "ovro_grid_image": (I, [P, I, P, P, I, I, D, I, P, P, P, S, P]),
         "ovro_uvw": (I, [P, I, P, I, I, D, P, P, P, S, P]),
+        "ovro_grid_image_ex": (I, [P, I, P, P, I, I, D, P, P, P, P, S, P]),
         "ovro_default_widths": (I, [P]),
         "ovro_detect_workspace_size": (S, [I, I, I, P]),
         "ovro_detect": (I, [P, I, I, D, I, P, P, P, P, I, P, P, S, P]),
@@ -220,10 +221,21 @@ def grid_image_workspace_size(n_ant: int, n_chan: int, image_size: int, storage:
     return _lib.ovro_grid_image_workspace_size(n_ant, n_chan, image_size, storage)
 
 
+class GridOptions(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int), ("d_gains_or_null", ctypes.c_void_p),
+                ("uv_min_lambda", ctypes.c_double), ("uv_max_lambda", ctypes.c_double)]
+
+
 def grid_image(vis: torch.Tensor, ant_enu_m, freqs_hz, image_size: int, cell: float,
                storage: int = STORE_FP32, out: Optional[torch.Tensor] = None,
-               ws: Optional[torch.Tensor] = None, want_counts: bool = False, stream=None):
-    """vis: int32 [n_chan][n_bl][4][2].  Returns float images [n_chan][N][N] (and counts)."""
+               ws: Optional[torch.Tensor] = None, want_counts: bool = False, stream=None,
+               gains: Optional[torch.Tensor] = None, uv_range=None):
+    """vis: int32 [n_chan][n_bl][4][2].  Returns float images [n_chan][N][N] (and counts).
+    gains: optional complex64 [n_chan][2 n_ant] calibration corrections on the GPU;
+    uv_range: optional (uv_min, uv_max) in wavelengths (uv_max <= 0 or inf: no upper cut)."""
+    if gains is not None or uv_range is not None:
+        return _grid_image_ex(vis, ant_enu_m, freqs_hz, image_size, cell, storage, out, ws, want_counts, stream,
+                              gains, uv_range)
     _cuda(vis, torch.int32, "vis")
     pos = _host(ant_enu_m, np.float64)
     fr = _host(freqs_hz, np.float64)
@@ -236,6 +248,31 @@ def grid_image(vis: torch.Tensor, ant_enu_m, freqs_hz, image_size: int, cell: fl
     _check("ovro_grid_image", _lib.ovro_grid_image(
         _ptr(vis), n_ant, pos.ctypes.data_as(ctypes.c_void_p), fr.ctypes.data_as(ctypes.c_void_p), n_chan,
         image_size, float(cell), storage, _ptr(img), _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)))
+    return (img, cnt) if want_counts else img
+
+
+def _grid_image_ex(vis, ant_enu_m, freqs_hz, image_size, cell, storage, out, ws, want_counts, stream, gains,
+                   uv_range):
+    _cuda(vis, torch.int32, "vis")
+    pos = _host(ant_enu_m, np.float64)
+    fr = _host(freqs_hz, np.float64)
+    n_ant, n_chan = pos.shape[0], fr.shape[0]
+    if gains is not None:
+        _cuda(gains, torch.complex64, "gains")
+        if tuple(gains.shape) != (n_chan, 2 * n_ant):
+            raise ValueError("gains must be complex64 [n_chan][2 n_ant]")
+    lo, hi = (0.0, 0.0) if uv_range is None else (float(uv_range[0]), float(uv_range[1]))
+    if not np.isfinite(hi):
+        hi = 0.0
+    opt = GridOptions(storage, None if gains is None else gains.data_ptr(), lo, hi)
+    img = out if out is not None else torch.empty((n_chan, image_size, image_size), dtype=torch.float32,
+                                                  device=vis.device)
+    cnt = torch.empty(n_chan, dtype=torch.int32, device=vis.device) if want_counts else None
+    need = grid_image_workspace_size(n_ant, n_chan, image_size, storage)
+    ws = ws if ws is not None and ws.numel() >= need else workspace(need, vis.device)
+    _check("ovro_grid_image_ex", _lib.ovro_grid_image_ex(
+        _ptr(vis), n_ant, pos.ctypes.data_as(ctypes.c_void_p), fr.ctypes.data_as(ctypes.c_void_p), n_chan,
+        image_size, float(cell), ctypes.byref(opt), _ptr(img), _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)))
     return (img, cnt) if want_counts else img
 
 
