@@ -18,6 +18,7 @@ from .workloads import (  # noqa: F401
     generate,
     make_config,
     pack_nibbles,
+    pfb_prototype,
     substream,
     splitmix64,
 )

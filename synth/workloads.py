@@ -179,6 +179,16 @@ def _quantise(x: np.ndarray) -> np.ndarray:
     return np.clip(q, -7, 7).astype(np.int8)
 
 
+def pfb_prototype(nfft: int, n_taps: int) -> np.ndarray:
+    """A P-tap polyphase-filter-bank prototype for N fine channels: a sinc one
+    fine channel wide under a Hann taper, P N coefficients, FP32.  An input for
+    the PFB upchannelizer option (any real P N coefficients are valid)."""
+    m = np.arange(nfft * n_taps, dtype=np.float64) + 0.5
+    t = m / nfft - n_taps / 2.0
+    taper = 0.5 - 0.5 * np.cos(2.0 * np.pi * m / (nfft * n_taps))
+    return (np.sinc(t) * taper).astype(np.float32)
+
+
 def pixel_dircos(row: int, col: int, image_size: int, cell: float):
     return (col - image_size // 2) * cell, (row - image_size // 2) * cell
 

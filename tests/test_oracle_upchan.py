@@ -144,3 +144,144 @@ def test_paper_channel_widths():
     f = synth.fine_freqs_hz([2400])
     assert f[1] - f[0] == pytest.approx(24_000.0 / 2400, rel=1e-9)
     assert f[1200] == synth.coarse_centre_hz(0)
+
+
+# ---------------------------------------------------------------- N = 2400 and other 3,5-smooth N
+def _direct_dft(z):
+    """X_k = sum_n z_n exp(-2 pi i k n / N) as a matrix product, the phase taken
+    from the exact integer (k n) mod N."""
+    n = z.shape[0]
+    kn = np.outer(np.arange(n), np.arange(n)) % n
+    return np.exp(-2j * np.pi * kn / n) @ z
+
+
+@pytest.mark.parametrize("nfft", [6, 10, 12, 30, 60, 96, 360, 2400])
+def test_mixed_radix_matches_direct_dft(nfft):
+    # the library FFT of a 2^a 3^b 5^c length against the DFT summed directly
+    g = np.random.default_rng(nfft)
+    re = g.integers(-8, 8, (2 * nfft + 3, 2))
+    im = g.integers(-8, 8, (2 * nfft + 3, 2))
+    X = U.upchannelize(_bytes_from(re, im), nfft)                       # [N][in][K]
+    z = (re + 1j * im)[: 2 * nfft].reshape(2, nfft, 2)
+    for s in range(2):
+        for i in range(2):
+            d = np.fft.fftshift(_direct_dft(z[s, :, i]))
+            assert np.max(np.abs(X[:, i, s] - d)) < 1e-9 * nfft * 8
+
+
+@pytest.mark.parametrize("nfft", [12, 2400])
+@pytest.mark.parametrize("quarter", [0, 1, 3])
+def test_2400_pure_tone(nfft, quarter):
+    a, b = -7, 2
+    v = _rotating_tone(2 * nfft, 1, quarter, a, b)
+    X = U.upchannelize(v, nfft)
+    kp = (quarter * nfft // 4 + nfft // 2) % nfft
+    assert abs(X[kp, 0, 0] - nfft * (a + 1j * b)) < 1e-9 * nfft
+    assert np.delete(np.abs(X[:, 0, :]), kp, axis=0).max() < 1e-9 * nfft
+
+
+def test_2400_parseval():
+    g = np.random.default_rng(7)
+    nfft, k = 2400, 2
+    re = g.integers(-8, 8, (k * nfft, 3))
+    im = g.integers(-8, 8, (k * nfft, 3))
+    X = U.upchannelize(_bytes_from(re, im), nfft)
+    lhs = (np.abs(X) ** 2).sum(axis=0)
+    rhs = nfft * (re ** 2 + im ** 2).reshape(k, nfft, 3).sum(axis=1).T
+    assert np.allclose(lhs, rhs, rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------- polyphase filter bank option
+def test_pfb_one_tap_of_ones_is_the_block_fft():
+    g = np.random.default_rng(8)
+    nfft = 60
+    v = g.integers(0, 256, (5 * nfft + 11, 3), dtype=np.uint8)
+    assert np.array_equal(U.pfb_upchannelize(v, nfft, np.ones(nfft)), U.upchannelize(v, nfft))
+
+
+@pytest.mark.parametrize("nfft,n_tap", [(12, 3), (2400, 4)])
+def test_pfb_constant_taps_on_a_tone(nfft, n_tap):
+    # N a multiple of 4: every block of i^n (a + ib) is the same, so constant taps c
+    # give X = c P N (a + ib) in the tone's channel and nothing elsewhere
+    a, b, c = 4, -3, 0.375
+    blocks = n_tap + 2
+    v = _rotating_tone(blocks * nfft + 5, 1, 1, a, b)
+    X = U.pfb_upchannelize(v, nfft, np.full(n_tap * nfft, c))
+    assert X.shape == (nfft, 1, blocks - n_tap + 1)
+    kp = (nfft // 4 + nfft // 2) % nfft
+    assert np.allclose(X[kp, 0, :], c * n_tap * nfft * (a + 1j * b), rtol=1e-12)
+    assert np.delete(np.abs(X[:, 0, :]), kp, axis=0).max() < 1e-9 * nfft
+
+
+def test_pfb_impulse_response():
+    # one non-zero sample at block b0, offset n0: spectrum s sees it through tap
+    # p = b0 - s (if 0 <= p < P) with weight h[p][n0], so |X_k| = |h[p][n0]| |x| for all k
+    nfft, n_tap, blocks = 30, 3, 6
+    h = np.random.default_rng(9).normal(size=n_tap * nfft)
+    re = np.zeros((blocks * nfft, 1), int)
+    im = np.zeros((blocks * nfft, 1), int)
+    b0, n0 = 3, 17
+    re[b0 * nfft + n0, 0], im[b0 * nfft + n0, 0] = -6, 5
+    X = U.pfb_upchannelize(_bytes_from(re, im), nfft, h)
+    for s in range(blocks - n_tap + 1):
+        p = b0 - s
+        w = abs(h[p * nfft + n0]) if 0 <= p < n_tap else 0.0
+        assert np.allclose(np.abs(X[:, 0, s]), w * math.hypot(6, 5), rtol=1e-12, atol=1e-12)
+        if w:
+            # phase: exp(-2 pi i k n0 / N) times sign(h) (-6 + 5i), k the unshifted bin
+            k = (np.arange(nfft) - nfft // 2) % nfft
+            ref = h[p * nfft + n0] * (-6 + 5j) * np.exp(-2j * np.pi * k * n0 / nfft)
+            assert np.allclose(X[:, 0, s], ref, atol=1e-12)
+
+
+def test_pfb_brute_force_small():
+    # N = 6, P = 2 written out as sums over taps and samples, no FFT
+    g = np.random.default_rng(10)
+    nfft, n_tap = 6, 2
+    re = g.integers(-8, 8, (4 * nfft, 2))
+    im = g.integers(-8, 8, (4 * nfft, 2))
+    h = g.normal(size=n_tap * nfft)
+    X = U.pfb_upchannelize(_bytes_from(re, im), nfft, h)
+    z = re + 1j * im
+    for s in range(3):
+        for i in range(2):
+            for kp in range(nfft):
+                k = (kp - nfft // 2) % nfft
+                acc = 0j
+                for n in range(nfft):
+                    y = sum(h[p * nfft + n] * z[(s + p) * nfft + n, i] for p in range(n_tap))
+                    acc += y * complex(math.cos(2 * math.pi * k * n / nfft), -math.sin(2 * math.pi * k * n / nfft))
+                assert abs(X[kp, i, s] - acc) < 1e-10
+
+
+def test_pfb_scale_and_level():
+    # constant (1, 0) samples: mean power 1, s = 8 sqrt(2) / sqrt(sum h^2)
+    nfft, n_tap = 2400, 4
+    h = synth.pfb_prototype(nfft, n_tap).astype(np.float64)
+    v = _bytes_from(np.ones((6 * nfft, 1), int), np.zeros((6 * nfft, 1), int))
+    _, ss, _ = U.upchan_all(v[None], [nfft], taps=[h])
+    assert ss[0][0] == pytest.approx(8 * math.sqrt(2) / math.sqrt((h * h).sum()), rel=1e-15)
+    # white Gaussian voltages through the prototype requantise to ~8 levels rms
+    cfg = synth.make_config("tiny", n_tones=0)
+    vol = synth.generate(cfg)[:, :, :8]
+    hp = [synth.pfb_prototype(n, 4) for n in cfg.nfft]
+    specs, _, qs = U.upchan_all(vol, cfg.nfft, taps=hp)
+    assert specs[0].shape[2] == cfg.n_time // cfg.nfft[0] - 3
+    rms = np.sqrt((qs[0].astype(float) ** 2).mean())
+    assert 7.6 < rms < 8.4
+
+
+def test_pfb_too_few_blocks_gives_no_spectra():
+    v = np.zeros((3 * 12, 2), np.uint8)
+    assert U.pfb_upchannelize(v, 12, np.ones(4 * 12)).shape == (12, 2, 0)
+
+
+def test_channel_window_is_a_slice():
+    g = np.random.default_rng(11)
+    v = g.integers(0, 256, (2, 2 * 2400, 4), dtype=np.uint8)
+    full = U.upchan_all(v, [2400, 2400])
+    win = U.upchan_all(v, [2400, 2400], window=(900, 300))
+    for c in range(2):
+        assert np.array_equal(win[0][c], full[0][c][900:1200])
+        assert np.array_equal(win[1][c], full[1][c])
+        assert np.array_equal(win[2][c], full[2][c][900:1200])
