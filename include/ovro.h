@@ -57,7 +57,7 @@ int ovro_version(void);
 unsigned long long ovro_launch_count(void);
 /* Kernel tracing.  ovro_profile(1) clears the trace and starts recording a
  * CUDA event pair on the launch stream around every launch of the main
- * kernels (k_upchan, k_xeng_tc, k_xeng_simt, k_grid_rows, k_fft_cols,
+ * kernels (k_upchan, k_upchan_mr, k_xeng_tc, k_xeng_simt, k_grid_rows, k_fft_cols,
  * k_stats, k_ztrans, k_rank, k_walk, k_mf); ovro_profile(0) stops recording.
  * ovro_profile_query waits for the recorded launches of one kernel and
  * returns their summed device time and count. */
@@ -74,8 +74,10 @@ int ovro_profile_query(const char* kernel, double* total_ms, int* launches);
  * d_volt   uint8 [n_coarse][n_time][n_input]; each byte is one complex sample,
  *          real part in the high nibble, imaginary in the low nibble, both
  *          4-bit two's complement.
- * h_nfft   [n_coarse] FFT length N_c per coarse channel, a power of two in
- *          [2, 16384].  Each coarse channel yields K_c = n_time / N_c spectra
+ * h_nfft   [n_coarse] FFT length N_c per coarse channel: a power of two in
+ *          [2, 16384], or an even 2^a 3^b 5^c up to 8192 such as the paper's
+ *          2400 (mixed-radix kernel).  Each coarse channel yields
+ *          K_c = n_time / N_c spectra
  *          from non-overlapping blocks (rectangular window, unnormalised
  *          exp(-2 pi i k n / N) transform); leftover samples are ignored.
  *          Fine channel k' = (k + N/2) mod N (fftshift) sits at
@@ -92,13 +94,49 @@ int ovro_profile_query(const char* kernel, double* total_ms, int* launches);
  * d_fine_f32_or_null  optional FP32 spectra in the same layout (floats).
  * Workspace: ovro_upchan_workspace_size(n_input, n_coarse) bytes.
  * Errors: OVRO_ERR_INVALID_ARG (null pointers, n_* <= 0), OVRO_ERR_UNSUPPORTED
- *          (N_c not a power of two in range, n_time < N_c).
+ *          (N_c not one of the lengths above, n_time < N_c).
  * ------------------------------------------------------------------------- */
 size_t ovro_upchan_workspace_size(int n_input, int n_coarse);
 int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time,
                 const int32_t* h_nfft, const double* h_scale_or_null,
                 int8_t* d_fine_q, float* d_fine_f32_or_null,
                 void* d_ws, size_t ws_bytes, void* stream);
+
+/* Upchannelizer options (Section 2.1).
+ *
+ * Fine-channel batches: the paper cross-correlates 300 fine channels at a
+ * time to bound the memory the upchannelized data take.  chan_count > 0 keeps
+ * only fine channels [chan_lo, chan_lo + chan_count) of the fftshifted axis
+ * of every coarse channel (chan_lo + chan_count <= N_c for all c); 0 keeps all.
+ *
+ * Polyphase filter bank in place of the bare block FFT: with n_taps = P and
+ * h_taps non-NULL, spectrum s of coarse channel c is the FFT of
+ * y_n = sum_{p < P} h[p N + n] x[(s + p) N + n], n < N, with h the P N FP32
+ * coefficients at h_taps[c] (a device pointer; the prototype filter read row
+ * by row), so K_c = n_time / N_c - P + 1 spectra; P = 1 with h = 1 is the
+ * plain FFT.  The scale becomes s = 8 sqrt(2) / sqrt(P_mean sum h^2) (sum in
+ * FP64), the power still taken over all n_time / N_c whole blocks.
+ * h_taps NULL requires n_taps = 1.  Either option runs the mixed-radix kernel,
+ * so N_c <= 8192 there. */
+typedef struct ovro_upchan_options {
+  int32_t n_taps;              /* P >= 1 */
+  const float* const* h_taps;  /* host array [n_coarse] of device pointers, or NULL */
+  int32_t chan_lo;             /* first fftshifted fine channel written */
+  int32_t chan_count;          /* fine channels written per coarse channel; 0 = all N_c */
+} ovro_upchan_options;
+
+/* ovro_upchan with options (NULL = ovro_upchan).  Block c of d_fine_q (and of
+ * d_fine_f32_or_null) is [C_c][K_c][n_input][2], C_c = chan_count or N_c,
+ * at element offset sum_{c' < c} C_c' K_c' n_input * 2; row i of the block is
+ * fine channel chan_lo + i.  Same workspace as ovro_upchan.  Errors as
+ * ovro_upchan, plus OVRO_ERR_INVALID_ARG for n_taps < 1, n_taps > 1 without
+ * taps, a NULL taps pointer, chan_lo < 0, chan_count < 0 or a window past N_c,
+ * and OVRO_ERR_UNSUPPORTED when K_c < 1 or a length the kernels do not take. */
+int ovro_upchan_ex(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time,
+                   const int32_t* h_nfft, const double* h_scale_or_null,
+                   const ovro_upchan_options* opt_or_null,
+                   int8_t* d_fine_q, float* d_fine_f32_or_null,
+                   void* d_ws, size_t ws_bytes, void* stream);
 
 /* Allocation-free ovro_upchan (no counterpart in the paper; an interface
  * convenience).  For callers that cannot allocate device memory at all -- a

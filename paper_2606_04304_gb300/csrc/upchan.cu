@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "upchan_impl.h"
 
 namespace ovro {
 namespace {
@@ -66,19 +67,39 @@ __global__ void k_power(const uint8_t* __restrict__ volt, int n_input, long long
     if (v * VW + j < n_input && acc[j]) atomicAdd(power + v * VW + j, static_cast<unsigned long long>(acc[j]));
 }
 
-// s = 8 sqrt(2) / sqrt(N P), P = power / n_used, in FP64; rounded to FP32.
+// s = 8 sqrt(2) / sqrt(W P), P = power / n_used, in FP64; rounded to FP32.
+// W = N for the plain FFT, the sum of the squared taps (*h2) for a PFB.
 __global__ void k_scale(const unsigned long long* __restrict__ power, const double* __restrict__ user,
-                        int n, int nfft, long long n_used, float* __restrict__ scale) {
+                        int n, int nfft, long long n_used, const double* __restrict__ h2,
+                        float* __restrict__ scale) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s;
   if (user) {
     s = user[i];
   } else {
+    const double w = h2 ? *h2 : static_cast<double>(nfft);
     double pbar = static_cast<double>(power[i]) / static_cast<double>(n_used);
-    s = pbar > 0.0 ? (8.0 * sqrt(2.0)) / sqrt(static_cast<double>(nfft) * pbar) : 0.0;
+    s = pbar > 0.0 ? (8.0 * sqrt(2.0)) / sqrt(w * pbar) : 0.0;
   }
   scale[i] = static_cast<float>(s);
+}
+
+// *out = sum of h[i]^2 in FP64 (each square exact), one CTA of 256 threads.
+__global__ void __launch_bounds__(256) k_sumsq(const float* __restrict__ h, int n, double* __restrict__ out) {
+  __shared__ double part[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const double x = static_cast<double>(h[i]);
+    acc += x * x;
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = part[0];
 }
 
 // omega_N^k = exp(-2 pi i k / N) for the largest N in the call, FP64 -> FP32.
@@ -91,17 +112,7 @@ __global__ void k_twiddle(float2* tw, int n) {
 }
 
 // --------------------------------------------------------- FFT + requantise
-struct UpchanArgs {
-  const uint8_t* volt;      // this coarse channel, [n_time][n_input]
-  const float2* tw;         // omega_{tw_n}^k
-  const float* scale;       // [n_input] for this coarse channel
-  int8_t* out_q;            // this coarse block, [N][K][n_input][2]
-  float* out_f;             // same layout, floats (optional)
-  int n_input;
-  int n_spec;
-  int tw_n;
-  int group;                // G inputs per CTA
-};
+
 
 // Radix schedule for N = 2^LOG2N: passes of 16, then one of 2^(LOG2N % 4).
 template <int LOG2N>
@@ -433,6 +444,7 @@ struct UpchanWs {
   unsigned long long* power;
   float* scale;
   double* user;
+  double* h2;
   float2* tw;
 };
 
@@ -442,6 +454,7 @@ UpchanWs carve_upchan(void* ws, size_t bytes, int n_input, int n_coarse, size_t*
   w.power = c.take<unsigned long long>(static_cast<size_t>(n_input) * n_coarse);
   w.scale = c.take<float>(static_cast<size_t>(n_input) * n_coarse);
   w.user = c.take<double>(static_cast<size_t>(n_input) * n_coarse);
+  w.h2 = c.take<double>(static_cast<size_t>(n_coarse));
   w.tw = c.take<float2>(kMaxN);
   *need = c.used;
   return w;
@@ -459,26 +472,50 @@ size_t ovro_upchan_workspace_size(int n_input, int n_coarse) {
   return need;
 }
 
-int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time,
-                const int32_t* h_nfft, const double* h_scale_or_null, int8_t* d_fine_q,
-                float* d_fine_f32_or_null, void* d_ws, size_t ws_bytes, void* stream) {
+int ovro_upchan_ex(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time,
+                   const int32_t* h_nfft, const double* h_scale_or_null, const ovro_upchan_options* opt,
+                   int8_t* d_fine_q, float* d_fine_f32_or_null, void* d_ws, size_t ws_bytes, void* stream) {
   using namespace ovro;
   if (!d_volt || !h_nfft || !d_fine_q || n_input <= 0 || n_coarse <= 0 || n_time <= 0)
     return OVRO_ERR_INVALID_ARG;
-  int max_n = 2;
+  const bool taps = opt && opt->h_taps;
+  const int n_tap = opt ? opt->n_taps : 1;
+  const int lo = opt ? opt->chan_lo : 0;
+  const int cnt_opt = opt ? opt->chan_count : 0;
+  if (n_tap < 1 || (n_tap > 1 && !taps) || lo < 0 || cnt_opt < 0) return OVRO_ERR_INVALID_ARG;
+  struct Coarse {
+    int n, cnt, k;
+    bool mixed;
+    MrPlan plan;
+    int group;
+    size_t smem;
+  };
+  std::vector<Coarse> cs(n_coarse);
+  int max_pow2 = 2;
   for (int c = 0; c < n_coarse; ++c) {
-    const int n = h_nfft[c];
-    if (n <= 0) return OVRO_ERR_INVALID_ARG;
-    if (!is_pow2(n) || n < 2 || n > kMaxN || n_time < n) return OVRO_ERR_UNSUPPORTED;
-    if (n > max_n) max_n = n;
+    Coarse& e = cs[c];
+    e.n = h_nfft[c];
+    if (e.n <= 0) return OVRO_ERR_INVALID_ARG;
+    if (taps && !opt->h_taps[c]) return OVRO_ERR_INVALID_ARG;
+    const long long blocks = n_time / e.n;
+    const long long k = blocks - n_tap + 1;
+    if (k < 1 || k > INT32_MAX) return OVRO_ERR_UNSUPPORTED;
+    e.k = static_cast<int>(k);
+    e.cnt = cnt_opt ? cnt_opt : e.n;
+    if (static_cast<long long>(lo) + e.cnt > e.n) return OVRO_ERR_INVALID_ARG;
+    e.mixed = taps || lo != 0 || e.cnt != e.n || !is_pow2(e.n) || e.n > kMaxN || k > 65535;
+    if (e.mixed) {
+      if (!mr_plan(e.n, n_input, taps ? n_tap : 1, e.cnt, &e.plan, &e.group, &e.smem)) return OVRO_ERR_UNSUPPORTED;
+    } else {
+      if (e.n < 2) return OVRO_ERR_UNSUPPORTED;
+      max_pow2 = std::max(max_pow2, e.n);
+    }
   }
   size_t need = 0;
   UpchanWs w = carve_upchan(d_ws, ws_bytes, n_input, n_coarse, &need);
   if (int e = check_workspace(d_ws, ws_bytes, need)) return e;
   cudaStream_t st = as_stream(stream);
 
-  k_twiddle<<<(max_n + 255) / 256, 256, 0, st>>>(w.tw, max_n);
-  OVRO_LAUNCH_CHECK();
   const size_t nsc = static_cast<size_t>(n_input) * n_coarse;
   if (h_scale_or_null) {
     OVRO_CUDA_TRY(cudaMemcpyAsync(w.user, h_scale_or_null, nsc * sizeof(double),
@@ -486,11 +523,12 @@ int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time
   } else {
     OVRO_CUDA_TRY(cudaMemsetAsync(w.power, 0, nsc * sizeof(unsigned long long), st));
   }
+  int table_n = 0;   // omega_{table_n}^k currently in w.tw
   long long q_off = 0;
   for (int c = 0; c < n_coarse; ++c) {
-    const int n = h_nfft[c];
-    const long long k = n_time / n;
-    const long long n_used = k * n;
+    const Coarse& e = cs[c];
+    const int n = e.n;
+    const long long n_used = (n_time / n) * n;
     if (!h_scale_or_null) {
       const int vw = (n_input % 16 == 0) ? 16 : ((n_input % 4 == 0) ? 4 : 1);
       const int nvec = (n_input + vw - 1) / vw;
@@ -506,12 +544,26 @@ int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time
       else
         k_power<1><<<grid, threads, 0, st>>>(vc, n_input, n_used, pc);
       OVRO_LAUNCH_CHECK();
+      if (taps) {
+        k_sumsq<<<1, 256, 0, st>>>(opt->h_taps[c], n_tap * n, w.h2 + c);
+        OVRO_LAUNCH_CHECK();
+      }
     }
     k_scale<<<(n_input + 255) / 256, 256, 0, st>>>(
         w.power + static_cast<size_t>(c) * n_input,
         h_scale_or_null ? w.user + static_cast<size_t>(c) * n_input : nullptr, n_input, n,
-        n_used, w.scale + static_cast<size_t>(c) * n_input);
+        n_used, taps ? w.h2 + c : nullptr, w.scale + static_cast<size_t>(c) * n_input);
     OVRO_LAUNCH_CHECK();
+
+    // twiddles: exactly omega_N for the mixed-radix kernel; any power-of-two
+    // table at least N long for the radix-16 kernel
+    const int want = e.mixed ? n : max_pow2;
+    const bool ok = e.mixed ? table_n == n : (is_pow2(table_n) && table_n >= n);
+    if (!ok) {
+      k_twiddle<<<(want + 255) / 256, 256, 0, st>>>(w.tw, want);
+      OVRO_LAUNCH_CHECK();
+      table_n = want;
+    }
 
     UpchanArgs a;
     a.volt = d_volt + static_cast<long long>(c) * n_time * n_input;
@@ -520,14 +572,30 @@ int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time
     a.out_q = d_fine_q + q_off;
     a.out_f = d_fine_f32_or_null ? d_fine_f32_or_null + q_off : nullptr;
     a.n_input = n_input;
-    a.n_spec = static_cast<int>(k);
-    a.tw_n = max_n;
-    const int l = ilog2(n);
-    a.group = group_for(l, n_input);
-    if (int e = launch_upchan(l, a, st)) return e;
-    q_off += static_cast<long long>(n) * k * n_input * 2;
+    a.n_spec = e.k;
+    a.tw_n = table_n;
+    a.taps = taps ? opt->h_taps[c] : nullptr;
+    a.n_tap = taps ? n_tap : 1;
+    a.chan_lo = lo;
+    a.chan_cnt = e.cnt;
+    if (e.mixed) {
+      a.group = e.group;
+      if (int err = launch_upchan_mr(a, e.plan, e.smem, st)) return err;
+    } else {
+      const int l = ilog2(n);
+      a.group = group_for(l, n_input);
+      if (int err = launch_upchan(l, a, st)) return err;
+    }
+    q_off += static_cast<long long>(e.cnt) * e.k * n_input * 2;
   }
   return OVRO_OK;
+}
+
+int ovro_upchan(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_time,
+                const int32_t* h_nfft, const double* h_scale_or_null, int8_t* d_fine_q,
+                float* d_fine_f32_or_null, void* d_ws, size_t ws_bytes, void* stream) {
+  return ovro_upchan_ex(d_volt, n_input, n_coarse, n_time, h_nfft, h_scale_or_null, nullptr, d_fine_q,
+                        d_fine_f32_or_null, d_ws, ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import Optional, Sequence
+from typing import Optional, Sequence, Tuple
 
 import numpy as np
 import torch
@@ -62,6 +62,7 @@ def _load() -> ctypes.CDLL:
         "ovro_profile_query": (I, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
         "ovro_upchan_workspace_size": (S, [I, I]),
         "ovro_upchan": (I, [P, I, I, L, P, P, P, P, P, S, P]),
+        "ovro_upchan_ex": (I, [P, I, I, L, P, P, P, P, P, P, S, P]),
         "ovro_correlate": (I, [P, I, I, I, I, P, P]),
         "ovro_correlate_status": (I, [P]),
         "ovro_grid_image_workspace_size": (S, [I, I, I, I]),
@@ -139,7 +140,7 @@ def profile_query(kernel: str):
     return ms.value, n.value
 
 
-TRACED_KERNELS = ("k_upchan", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
+TRACED_KERNELS = ("k_upchan", "k_upchan_mr", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
                   "k_rank", "k_walk", "k_median_sub", "k_mf", "k_nms_warp")
 
 
@@ -171,29 +172,52 @@ def workspace(nbytes: int, device=None) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
 
 
-def fine_elements(nfft: Sequence[int], n_time: int, n_input: int) -> int:
-    return int(sum(n * (n_time // n) * n_input * 2 for n in nfft))
+def fine_elements(nfft: Sequence[int], n_time: int, n_input: int, n_taps: int = 1,
+                  chan_count: int = 0) -> int:
+    return int(sum((chan_count or n) * (n_time // n - n_taps + 1) * n_input * 2 for n in nfft))
+
+
+class _UpchanOptions(ctypes.Structure):
+    _fields_ = [("n_taps", ctypes.c_int32), ("h_taps", ctypes.c_void_p), ("chan_lo", ctypes.c_int32),
+                ("chan_count", ctypes.c_int32)]
 
 
 # ---------------------------------------------------------------------- a1-a3
 def upchan(volt: torch.Tensor, nfft: Sequence[int], scales=None, want_f32: bool = False,
-           out_q: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None):
+           out_q: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None,
+           taps: Optional[Sequence[torch.Tensor]] = None, window: Optional[Tuple[int, int]] = None):
     """volt: uint8 [n_coarse][n_time][n_input] on the GPU.  Returns (q int8, f32 or None),
-    both flat in the coarse-major [N][K][n_input][2] block layout of ovro_upchan."""
+    both flat in the coarse-major [C][K][n_input][2] block layout of ovro_upchan_ex.
+
+    taps: None (plain FFT) or one contiguous CUDA float32 tensor of P N_c
+    polyphase-filter coefficients per coarse channel, all with the same P.
+    window: None or (chan_lo, chan_count), the fftshifted fine channels kept."""
     _cuda(volt, torch.uint8, "volt")
     n_coarse, n_time, n_input = volt.shape
     nf = _host(nfft, np.int32)
-    total = fine_elements(nf, n_time, n_input)
-    q = out_q if out_q is not None else torch.empty(total, dtype=torch.int8, device=volt.device)
-    f = torch.empty(total, dtype=torch.float32, device=volt.device) if want_f32 else None
+    n_taps = 1
+    tap_ptrs = None
+    if taps is not None:
+        if len(taps) != n_coarse:
+            raise ValueError("taps: one tensor per coarse channel")
+        for t in taps:
+            _cuda(t, torch.float32, "taps")
+        n_taps = taps[0].numel() // int(nf[0])
+        tap_ptrs = (ctypes.c_void_p * n_coarse)(*[t.data_ptr() for t in taps])
+    lo, cnt = window if window is not None else (0, 0)
+    opt = _UpchanOptions(n_taps, ctypes.cast(tap_ptrs, ctypes.c_void_p) if tap_ptrs is not None else None,
+                         lo, cnt)
+    total = fine_elements(nf, n_time, n_input, n_taps, cnt)
+    q = out_q if out_q is not None else torch.empty(max(total, 1), dtype=torch.int8, device=volt.device)
+    f = torch.empty(max(total, 1), dtype=torch.float32, device=volt.device) if want_f32 else None
     need = _lib.ovro_upchan_workspace_size(n_input, n_coarse)
     ws = ws if ws is not None and ws.numel() >= need else workspace(need, volt.device)
     sc = None if scales is None else _host(scales, np.float64)
-    _check("ovro_upchan", _lib.ovro_upchan(
+    _check("ovro_upchan_ex", _lib.ovro_upchan_ex(
         _ptr(volt), n_input, n_coarse, n_time, nf.ctypes.data_as(ctypes.c_void_p),
-        None if sc is None else sc.ctypes.data_as(ctypes.c_void_p), _ptr(q), _ptr(f), _ptr(ws),
-        ws.numel(), _stream(stream)))
-    return q, f
+        None if sc is None else sc.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt), _ptr(q), _ptr(f),
+        _ptr(ws), ws.numel(), _stream(stream)))
+    return q[:total], (None if f is None else f[:total])
 
 
 # ------------------------------------------------------------------------- a4

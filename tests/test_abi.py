@@ -45,15 +45,39 @@ def test_host_validation_without_gpu(ov):
     assert lib.ovro_correlate(ctypes.c_void_p(16), 4, 1, 521, 0, ctypes.c_void_p(16), None) == -6
     assert lib.ovro_correlate(ctypes.c_void_p(16), 4, 1, 1, 7, ctypes.c_void_p(16), None) == -1
     assert lib.ovro_correlate(ctypes.c_void_p(16), 5000, 1, 1, 0, ctypes.c_void_p(16), None) == -2
-    nf = (ctypes.c_int32 * 1)(1000)
+    nf = (ctypes.c_int32 * 1)(1002)          # 2 x 3 x 167: no mixed-radix plan
     assert lib.ovro_upchan(ctypes.c_void_p(16), 4, 1, 4096, nf, None, ctypes.c_void_p(16), None,
                            None, 0, None) == -2
+    nf[0] = 2400                                # planned; then the missing workspace is refused
+    assert lib.ovro_upchan(ctypes.c_void_p(16), 4, 1, 4800, nf, None, ctypes.c_void_p(16), None,
+                           None, 0, None) == -5
     nf[0] = 1024
     assert lib.ovro_upchan(ctypes.c_void_p(16), 4, 1, 4096, nf, None, ctypes.c_void_p(16), None,
                            None, 0, None) == -5
     assert lib.ovro_upchan_workspace_size(704, 1) > 0
     assert lib.ovro_grid_image_workspace_size(352, 8192, 256, 0) > 0
     assert lib.ovro_grid_image_workspace_size(352, 8192, 300, 0) == 0
+
+
+def test_upchan_options_validation_without_gpu(ov):
+    lib = ov.lib()
+    nf = (ctypes.c_int32 * 2)(2400, 4096)
+    v, q = ctypes.c_void_p(16), ctypes.c_void_p(16)
+
+    def call(opt, n_time=3 * 4096):
+        return lib.ovro_upchan_ex(v, 4, 2, n_time, nf, None, ctypes.byref(opt), q, None, None, 0, None)
+
+    O = ov._UpchanOptions
+    assert call(O(0, None, 0, 0)) == -1                 # n_taps < 1
+    assert call(O(2, None, 0, 0)) == -1                 # taps needed for P > 1
+    assert call(O(1, None, -1, 0)) == -1                # chan_lo < 0
+    assert call(O(1, None, 0, -3)) == -1                # chan_count < 0
+    assert call(O(1, None, 2200, 300)) == -1            # window past N = 2400
+    taps = (ctypes.c_void_p * 2)(16, None)
+    assert call(O(2, ctypes.cast(taps, ctypes.c_void_p), 0, 0)) == -1     # a NULL taps pointer
+    taps = (ctypes.c_void_p * 2)(16, 16)
+    assert call(O(4, ctypes.cast(taps, ctypes.c_void_p), 0, 0)) == -2     # K = 3 - 4 + 1 = 0 for N = 4096
+    assert call(O(1, None, 2100, 300)) == -5            # valid: only the workspace is missing
 
 
 def test_default_widths(ov):

@@ -144,3 +144,31 @@ def test_two_shards_equal_one_search(lib, case):
         got += [(int(c["chan"]) + ch0, int(c["row"]), int(c["col"]), int(c["width"]), float(c["snr"])) for c in cands]
     want = [(int(c["chan"]), int(c["row"]), int(c["col"]), int(c["width"]), float(c["snr"])) for c in ref]
     assert sorted(got) == sorted(want)
+
+
+def test_pipeline_with_3_5_smooth_lengths(lib):
+    # the paper's factor N = 2400 beside other 2^a 3^b 5^c lengths, through the
+    # captured pipeline: equal to the stage-by-stage calls and the oracle's search
+    cfg = synth.make_config("batched", n_ant=16, n_coarse=3, nfft=[2400, 480, 96], n_time=9600,
+                            image_size=32, core_ant=16, core_radius_m=30.0, n_tones=3)
+    volt = torch.from_numpy(synth.generate(cfg)).cuda()
+    pos = synth.antenna_positions(cfg)
+    freqs = synth.fine_freqs_hz(cfg.nfft)
+    q, _ = lib.upchan(volt, cfg.nfft)
+    vis = torch.empty((cfg.n_chan_total, lib.n_baselines(cfg.n_ant), 4, 2), dtype=torch.int32, device="cuda")
+    qoff = c0 = 0
+    for n, k in zip(cfg.nfft, cfg.n_spec):
+        m = n * k * cfg.n_input * 2
+        lib.correlate(q[qoff:qoff + m], cfg.n_ant, n, k, lib.XENG_TC, out=vis[c0:c0 + n])
+        qoff += m
+        c0 += n
+    img = lib.grid_image(vis, pos, freqs, cfg.image_size, cfg.cell)
+    ref = lib.detect(img, cfg.cell, cfg.nfft, freqs)
+    pl = _pipeline(lib, cfg, pos)
+    assert np.array_equal(pl.channels(), freqs)
+    got = pl.run(volt)
+    _same(got, ref)
+    mask = OI.horizon_mask(cfg.image_size, cfg.cell)
+    oref = OD.detect(img.cpu().numpy().astype(np.float64), mask, cfg.nfft)
+    assert {(int(c["chan"]), int(c["row"]), int(c["col"])) for c in got} == {(c.chan, c.row, c.col) for c in oref}
+    pl.close()
