@@ -280,7 +280,7 @@ typedef struct {
   int mode;               /* OVRO_DETECT_BH or OVRO_DETECT_FIXED */
   double alpha;           /* BH false-discovery level (e.g. 0.01) */
   double nsigma;          /* fixed-mode threshold (the paper quotes 10) */
-  double highpass_hz;     /* running-median span, "over 5 kHz" -> 5000 */
+  double highpass_hz;     /* running-median span: wider than 5 kHz -> 5000 */
   double coarse_bw_hz;    /* coarse-channel width (24000) */
 } ovro_detect_params;
 

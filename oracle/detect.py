@@ -8,7 +8,7 @@ Steps in the paper's order:
    The constant is 1 / Phi^{-1}(3/4), which makes 1.4826 MAD the standard
    deviation of Gaussian noise.  A channel with MAD = 0 gives z = 0.
 2. Subtract a running median along frequency at every pixel, with a window
-   "over 5 kHz" (Section 2.4): W = the smallest odd number of channels with
+   wider than 5 kHz (Section 2.4): W = the smallest odd number of channels with
    W * df > 5 kHz, centred, clipped at the edges of the coarse channel (the
    window shrinks there; an even count takes the mean of the two middles).
 3. Convolve every pixel spectrum with unit-normalised boxcars of widths 1 to
