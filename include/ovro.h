@@ -328,6 +328,78 @@ int ovro_detect_filter(const float* d_img, const double* d_stats, int n_chan, in
                        int32_t* d_width, void* d_ws, size_t ws_bytes, void* stream);
 
 /* -------------------------------------------------------------------------
+ * Stage I re-evaluation and Stage II automated cuts (Section 2.4)
+ *
+ * For each candidate (an ovro_detect record, width w at global channel k,
+ * boxcar support S, coarse channel [c_lo, c_hi)):
+ *  - re-evaluation: off-line channels O = the offline_half channels on each
+ *    side beyond the NMS guard g = max(1, floor(w/2)) around S, clipped to
+ *    the coarse channel; at the candidate's pixel b = median z_O,
+ *    sigma = 1.482602218505602 median |z_O - b| (1 if |O| < 16 or sigma = 0),
+ *    snr_re = sum_S (z - b) / (sigma sqrt(w)); OVRO_VET_REEVAL if < cut.
+ *    z is the MAD-standardised image (d_stats from ovro_detect_stats).
+ *  - line image over the (2 fit_half + 1)^2 cutout: L_p = sum_S (z_p - b_p) /
+ *    sqrt(w), b_p the median over O at pixel p; pixels off the image or below
+ *    the horizon are left out.
+ *  - centroid: least squares of A exp(-(a dx^2 + 2 b dx dy + c dy^2) / 2),
+ *    dx = col - x0, dy = row - y0, started from (L_centre, col, row) and the
+ *    beam's (a, b, c); errors from (J^T J)^-1 chi2_red (rescaled by
+ *    sqrt(chi2_red)).  The beam is the same fit to the point-spread image
+ *    d_psf of the candidate's coarse channel around pixel (N/2, N/2), started
+ *    at (peak, N/2, N/2, 1, 0, 1); beam_fwhm = 2 sqrt(2 ln 2) (ac - b^2)^-1/4
+ *    pixels and sigma_therm = beam_fwhm / (2 snr), snr the Stage I SNR.
+ *  - OVRO_VET_EXTENDED if sqrt(det Q_beam / det Q_fit) > max_area_ratio;
+ *    OVRO_VET_FIT if either fit failed (non-finite, A <= 0, Q not positive
+ *    definite, centroid more than fit_half pixels off, fewer than 7 pixels).
+ *  - OVRO_VET_NOISY if the candidate channel's standardised in-horizon
+ *    pixels have a standard deviation above max_noise_std, or its robust
+ *    sigma 1.4826 MAD is more than max_sigma_dev times above or below the
+ *    median over its coarse channel.
+ * keep = (flags == 0).  Pixels are (col, row) with l = (col - N/2) cell,
+ * m = (row - N/2) cell.  Fits run in FP64 on the GPU, one warp each.
+ * ------------------------------------------------------------------------- */
+enum { OVRO_VET_REEVAL = 1, OVRO_VET_EXTENDED = 2, OVRO_VET_NOISY = 4, OVRO_VET_FIT = 8 };
+
+typedef struct {
+  int32_t offline_half;    /* off-line channels per side, 1..64 (64) */
+  int32_t fit_half;        /* cutout half-size in pixels, 1..7 (3) */
+  double max_area_ratio;   /* (2.0) */
+  double max_noise_std;    /* (1.5) */
+  double max_sigma_dev;    /* (2.0) */
+} ovro_vet_params;
+
+typedef struct {
+  int32_t keep;            /* 1: survives every cut */
+  int32_t flags;           /* OVRO_VET_* bits */
+  float snr_re;            /* re-evaluated SNR */
+  float area_ratio;        /* fitted area / beam area (NaN if a fit failed) */
+  double amp;              /* fitted amplitude */
+  double col, row;         /* fitted centroid, pixels */
+  double sigma_col, sigma_row;   /* 1-sigma fit errors x sqrt(chi2_red), pixels */
+  double chi2_red;
+  double beam_fwhm;        /* synthesized-beam FWHM, pixels */
+  double sigma_therm;      /* beam_fwhm / (2 snr), pixels */
+  double noise_std;        /* std of the candidate channel's standardised image */
+  int32_t iterations;      /* Levenberg-Marquardt steps taken */
+  int32_t pad_;
+} ovro_vet_result;
+
+void ovro_vet_default_params(ovro_vet_params* p);
+size_t ovro_vet_workspace_size(int n_cand, int n_coarse);
+/* d_img float [n_chan][N][N] images and d_stats double [n_chan][2] (median,
+ * MAD) as ovro_detect_stats; d_psf float [n_coarse][N][N] point-spread
+ * images (the dirty image of unit visibilities at each coarse channel);
+ * h_cand [n_cand] candidates; cut the Stage I decision threshold; params
+ * NULL for the defaults.  h_out [n_cand].  Synchronises stream.  Errors:
+ * OVRO_ERR_INVALID_ARG (null pointers, sizes, channel counts not summing to
+ * n_chan, a candidate outside its coarse channel or the image),
+ * OVRO_ERR_UNSUPPORTED (params out of range). */
+int ovro_vet(const float* d_img, const double* d_stats, int n_chan, int image_size, double cell_dircos,
+             int n_coarse, const int32_t* h_nfft, const float* d_psf, const ovro_candidate* h_cand, int n_cand,
+             float cut, const ovro_vet_params* params_or_null, ovro_vet_result* h_out, void* d_ws,
+             size_t ws_bytes, void* stream);
+
+/* -------------------------------------------------------------------------
  * a13  Learned candidate scorer (no counterpart in the paper, which keeps or
  * drops Stage I triggers by threshold alone; the plain detector stays the
  * fallback and the judge of recall and false alarms).

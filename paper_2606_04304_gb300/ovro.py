@@ -101,6 +101,9 @@ def _load() -> ctypes.CDLL:
         "ovro_bh_bin_verdict": (I, [P, I, ctypes.c_uint32, D, D, I, P, P]),
         "ovro_bh_resolve": (I, [P, ctypes.c_longlong, ctypes.c_ulonglong, D, D, P]),
         "ovro_snr_bin_key": (ctypes.c_uint32, [ctypes.c_float]),
+        "ovro_vet_default_params": (None, [P]),
+        "ovro_vet_workspace_size": (S, [I, I]),
+        "ovro_vet": (I, [P, P, I, I, D, I, P, P, P, I, ctypes.c_float, P, P, P, S, P]),
         "ovro_autotune": (I, [I]),
         "ovro_tune_get": (I, [ctypes.c_char_p, P]),
         "ovro_tune_set": (I, [ctypes.c_char_p, I]),
@@ -140,7 +143,7 @@ def profile_query(kernel: str):
     return ms.value, n.value
 
 
-TRACED_KERNELS = ("k_upchan", "k_upchan_mr", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
+TRACED_KERNELS = ("k_upchan", "k_upchan_mr", "k_vet_line", "k_vet_fit", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
                   "k_rank", "k_walk", "k_median_sub", "k_mf", "k_nms_warp")
 
 
@@ -352,6 +355,58 @@ def detect(img: torch.Tensor, cell: float, nfft: Sequence[int], freqs_hz, params
                           ws.numel(), _stream(stream))
     _check("ovro_detect", st)
     return out[: n_out.value]
+
+
+# --------------------------------------------- Stage I re-evaluation, Stage II
+VET_REEVAL, VET_EXTENDED, VET_NOISY, VET_FIT = 1, 2, 4, 8
+VET_RESULT_DTYPE = np.dtype([("keep", "<i4"), ("flags", "<i4"), ("snr_re", "<f4"), ("area_ratio", "<f4"),
+                             ("amp", "<f8"), ("col", "<f8"), ("row", "<f8"), ("sigma_col", "<f8"),
+                             ("sigma_row", "<f8"), ("chi2_red", "<f8"), ("beam_fwhm", "<f8"),
+                             ("sigma_therm", "<f8"), ("noise_std", "<f8"), ("iterations", "<i4"), ("pad_", "<i4")])
+
+
+class VetParams(ctypes.Structure):
+    _fields_ = [("offline_half", ctypes.c_int32), ("fit_half", ctypes.c_int32), ("max_area_ratio", ctypes.c_double),
+                ("max_noise_std", ctypes.c_double), ("max_sigma_dev", ctypes.c_double)]
+
+
+def vet_params(**kw) -> VetParams:
+    p = VetParams()
+    _lib.ovro_vet_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def psf_images(ant_enu_m, freqs_hz, image_size: int, cell: float, stream=None) -> torch.Tensor:
+    """Point-spread images [n][N][N]: the dirty images of unit XX and YY
+    visibilities on every cross baseline, one per frequency (ovro_grid_image)."""
+    pos = _host(ant_enu_m, np.float64)
+    n_ant = pos.shape[0]
+    fr = _host(freqs_hz, np.float64)
+    vis = torch.zeros((fr.size, n_baselines(n_ant), 4, 2), dtype=torch.int32, device="cuda")
+    vis[:, :, 0, 0] = 1
+    vis[:, :, 3, 0] = 1
+    return grid_image(vis, pos, fr, image_size, cell, stream=stream)
+
+
+def vet(img: torch.Tensor, stats: torch.Tensor, cell: float, nfft: Sequence[int], psf: torch.Tensor, cands,
+        cut: float, params: Optional[VetParams] = None, stream=None) -> np.ndarray:
+    """Re-evaluate and vet Stage I candidates (CANDIDATE_DTYPE records); returns
+    VET_RESULT_DTYPE records in the same order."""
+    _cuda(img, torch.float32, "img")
+    _cuda(stats, torch.float64, "stats")
+    _cuda(psf, torch.float32, "psf")
+    n_chan, n, _ = img.shape
+    nf = _host(nfft, np.int32)
+    cd = np.ascontiguousarray(np.asarray(cands, CANDIDATE_DTYPE))
+    out = np.zeros(max(cd.size, 1), VET_RESULT_DTYPE)
+    ws = workspace(_lib.ovro_vet_workspace_size(cd.size, nf.size), img.device)
+    _check("ovro_vet", _lib.ovro_vet(
+        _ptr(img), _ptr(stats), n_chan, n, float(cell), nf.size, nf.ctypes.data_as(ctypes.c_void_p), _ptr(psf),
+        cd.ctypes.data_as(ctypes.c_void_p), cd.size, float(cut), None if params is None else ctypes.byref(params),
+        out.ctypes.data_as(ctypes.c_void_p), _ptr(ws), ws.numel(), _stream(stream)))
+    return out[: cd.size]
 
 
 def detect_stats(img: torch.Tensor, cell: float, stream=None) -> torch.Tensor:

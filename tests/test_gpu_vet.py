@@ -1,0 +1,162 @@
+"""GPU parity: Stage I re-evaluation and Stage II vetting (ovro_vet) against
+the oracle on synthetic cubes with compact, extended and weak lines, noisy
+images and candidates at the edges; and end to end on the tiny workload."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import detect as OD, imaging as OI, vetting as OV
+
+pytestmark = pytest.mark.gpu
+
+
+def _gauss(n, r, c, s, amp=1.0):
+    yy, xx = np.mgrid[0:n, 0:n]
+    return amp * np.exp(-0.5 * ((xx - c) ** 2 + (yy - r) ** 2) / s ** 2)
+
+
+def _cube(seed, n, nfft, lines, noisy=(), tails=()):
+    g = np.random.default_rng(seed)
+    nc = sum(nfft)
+    cube = g.normal(size=(nc, n, n))
+    for r, c, k, w, amp, s in lines:
+        lo, hi = OV.support(k, w)
+        cube[lo:hi + 1] += _gauss(n, r, c, s, amp)
+    for f in noisy:
+        cube[f] *= 3.0
+    for f in tails:
+        t = g.random((n, n)) < 0.05
+        cube[f][t] = 25.0 * np.sign(g.normal(size=t.sum()))
+    return cube.astype(np.float32)
+
+
+def _compare(lib, cube, cell, nfft, cands, cut, psf, params=None, loose=()):
+    """GPU against oracle; for candidates in `loose` (fits on pure noise, whose
+    minimiser is not unique) only the re-evaluation and noise results."""
+    n = cube.shape[1]
+    d = torch.from_numpy(cube).cuda()
+    stats = lib.detect_stats(d, cell)
+    dpsf = torch.from_numpy(np.ascontiguousarray(psf, np.float32)).cuda()
+    rec = np.zeros(len(cands), lib.CANDIDATE_DTYPE)
+    for i, cd in enumerate(cands):
+        rec[i] = (cd.coarse, cd.fine, cd.chan, cd.row, cd.col, cd.width, cd.snr, 0, 0, 0)
+    kw = {} if params is None else params
+    got = lib.vet(d, stats, cell, nfft, dpsf, rec, cut, lib.vet_params(**kw) if kw else None)
+    mask = OI.horizon_mask(n, cell)
+    ref = OV.vet(cube, stats.cpu().numpy(), mask, nfft, cands, cut, [p.astype(np.float64) for p in psf],
+                 h=kw.get("fit_half", OV.FIT_HALF), m=kw.get("offline_half", OV.OFFLINE_HALF))
+    for i, (gr, rr) in enumerate(zip(got, ref)):
+        assert gr["snr_re"] == pytest.approx(rr.snr_re, rel=1e-6, abs=1e-6)
+        assert gr["noise_std"] == pytest.approx(rr.noise_std, rel=1e-9)
+        if i in loose:
+            m = OV.REEVAL | OV.NOISY
+            assert gr["flags"] & m == rr.flags & m, (gr, rr)
+            continue
+        assert gr["flags"] == rr.flags, (gr, rr)
+        assert bool(gr["keep"]) == rr.keep
+        if not rr.flags & OV.FIT:
+            assert gr["col"] == pytest.approx(rr.col, abs=1e-6)
+            assert gr["row"] == pytest.approx(rr.row, abs=1e-6)
+            assert gr["amp"] == pytest.approx(rr.amp, rel=1e-6)
+            assert gr["sigma_col"] == pytest.approx(rr.sigma_col, rel=1e-5)
+            assert gr["sigma_row"] == pytest.approx(rr.sigma_row, rel=1e-5)
+            assert gr["chi2_red"] == pytest.approx(rr.chi2_red, rel=1e-6)
+            assert gr["area_ratio"] == pytest.approx(rr.area_ratio, rel=1e-5)
+        assert gr["beam_fwhm"] == pytest.approx(rr.beam_fwhm, rel=1e-7)
+        assert gr["sigma_therm"] == pytest.approx(rr.sigma_therm, rel=1e-7)
+    return got, ref
+
+
+def test_synthetic_lines_against_oracle(lib):
+    n, nfft = 32, [300]
+    lines = [(10, 12, 80, 3, 6.0, 1.3), (20, 22, 150, 5, 4.0, 3.5), (27, 9, 220, 1, 2.2, 1.3),
+             (16, 16, 40, 9, 3.0, 1.3)]
+    cube = _cube(14, n, nfft, lines)
+    psf = [_gauss(n, n // 2, n // 2, 1.3)]
+    cands = [OD.Candidate(0, k, k, r, c, w, 8.0) for r, c, k, w, _, _ in lines]
+    got, _ = _compare(lib, cube, 1.0 / n, nfft, cands, 5.0, psf)
+    assert got["keep"].tolist() == [1, 0, 0, 1]
+    assert got["flags"][1] & lib.VET_EXTENDED and got["flags"][2] & lib.VET_REEVAL
+
+
+def test_edges_horizon_noise_and_params(lib):
+    # two coarse channels; candidates at the image edge, below the horizon's
+    # edge, at coarse-channel edges (few off-line channels), the widest
+    # boxcar, and in a scaled and a heavy-tailed image
+    n, nfft = 64, [200, 160]
+    cell = 2.0 / n
+    lines = [(2, 24, 60, 2, 5.0, 1.3), (32, 1, 110, 4, 5.0, 1.3), (24, 24, 1, 3, 6.0, 1.3),
+             (30, 30, 250, 100, 1.5, 1.3), (20, 22, 358, 1, 8.0, 1.3), (26, 20, 120, 3, 5.0, 1.3),
+             (14, 30, 300, 3, 5.0, 1.3)]
+    cube = _cube(15, n, nfft, lines, noisy=(121,), tails=(299, 300, 301))
+    psf = [_gauss(n, n // 2, n // 2, 1.3), _gauss(n, n // 2, n // 2, 1.6)]
+    bounds = OD.chan_bounds_of(nfft)
+    cands = []
+    for r, c, k, w, _, _ in lines:
+        ci = 0 if k < nfft[0] else 1
+        cands.append(OD.Candidate(ci, k - bounds[ci][0], k, r, c, w, 7.0))
+    got, ref = _compare(lib, cube, cell, nfft, cands, 4.0, psf, loose=(6,))
+    assert got["flags"][5] & lib.VET_NOISY == 0 and got["flags"][6] & lib.VET_NOISY
+    # other parameters: a wider cutout, fewer off-line channels, stricter area cut
+    _compare(lib, cube, cell, nfft, cands, 4.0, psf,
+             dict(fit_half=5, offline_half=20, max_area_ratio=1.3, max_noise_std=1.2, max_sigma_dev=1.5), loose=(6,))
+
+
+def test_tiny_workload_end_to_end(lib):
+    # upchannelize -> correlate -> image -> Stage I -> vet: the injected tone
+    # survives and its centroid sits on its pixel; the oracle vets the same way
+    cfg = synth.make_config("tiny", cell_dircos=0.005)      # a beam of a few pixels
+    volt = torch.from_numpy(synth.generate(cfg)).cuda()
+    pos = synth.antenna_positions(cfg)
+    freqs = synth.fine_freqs_hz(cfg.nfft)
+    q, _ = lib.upchan(volt, cfg.nfft)
+    vis = torch.empty((cfg.n_chan_total, lib.n_baselines(cfg.n_ant), 4, 2), dtype=torch.int32, device="cuda")
+    qoff = c0 = 0
+    for nn, k in zip(cfg.nfft, cfg.n_spec):
+        m = nn * k * cfg.n_input * 2
+        lib.correlate(q[qoff:qoff + m], cfg.n_ant, nn, k, out=vis[c0:c0 + nn])
+        qoff += m
+        c0 += nn
+    img = lib.grid_image(vis, pos, freqs, cfg.image_size, cfg.cell)
+    prm = lib.detect_params(mode=lib.DETECT_FIXED, nsigma=8.0)
+    cands = lib.detect(img, cfg.cell, cfg.nfft, freqs, prm)
+    assert cands.size >= 1
+    centres = [synth.coarse_centre_hz(c) for c in range(cfg.n_coarse)]
+    psf = lib.psf_images(pos, centres, cfg.image_size, cfg.cell)
+    stats = lib.detect_stats(img, cfg.cell)
+    got = lib.vet(img, stats, cfg.cell, cfg.nfft, psf, cands, 8.0)
+    t = cfg.tones[0]
+    hit = [i for i, c in enumerate(cands) if c["row"] == t.row and c["col"] == t.col]
+    assert hit, "tone not among the candidates"
+    g0 = got[hit[0]]
+    assert g0["keep"] == 1, g0
+    assert abs(g0["col"] - t.col) < 1.0 and abs(g0["row"] - t.row) < 1.0
+    assert g0["sigma_therm"] == pytest.approx(g0["beam_fwhm"] / (2 * cands[hit[0]]["snr"]), rel=1e-6)
+    # the oracle on the same images, statistics and beams
+    oc = [OD.Candidate(int(c["coarse"]), int(c["fine"]), int(c["chan"]), int(c["row"]), int(c["col"]),
+                       int(c["width"]), float(c["snr"])) for c in cands]
+    ref = OV.vet(img.cpu().numpy(), stats.cpu().numpy(), OI.horizon_mask(cfg.image_size, cfg.cell), cfg.nfft, oc,
+                 8.0, [p.astype(np.float64) for p in psf.cpu().numpy()])
+    m = OV.REEVAL | OV.NOISY
+    assert [r.flags & m for r in ref] == (got["flags"] & m).tolist()
+    assert ref[hit[0]].flags == g0["flags"] and ref[hit[0]].col == pytest.approx(g0["col"], abs=1e-6)
+    assert [r.snr_re for r in ref] == pytest.approx(got["snr_re"].tolist(), rel=1e-5)
+
+
+def test_rejects_bad_candidates(lib):
+    n = 16
+    d = torch.zeros((40, n, n), dtype=torch.float32, device="cuda")
+    stats = torch.ones((40, 2), dtype=torch.float64, device="cuda")
+    psf = torch.zeros((1, n, n), dtype=torch.float32, device="cuda")
+    rec = np.zeros(1, lib.CANDIDATE_DTYPE)
+    rec[0] = (0, 38, 38, 5, 5, 5, 9.0, 0, 0, 0)           # boxcar 36..40 runs past channel 39
+    with pytest.raises(lib.OvroError):
+        lib.vet(d, stats, 1.0 / n, [40], psf, rec, 5.0)
+    rec[0] = (0, 10, 10, n, 5, 1, 9.0, 0, 0, 0)           # row off the image
+    with pytest.raises(lib.OvroError):
+        lib.vet(d, stats, 1.0 / n, [40], psf, rec, 5.0)
+    with pytest.raises(lib.OvroError):
+        lib.vet(d, stats, 1.0 / n, [40], psf, rec[:0], 5.0, lib.vet_params(fit_half=9))
