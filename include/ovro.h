@@ -400,6 +400,42 @@ int ovro_vet(const float* d_img, const double* d_stats, int n_chan, int image_si
              size_t ws_bytes, void* stream);
 
 /* -------------------------------------------------------------------------
+ * Drift-rate search (the paper's future work, Sections 2.3.4 and 4)
+ *
+ * Sub-integrations: the K spectra of an integration split into T = 2^k
+ * equal chunks (ovro_spectra_slice), each correlated, imaged and passed
+ * through ovro_detect_filter, give high-passed standardised cubes z'_t.
+ * For every in-horizon pixel and start channel f of coarse channel
+ * [c_lo, c_hi) the search sums z'_t along the Taylor tree's digital lines of
+ * total drift d, |d| < T: shift(d, 1, 0) = 0; shift(d, n, t) =
+ * shift(floor(d/2), n/2, t) for t < n/2, ceil(d/2) + shift(floor(d/2), n/2,
+ * t - n/2) otherwise; channel f + shift for d >= 0, f - shift for d < 0.
+ * A path counts only if its end f + d lies inside the coarse channel.
+ * SNR = sum / sqrt(T), the largest over drifts visited 0, +1, -1, +2, ...
+ * (strictly larger replaces).  Candidates: SNR >= n_sigma, then greedy NMS
+ * along frequency per (pixel, coarse channel) with half-width
+ * max(1, floor((|d| + 1) / 2)); records as ovro_candidate with width
+ * = |d| + 1 (channels the line crosses) and the signed drift in
+ * h_drift_out (channels per integration; Hz/s = d * df / integration time),
+ * ordered by (pixel, coarse channel, channel).
+ * ------------------------------------------------------------------------- */
+size_t ovro_drift_workspace_size(int n_chan, int image_size, int n_coarse, const int32_t* h_nfft);
+/* d_zp float [T][n_chan][N][N] (T = n_sub in {2, 4, 8, 16}); optional
+ * d_snr_or_null float [n_chan][N][N] (-inf below the horizon) and
+ * d_drift_or_null int32 [n_chan][N][N] maps.  Synchronises stream.
+ * OVRO_ERR_CAPACITY if more than max_out candidates (the first max_out are
+ * written, *n_out holds the true count) or a (pixel, coarse channel) pair
+ * holds more than 256 detections. */
+int ovro_drift_search(const float* d_zp, int n_sub, int n_chan, int image_size, double cell_dircos, int n_coarse,
+                      const int32_t* h_nfft, const double* h_chan_freq_hz, float n_sigma, float* d_snr_or_null,
+                      int32_t* d_drift_or_null, ovro_candidate* h_out, int32_t* h_drift_out, int max_out,
+                      int* n_out, void* d_ws, size_t ws_bytes, void* stream);
+/* d_out int8 [n_chan][count][n_input][2] = spectra s0 .. s0 + count - 1 of
+ * d_q int8 [n_chan][n_spec][n_input][2] (one sub-integration's block). */
+int ovro_spectra_slice(const int8_t* d_q, int n_chan, int n_spec, int n_input, int s0, int count, int8_t* d_out,
+                       void* stream);
+
+/* -------------------------------------------------------------------------
  * a13  Learned candidate scorer (no counterpart in the paper, which keeps or
  * drops Stage I triggers by threshold alone; the plain detector stays the
  * fallback and the judge of recall and false alarms).

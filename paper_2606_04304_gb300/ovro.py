@@ -104,6 +104,9 @@ def _load() -> ctypes.CDLL:
         "ovro_vet_default_params": (None, [P]),
         "ovro_vet_workspace_size": (S, [I, I]),
         "ovro_vet": (I, [P, P, I, I, D, I, P, P, P, I, ctypes.c_float, P, P, P, S, P]),
+        "ovro_drift_workspace_size": (S, [I, I, I, P]),
+        "ovro_drift_search": (I, [P, I, I, I, D, I, P, P, ctypes.c_float, P, P, P, P, I, P, P, S, P]),
+        "ovro_spectra_slice": (I, [P, I, I, I, I, I, P, P]),
         "ovro_autotune": (I, [I]),
         "ovro_tune_get": (I, [ctypes.c_char_p, P]),
         "ovro_tune_set": (I, [ctypes.c_char_p, I]),
@@ -143,7 +146,7 @@ def profile_query(kernel: str):
     return ms.value, n.value
 
 
-TRACED_KERNELS = ("k_upchan", "k_upchan_mr", "k_vet_line", "k_vet_fit", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
+TRACED_KERNELS = ("k_upchan", "k_upchan_mr", "k_vet_line", "k_vet_fit", "k_drift", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
                   "k_rank", "k_walk", "k_median_sub", "k_mf", "k_nms_warp")
 
 
@@ -407,6 +410,40 @@ def vet(img: torch.Tensor, stats: torch.Tensor, cell: float, nfft: Sequence[int]
         cd.ctypes.data_as(ctypes.c_void_p), cd.size, float(cut), None if params is None else ctypes.byref(params),
         out.ctypes.data_as(ctypes.c_void_p), _ptr(ws), ws.numel(), _stream(stream)))
     return out[: cd.size]
+
+
+# ------------------------------------------------------------ drift search
+def spectra_slice(q: torch.Tensor, n_chan: int, n_spec: int, n_input: int, s0: int, count: int,
+                  stream=None) -> torch.Tensor:
+    """int8 [n_chan][count][n_input][2]: spectra s0 .. s0+count-1 of q [n_chan][n_spec][n_input][2]."""
+    _cuda(q, torch.int8, "q")
+    out = torch.empty((n_chan, count, n_input, 2), dtype=torch.int8, device=q.device)
+    _check("ovro_spectra_slice", _lib.ovro_spectra_slice(_ptr(q), n_chan, n_spec, n_input, s0, count, _ptr(out),
+                                                         _stream(stream)))
+    return out
+
+
+def drift_search(zp: torch.Tensor, cell: float, nfft: Sequence[int], freqs_hz, n_sigma: float,
+                 want_maps: bool = False, max_out: int = 1 << 20, stream=None):
+    """zp float [T][n_chan][N][N] (high-passed standardised sub-integration cubes).
+    Returns (candidates CANDIDATE_DTYPE, signed drifts int32[, snr map, drift map])."""
+    _cuda(zp, torch.float32, "zp")
+    T, n_chan, n, _ = zp.shape
+    nf = _host(nfft, np.int32)
+    fr = _host(freqs_hz, np.float64)
+    ws = workspace(_lib.ovro_drift_workspace_size(n_chan, n, nf.size, nf.ctypes.data_as(ctypes.c_void_p)),
+                   zp.device)
+    snr = torch.empty((n_chan, n, n), dtype=torch.float32, device=zp.device) if want_maps else None
+    drm = torch.empty((n_chan, n, n), dtype=torch.int32, device=zp.device) if want_maps else None
+    out = np.zeros(max_out, CANDIDATE_DTYPE)
+    dr = np.zeros(max_out, np.int32)
+    n_out = ctypes.c_int(0)
+    _check("ovro_drift_search", _lib.ovro_drift_search(
+        _ptr(zp), T, n_chan, n, float(cell), nf.size, nf.ctypes.data_as(ctypes.c_void_p),
+        fr.ctypes.data_as(ctypes.c_void_p), float(n_sigma), _ptr(snr), _ptr(drm), out.ctypes.data_as(ctypes.c_void_p),
+        dr.ctypes.data_as(ctypes.c_void_p), max_out, ctypes.byref(n_out), _ptr(ws), ws.numel(), _stream(stream)))
+    k = n_out.value
+    return (out[:k], dr[:k], snr, drm) if want_maps else (out[:k], dr[:k])
 
 
 def detect_stats(img: torch.Tensor, cell: float, stream=None) -> torch.Tensor:

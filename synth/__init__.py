@@ -21,4 +21,5 @@ from .workloads import (  # noqa: F401
     pfb_prototype,
     substream,
     splitmix64,
+    tone_amplitude,
 )
