@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "tune.h"
 #include "upchan_impl.h"
 
 namespace ovro {
@@ -440,6 +441,29 @@ int launch_upchan(int log2n, const UpchanArgs& a, cudaStream_t st) {
   }
 }
 
+// G inputs per CTA from the autotuner: every G with F <= G <= 64 whose shared
+// memory fits (results do not depend on G).
+int launch_upchan_tuned(int l, UpchanArgs a, cudaStream_t st) {
+  const int F = l >= 13 ? 1 : (l < 4 ? 256 : (8192 >> l));
+  int np2 = 1;
+  while (np2 < a.n_input) np2 *= 2;
+  const int g0 = group_for(l, a.n_input);
+  std::vector<int> cands;
+  for (int g = F; g <= 64; g *= 2) {
+    if (g > np2 && g > F) break;
+    if (smem_for(l, g) <= (size_t(227) << 10)) cands.push_back(g);
+  }
+  auto run = [&](int g) -> int {
+    a.group = g;
+    return launch_upchan(l, a, st);
+  };
+  const std::string key = tune_key("k_upchan", {l, a.n_input});
+  int g = tuned(key, g0);
+  if (tuning(st) && cands.size() > 1)
+    if (int e = tune_pick(key, cands, run, st, &g)) return e;
+  return run(g);
+}
+
 struct UpchanWs {
   unsigned long long* power;
   float* scale;
@@ -486,9 +510,6 @@ int ovro_upchan_ex(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_t
   struct Coarse {
     int n, cnt, k;
     bool mixed;
-    MrPlan plan;
-    int group;
-    size_t smem;
   };
   std::vector<Coarse> cs(n_coarse);
   int max_pow2 = 2;
@@ -505,7 +526,10 @@ int ovro_upchan_ex(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_t
     if (static_cast<long long>(lo) + e.cnt > e.n) return OVRO_ERR_INVALID_ARG;
     e.mixed = taps || lo != 0 || e.cnt != e.n || !is_pow2(e.n) || e.n > kMaxN || k > 65535;
     if (e.mixed) {
-      if (!mr_plan(e.n, n_input, taps ? n_tap : 1, e.cnt, &e.plan, &e.group, &e.smem)) return OVRO_ERR_UNSUPPORTED;
+      MrPlan plan;
+      int group = 0;
+      size_t smem = 0;
+      if (!mr_plan(e.n, n_input, taps ? n_tap : 1, e.cnt, &plan, &group, &smem)) return OVRO_ERR_UNSUPPORTED;
     } else {
       if (e.n < 2) return OVRO_ERR_UNSUPPORTED;
       max_pow2 = std::max(max_pow2, e.n);
@@ -579,12 +603,9 @@ int ovro_upchan_ex(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_t
     a.chan_lo = lo;
     a.chan_cnt = e.cnt;
     if (e.mixed) {
-      a.group = e.group;
-      if (int err = launch_upchan_mr(a, e.plan, e.smem, st)) return err;
+      if (int err = launch_upchan_mr(a, a.n_tap, st)) return err;
     } else {
-      const int l = ilog2(n);
-      a.group = group_for(l, n_input);
-      if (int err = launch_upchan(l, a, st)) return err;
+      if (int err = launch_upchan_tuned(ilog2(n), a, st)) return err;
     }
     q_off += static_cast<long long>(e.cnt) * e.k * n_input * 2;
   }

@@ -41,7 +41,8 @@ struct MrPlan {
 // taps and C output channels: false if N is not such a length or no CTA shape fits.
 bool mr_plan(int n, int n_input, int n_tap, int chan_cnt, MrPlan* plan, int* group, size_t* smem);
 
-// One launch over every spectrum of one coarse channel (a.tw = omega_N table).
-int launch_upchan_mr(const UpchanArgs& a, const MrPlan& plan, size_t smem, cudaStream_t st);
+// One launch over every spectrum of one coarse channel (a.tw = omega_N table,
+// a.tw_n = N); the CTA shape comes from the autotuner, a.group is ignored.
+int launch_upchan_mr(const UpchanArgs& a, int n_tap, cudaStream_t st);
 
 }  // namespace ovro

@@ -4,6 +4,7 @@
 
 #include "common.cuh"
 #include "mixed_radix.cuh"
+#include "tune.h"
 #include "upchan_impl.h"
 
 namespace ovro {
@@ -132,9 +133,10 @@ constexpr unsigned kMrAll = radix_bit(2) | radix_bit(3) | radix_bit(4) | radix_b
 
 // SET: the radices this instantiation handles (a bit per radix).  Every radix
 // compiled in keeps some registers busy, so the common schedules get kernels
-// with just their own radices; kMrAll serves every other length.
-template <unsigned SET>
-__global__ void __launch_bounds__(kMrThreads, 1) k_upchan_mr(UpchanArgs a, MrPlan pl) {
+// with just their own radices; kMrAll serves every other length.  MINB: CTAs
+// per SM the register allocation leaves room for (the autotuner picks 1 or 2).
+template <unsigned SET, int MINB>
+__global__ void __launch_bounds__(kMrThreads, MINB) k_upchan_mr(UpchanArgs a, MrPlan pl) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = pl.n;
   const int F = pl.f;
@@ -318,9 +320,9 @@ bool mr_plan_impl(int n, int n_input, int p, int cnt, MrPlan* pl, int* group, si
   return false;
 }
 
-template <unsigned SET>
+template <unsigned SET, int MINB>
 int launch_mr_set(const UpchanArgs& a, const MrPlan& pl, size_t smem, cudaStream_t st) {
-  auto kern = k_upchan_mr<SET>;
+  auto kern = k_upchan_mr<SET, MINB>;
   OVRO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   dim3 grid((a.n_input + a.group - 1) / a.group, std::min(a.n_spec, 65535));
   OVRO_PROF("k_upchan_mr", st);
@@ -329,27 +331,84 @@ int launch_mr_set(const UpchanArgs& a, const MrPlan& pl, size_t smem, cudaStream
   return OVRO_OK;
 }
 
+constexpr unsigned k2400 = radix_bit(16) | radix_bit(15) | radix_bit(10);   // 2400 = 16 x 15 x 10
+constexpr unsigned kPow2a = radix_bit(16) | radix_bit(2);
+constexpr unsigned kPow2b = radix_bit(16) | radix_bit(4);
+constexpr unsigned kPow2c = radix_bit(16) | radix_bit(8);
+
+unsigned radix_set(const MrPlan& pl) {
+  unsigned set = 0;
+  for (int p = 0; p < pl.n_pass; ++p) set |= radix_bit(pl.radix[p]);
+  return set;
+}
+
+bool has_minb2(unsigned set) { return set == k2400 || set == kPow2a; }
+
+int launch_shape(const UpchanArgs& a, const MrPlan& pl, size_t smem, int minb, cudaStream_t st) {
+  const unsigned set = radix_set(pl);
+  if (minb == 2 && set == k2400) return launch_mr_set<k2400, 2>(a, pl, smem, st);
+  if (minb == 2 && set == kPow2a) return launch_mr_set<kPow2a, 2>(a, pl, smem, st);
+  switch (set) {
+    case k2400: return launch_mr_set<k2400, 1>(a, pl, smem, st);
+    case kPow2a: return launch_mr_set<kPow2a, 1>(a, pl, smem, st);
+    case kPow2b: return launch_mr_set<kPow2b, 1>(a, pl, smem, st);
+    case kPow2c: return launch_mr_set<kPow2c, 1>(a, pl, smem, st);
+    case radix_bit(16): return launch_mr_set<radix_bit(16), 1>(a, pl, smem, st);
+    default: return launch_mr_set<kMrAll, 1>(a, pl, smem, st);
+  }
+}
+
+// The plan for G inputs per CTA (F = min(largest F within the thread limit, G)).
+bool mr_shape(int n, int g, int p, int cnt, const MrPlan& base, int f_max, MrPlan* pl, size_t* smem) {
+  *pl = base;
+  pl->f = std::min(f_max, g);
+  pl->threads = mr_threads(n, pl->f, pl->radix, pl->n_pass);
+  *smem = mr_smem(n, pl->f, g, p, cnt);
+  return pl->threads <= kMrThreads && *smem <= (size_t(220) << 10);
+}
+
 }  // namespace
 
 bool mr_plan(int n, int n_input, int p, int cnt, MrPlan* pl, int* group, size_t* smem) {
   return mr_plan_impl(n, n_input, p, cnt, pl, group, smem);
 }
 
-int launch_upchan_mr(const UpchanArgs& a, const MrPlan& pl, size_t smem, cudaStream_t st) {
-  unsigned set = 0;
-  for (int p = 0; p < pl.n_pass; ++p) set |= radix_bit(pl.radix[p]);
-  constexpr unsigned k2400 = radix_bit(16) | radix_bit(15) | radix_bit(10);   // 2400 = 16 x 15 x 10
-  constexpr unsigned kPow2a = radix_bit(16) | radix_bit(2);
-  constexpr unsigned kPow2b = radix_bit(16) | radix_bit(4);
-  constexpr unsigned kPow2c = radix_bit(16) | radix_bit(8);
-  switch (set) {
-    case k2400: return launch_mr_set<k2400>(a, pl, smem, st);
-    case kPow2a: return launch_mr_set<kPow2a>(a, pl, smem, st);
-    case kPow2b: return launch_mr_set<kPow2b>(a, pl, smem, st);
-    case kPow2c: return launch_mr_set<kPow2c>(a, pl, smem, st);
-    case radix_bit(16): return launch_mr_set<radix_bit(16)>(a, pl, smem, st);
-    default: return launch_mr_set<kMrAll>(a, pl, smem, st);
+// Shape: G inputs per CTA and the register budget (1 or 2 CTAs per SM), from
+// the autotuner (every shape computes the same values in the same order).
+int launch_upchan_mr(const UpchanArgs& a_in, int n_tap, cudaStream_t st) {
+  const int n = a_in.tw_n;
+  MrPlan base;
+  int g0 = 1;
+  size_t sm0 = 0;
+  if (!mr_plan_impl(n, a_in.n_input, n_tap, a_in.chan_cnt, &base, &g0, &sm0)) return OVRO_ERR_UNSUPPORTED;
+  int f_max = 0;
+  for (int f = 4; f >= 1 && !f_max; f /= 2)
+    if (mr_threads(n, f, base.radix, base.n_pass) <= kMrThreads) f_max = f;
+  int np2 = 1;
+  while (np2 < a_in.n_input) np2 *= 2;
+  std::vector<int> cands;
+  const bool two = has_minb2(radix_set(base));
+  for (int g = 1; g <= 8; g *= 2) {
+    if (g > np2 && g > 1) break;
+    MrPlan pl;
+    size_t sm = 0;
+    if (!mr_shape(n, g, n_tap, a_in.chan_cnt, base, f_max, &pl, &sm)) continue;
+    cands.push_back(g * 4 + 1);
+    if (two) cands.push_back(g * 4 + 2);
   }
+  auto run = [&](int c) -> int {
+    UpchanArgs a = a_in;
+    a.group = c / 4;
+    MrPlan pl;
+    size_t sm = 0;
+    if (!mr_shape(n, a.group, n_tap, a.chan_cnt, base, f_max, &pl, &sm)) return OVRO_ERR_UNSUPPORTED;
+    return launch_shape(a, pl, sm, c % 4, st);
+  };
+  const std::string key = tune_key("k_upchan_mr", {n, a_in.n_input, n_tap, a_in.chan_cnt});
+  int choice = tuned(key, g0 * 4 + 1);
+  if (tuning(st) && cands.size() > 1)
+    if (int e = tune_pick(key, cands, run, st, &choice)) return e;
+  return run(choice);
 }
 
 }  // namespace ovro
