@@ -63,6 +63,11 @@ unsigned long long ovro_launch_count(void);
  * returns their summed device time and count. */
 int ovro_profile(int enable);
 int ovro_profile_query(const char* kernel, double* total_ms, int* launches);
+/* Measured ceiling of the gridder's accumulation on this GPU (a measurement
+ * aid): the taps per second of k_grid_rows's shared-memory atomic pattern
+ * (one 7x7 record per warp into a 32-row FP32 band) with no other work.
+ * Allocates 4 bytes, synchronises stream. */
+int ovro_probe_accumulate(double* h_gtaps_per_s, void* stream);
 
 /* -------------------------------------------------------------------------
  * a1-a3  Unpack + FFT upchannelizer + 8-bit requantisation

@@ -107,6 +107,7 @@ def _load() -> ctypes.CDLL:
         "ovro_drift_workspace_size": (S, [I, I, I, P]),
         "ovro_drift_search": (I, [P, I, I, I, D, I, P, P, ctypes.c_float, P, P, P, P, I, P, P, S, P]),
         "ovro_spectra_slice": (I, [P, I, I, I, I, I, P, P]),
+        "ovro_probe_accumulate": (I, [P, P]),
         "ovro_autotune": (I, [I]),
         "ovro_tune_get": (I, [ctypes.c_char_p, P]),
         "ovro_tune_set": (I, [ctypes.c_char_p, I]),
@@ -136,6 +137,13 @@ def launch_count() -> int:
 def profile(enable: bool) -> None:
     """Start (clearing the trace) or stop per-kernel CUDA-event tracing."""
     _check("ovro_profile", _lib.ovro_profile(1 if enable else 0))
+
+
+def probe_accumulate(stream=None) -> float:
+    """Measured ceiling of the gridder's shared-memory accumulation, taps/s."""
+    v = ctypes.c_double(0.0)
+    _check("ovro_probe_accumulate", _lib.ovro_probe_accumulate(ctypes.byref(v), _stream(stream)))
+    return v.value * 1e9
 
 
 def profile_query(kernel: str):
