@@ -350,15 +350,24 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restric
     const int S = walk_stride(nc, h);
     float* svp = sv + static_cast<long long>(p) * nc;
     uint32_t* sp = steps + static_cast<long long>(p) * S;
-    for (int k = threadIdx.x; k < S; k += blockDim.x) sp[k] = 0xffffffffu;
+    // four passes leave the sorted keys in ka and their channels in ia; once
+    // the sorted values are out, ka..kb (2 nc >= S words) holds the stream,
+    // built in shared memory and written out with coalesced stores
+    for (int r = threadIdx.x; r < nc; r += blockDim.x) svp[r] = key2f(ks[r]);
     __syncthreads();
-    uint16_t* sp16 = reinterpret_cast<uint16_t*>(sp);
+    uint32_t* stp = ka;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) stp[k] = 0xffffffffu;
+    __syncthreads();
+    uint16_t* st16 = reinterpret_cast<uint16_t*>(stp);
     for (int r = threadIdx.x; r < nc; r += blockDim.x) {
-      svp[r] = key2f(ks[r]);
       const int j = is[r];
-      sp16[2 * (j - h + H)] = static_cast<uint16_t>(r);
-      if (j + h + 1 < nc) sp16[2 * (j + h + 1 + H) + 1] = static_cast<uint16_t>(r);
+      st16[2 * (j - h + H)] = static_cast<uint16_t>(r);
+      if (j + h + 1 < nc) st16[2 * (j + h + 1 + H) + 1] = static_cast<uint16_t>(r);
     }
+    __syncthreads();
+    // S is a multiple of 4 and every pixel's stream starts 16-byte aligned
+    for (int k = threadIdx.x; k < S / 4; k += blockDim.x)
+      reinterpret_cast<uint4*>(sp)[k] = reinterpret_cast<const uint4*>(stp)[k];
     __syncthreads();
   }
 }
