@@ -427,10 +427,11 @@ def run_ours(args):
     # the first warm-up step runs eagerly under the autotuner (every candidate
     # shape gives the same results); the rest capture the graph with its choices
     for i in range(args.warmup):
-        if i == 0:
+        tune = i == 0 and not args.no_autotune
+        if tune:
             ovro.autotune(True)
         step()
-        if i == 0:
+        if tune:
             torch.cuda.synchronize()
             ovro.autotune(False)
     torch.cuda.synchronize()
@@ -507,7 +508,7 @@ def run_ours(args):
     # ---- the same X-engine contraction on the plain FP32 path (same int8
     # spectra, same visibilities): device time per step of each path
     xeng_cmp = None
-    if world == 1:
+    if world == 1 and not args.no_extras:
         qx = torch.empty(ovro.fine_elements(cfg.nfft, cfg.n_time, cfg.n_input), dtype=torch.int8, device=dev)
         ovro.upchan(volt, cfg.nfft, out_q=qx)
         outs, times = {}, {}
@@ -529,7 +530,8 @@ def run_ours(args):
                     "speedup": times["fp32_simt"] / times["int8_tc"], "bit_identical": same}
         del qx, outs
     d2h = int(len(c2)) * ovro.CANDIDATE_DTYPE.itemsize
-    next_rows = next_row_measurements(volt, cfg, n_kept_vis, kern, args.steps, dev) if world == 1 else None
+    next_rows = (next_row_measurements(volt, cfg, n_kept_vis, kern, args.steps, dev)
+                 if world == 1 and not args.no_extras else None)
 
     if rank == 0:
         peaks = _peaks()
@@ -600,6 +602,9 @@ def main():
     ap.add_argument("--xeng", default="tc", choices=["tc", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no tuning warm-up)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the X-engine comparison and the other rows' measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
