@@ -623,6 +623,24 @@ __global__ void k_gather_bin(const float* __restrict__ snr, long long n, uint32_
   }
 }
 
+// Values of every histogram bin b with want[b] != 0 in one pass (keys at or
+// above the top bin count as the top bin, as in k_gather_bin).
+__global__ void k_gather_bins(const float* __restrict__ snr, long long n, uint32_t key0, int nb,
+                              const uint8_t* __restrict__ want, float* __restrict__ out, int cap,
+                              int* __restrict__ count) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float v = snr[i];
+    const uint32_t kb = f2key(v) >> kHistShift;
+    if (kb < key0) continue;
+    const uint32_t b = min(kb - key0, static_cast<uint32_t>(nb - 1));
+    if (want[b]) {
+      const int slot = atomicAdd(count, 1);
+      if (slot < cap) out[slot] = v;
+    }
+  }
+}
+
 // One detection as the kernels hand it to the host.
 struct CandRec {
   int coarse, p, k, width;
@@ -1021,6 +1039,7 @@ struct DetectWs {
   int* ovf;
   CandRec* recs;
   int* count;            // [0] gathered values, [1] overflow pairs, [2] candidates
+  uint8_t* want;         // [kMaxBins] bins gathered in one pass
 };
 
 long long n_pairs_of(const DetectPlan& p) { return static_cast<long long>(p.n_valid) * p.n_coarse; }
@@ -1048,6 +1067,7 @@ DetectWs carve_detect(void* ws, size_t bytes, const DetectPlan& p, size_t* need)
   w.ovf = c.take<int>(np);
   w.recs = c.take<CandRec>(kCandCap);
   w.count = c.take<int>(4);
+  w.want = c.take<uint8_t>(kMaxBins);
   *need = c.used;
   return w;
 }
@@ -1253,24 +1273,66 @@ int gather_bin(const DetectWs& w, const DetectPlan& p, uint32_t key0, int nb, in
 }
 
 // Single-search cut.  Returns 0 with *cut set, 1 when nothing is rejected, or
-// an error status.
+// an error status.  Bins are visited upwards: the first bin every value of
+// which passes gives the cut; an open bin below it is resolved from its
+// values.  The values of all the open bins below that one are gathered in one
+// pass over the SNR cube (per bin if together they exceed the gather buffer).
 int bh_cut(const std::vector<unsigned long long>& hist, uint32_t key0, int nb, double m, double alpha,
            const DetectWs& w, const DetectPlan& p, cudaStream_t st, float* cut) {
+  std::vector<int> verdict(nb);
+  std::vector<float> lo(nb);
+  std::vector<unsigned long long> above(nb);
+  int b1 = nb;
+  unsigned long long open_total = 0;
+  int n_open = 0;
   for (int b = 0; b < nb; ++b) {
-    float lo;
-    unsigned long long above;
-    const int v = bh_bin_verdict(hist.data(), nb, key0, m, alpha, b, &lo, &above);
-    if (v == 0 || v == 3) continue;
-    if (v == 1) {
-      *cut = lo;
-      return 0;
+    verdict[b] = bh_bin_verdict(hist.data(), nb, key0, m, alpha, b, &lo[b], &above[b]);
+    if (verdict[b] == 1) {
+      b1 = b;
+      break;
     }
-    if (hist[b] > static_cast<unsigned long long>(kGatherCap)) return OVRO_ERR_CAPACITY;
-    std::vector<float> vals;
-    if (int e = gather_bin(w, p, key0, nb, b, vals, st)) return e;
+    if (verdict[b] == 2) {
+      open_total += hist[b];
+      ++n_open;
+    }
+  }
+  std::vector<std::vector<float>> bins(nb);
+  const bool one_pass = n_open > 1 && open_total <= static_cast<unsigned long long>(kGatherCap);
+  if (one_pass) {
+    std::vector<uint8_t> want(nb, 0);
+    for (int b = 0; b < b1; ++b) want[b] = verdict[b] == 2;
+    OVRO_CUDA_TRY(cudaMemcpyAsync(w.want, want.data(), nb, cudaMemcpyHostToDevice, st));
+    OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, sizeof(int), st));
+    k_gather_bins<<<8 * num_sms(), 256, 0, st>>>(w.snr, p.n_vox, key0, nb, w.want, w.vals, kGatherCap, w.count);
+    OVRO_LAUNCH_CHECK();
+    int nv = 0;
+    OVRO_CUDA_TRY(cudaMemcpyAsync(&nv, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+    if (static_cast<unsigned long long>(nv) != open_total) return OVRO_ERR_CAPACITY;
+    std::vector<float> all(nv);
+    if (nv) {
+      OVRO_CUDA_TRY(cudaMemcpyAsync(all.data(), w.vals, nv * sizeof(float), cudaMemcpyDeviceToHost, st));
+      OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    for (float v : all) {
+      const uint32_t kb = host_f2key(v) >> kHistShift;
+      bins[std::min<uint32_t>(kb - key0, static_cast<uint32_t>(nb - 1))].push_back(v);
+    }
+  }
+  for (int b = 0; b < b1; ++b) {
+    if (verdict[b] != 2) continue;
+    std::vector<float>& vals = bins[b];
+    if (!one_pass) {
+      if (hist[b] > static_cast<unsigned long long>(kGatherCap)) return OVRO_ERR_CAPACITY;
+      if (int e = gather_bin(w, p, key0, nb, b, vals, st)) return e;
+    }
     if (static_cast<unsigned long long>(vals.size()) != hist[b]) return OVRO_ERR_CAPACITY;
     std::sort(vals.begin(), vals.end(), std::greater<float>());
-    if (bh_resolve(vals.data(), static_cast<long long>(vals.size()), above, m, alpha, cut)) return 0;
+    if (bh_resolve(vals.data(), static_cast<long long>(vals.size()), above[b], m, alpha, cut)) return 0;
+  }
+  if (b1 < nb) {
+    *cut = lo[b1];
+    return 0;
   }
   return 1;
 }
