@@ -1272,6 +1272,22 @@ int gather_bin(const DetectWs& w, const DetectPlan& p, uint32_t key0, int nb, in
   return OVRO_OK;
 }
 
+// Values of one histogram bin in descending order.  Below the top bin every
+// key of the bin shares its upper 16 bits, so a counting sort over the lower
+// 16 bits orders them (keys are monotone in the value, equal keys equal values).
+void sort_bin_desc(std::vector<float>& v, bool top) {
+  if (top || v.size() < 4096) {
+    std::sort(v.begin(), v.end(), std::greater<float>());
+    return;
+  }
+  const uint32_t hi = host_f2key(v[0]) >> kHistShift;
+  std::vector<uint32_t> cnt(1u << kHistShift, 0);
+  for (float x : v) ++cnt[host_f2key(x) & ((1u << kHistShift) - 1)];
+  size_t o = 0;
+  for (int k = (1 << kHistShift) - 1; k >= 0; --k)
+    for (uint32_t c = cnt[k]; c; --c) v[o++] = host_key2f((hi << kHistShift) | static_cast<uint32_t>(k));
+}
+
 // Single-search cut.  Returns 0 with *cut set, 1 when nothing is rejected, or
 // an error status.  Bins are visited upwards: the first bin every value of
 // which passes gives the cut; an open bin below it is resolved from its
@@ -1327,7 +1343,7 @@ int bh_cut(const std::vector<unsigned long long>& hist, uint32_t key0, int nb, d
       if (int e = gather_bin(w, p, key0, nb, b, vals, st)) return e;
     }
     if (static_cast<unsigned long long>(vals.size()) != hist[b]) return OVRO_ERR_CAPACITY;
-    std::sort(vals.begin(), vals.end(), std::greater<float>());
+    sort_bin_desc(vals, b == nb - 1);
     if (bh_resolve(vals.data(), static_cast<long long>(vals.size()), above[b], m, alpha, cut)) return 0;
   }
   if (b1 < nb) {
