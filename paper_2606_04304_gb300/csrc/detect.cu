@@ -18,15 +18,17 @@
 //                    neighbourhood as register prefix sums and evaluates all 29
 //                    boxcars as prefix differences; keeps max SNR and width and
 //                    histograms the SNRs above the p = alpha floor.
-//  a11 host + k_gather_bin  Benjamini-Hochberg: counts above every histogram
-//                    bin edge are exact, so the step-up rule is decided bin by
-//                    bin in FP64; only a bin whose outcome the edges leave open
-//                    is gathered and ranked value by value.
+//  a11 host + k_gather_bins  Benjamini-Hochberg: counts above every
+//                    histogram bin edge are exact, so the step-up rule is
+//                    decided bin by bin in FP64; only the bins whose outcome
+//                    the edges leave open are gathered (one pass) and ranked
+//                    value by value.
 //  a12 k_nms_warp    greedy 1D non-maximum suppression per (pixel, coarse
 //      k_nms_big     channel) on the device, one warp per pair (one CTA with a
-//                    bitonic sort for pairs with many detections); a count
-//                    pass, a prefix sum and a write pass give the candidates
-//                    in (pixel, coarse, channel) order.
+//                    bitonic sort for pairs with many detections) in one
+//                    pass over the SNR cube, each pair's detections written to
+//                    a range reserved by an atomic; the host orders the pairs
+//                    (counting sort) into (pixel, coarse, channel) order.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -656,14 +658,14 @@ constexpr int kNmsWarps = 8;
 // greedy NMS repeatedly accepts the undecided detection of highest SNR
 // (lowest channel on ties) and suppresses the undecided ones within
 // max(1, w / 2) channels of it, w the accepted width -- the same decisions as
-// walking the list in descending SNR.  mode 0 counts the accepted detections
-// of each pair (pairs with more than kNmsCap detections go to the overflow
-// list and k_nms_big); mode 1 writes them, in channel order, at pair_off[q].
+// walking the list in descending SNR.  The accepted detections are written in
+// channel order to a range reserved with one atomic per pair (counters[1]);
+// pairs with more than kNmsCap detections go to the overflow list
+// (counters[0]) for k_nms_big.
 __global__ void __launch_bounds__(kNmsWarps * 32)
 k_nms_warp(const float* __restrict__ snr, const uint8_t* __restrict__ width, const long long* __restrict__ vox0,
-           const int* __restrict__ nfft, int n_coarse, long long n_pairs, float cut, int mode,
-           int* __restrict__ pair_cnt, const int* __restrict__ pair_off, int* __restrict__ ovf,
-           int* __restrict__ n_ovf, CandRec* __restrict__ out, int out_cap) {
+           const int* __restrict__ nfft, int n_coarse, long long n_pairs, float cut, int* __restrict__ ovf,
+           int* __restrict__ counters, CandRec* __restrict__ out, int out_cap) {
   __shared__ uint32_t lk[kNmsWarps][kNmsCap];       // (k << 8) | width
   __shared__ float lv[kNmsWarps][kNmsCap];
   __shared__ uint8_t st[kNmsWarps][kNmsCap];        // 0 undecided, 1 accepted, 2 suppressed
@@ -695,10 +697,7 @@ k_nms_warp(const float* __restrict__ snr, const uint8_t* __restrict__ width, con
     n += __popc(m);
   }
   if (over) {
-    if (mode == 0 && lane == 0) {
-      ovf[atomicAdd(n_ovf, 1)] = static_cast<int>(q);
-      pair_cnt[q] = 0;                              // k_nms_big writes the count
-    }
+    if (lane == 0) ovf[atomicAdd(counters, 1)] = static_cast<int>(q);   // for k_nms_big
     return;
   }
   __syncwarp();
@@ -725,11 +724,11 @@ k_nms_warp(const float* __restrict__ snr, const uint8_t* __restrict__ width, con
     __syncwarp();
     ++n_acc;
   }
-  if (mode == 0) {
-    if (lane == 0) pair_cnt[q] = n_acc;
-    return;
-  }
-  int j = pair_off[q];
+  // the pair's accepted detections go to a range reserved here, in channel
+  // order (pairs land in any order; the host orders them)
+  int j = 0;
+  if (lane == 0 && n_acc) j = atomicAdd(counters + 1, n_acc);
+  j = __shfl_sync(full, j, 0);
   for (int i0 = 0; i0 < n; i0 += 32) {
     const int i = i0 + lane;
     const bool a = i < n && S[i] == 1;
@@ -759,9 +758,8 @@ k_nms_warp(const float* __restrict__ snr, const uint8_t* __restrict__ width, con
 // bitmaps of nc_max bits.
 __global__ void __launch_bounds__(1024)
 k_nms_big(const float* __restrict__ snr, const uint8_t* __restrict__ width, const long long* __restrict__ vox0,
-          const int* __restrict__ nfft, int n_coarse, const int* __restrict__ ovf, const int* __restrict__ n_ovf,
-          int p2max, float cut, int mode, int* __restrict__ pair_cnt, const int* __restrict__ pair_off,
-          CandRec* __restrict__ out, int out_cap) {
+          const int* __restrict__ nfft, int n_coarse, const int* __restrict__ ovf, int* __restrict__ counters,
+          int p2max, float cut, CandRec* __restrict__ out, int out_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);       // [p2max]
   uint32_t* cov = reinterpret_cast<uint32_t*>(keys + p2max);                     // [p2max / 32]
@@ -769,7 +767,7 @@ k_nms_big(const float* __restrict__ snr, const uint8_t* __restrict__ width, cons
   uint32_t* scan = acc + p2max / 32;                                             // [1024]
   uint32_t* wtot = scan + 1024;                                                  // [32]
   __shared__ int s_n;
-  if (blockIdx.x >= *n_ovf) return;
+  if (blockIdx.x >= counters[0]) return;
   const int q = ovf[blockIdx.x];
   const int p = q / n_coarse, c = q - p * n_coarse;
   const int nc = nfft[c];
@@ -825,14 +823,19 @@ k_nms_big(const float* __restrict__ snr, const uint8_t* __restrict__ width, cons
   }
   __syncthreads();
   const int words = (nc + 31) / 32;
-  if (mode == 0) {
+  // reserve the pair's output range: count the accepted detections
+  {
     int my = 0;
     for (int i = tid; i < words; i += T) my += __popc(acc[i]);
     for (int o = 16; o; o >>= 1) my += __shfl_xor_sync(0xffffffffu, my, o);
-    if ((tid & 31) == 0 && my) atomicAdd(&pair_cnt[q], my);
-    return;
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    if ((tid & 31) == 0 && my) atomicAdd(&s_n, my);
+    __syncthreads();
+    if (tid == 0) s_n = s_n ? atomicAdd(counters + 1, s_n) : 0;
+    __syncthreads();
   }
-  int j0 = pair_off[q];
+  int j0 = s_n;
   for (int w0 = 0; w0 < words; w0 += T) {
     const int wi = w0 + tid;
     const uint32_t bits = wi < words ? acc[wi] : 0u;
@@ -860,72 +863,6 @@ k_nms_big(const float* __restrict__ snr, const uint8_t* __restrict__ width, cons
     __syncthreads();
     j0 += static_cast<int>(scan[0]);
     __syncthreads();
-  }
-}
-
-// Exclusive prefix sums of pair_cnt (n entries) into pair_off[0..n]: per-block
-// sums, a single-block scan of those, then the block offsets.
-constexpr int kScanPer = 4096;         // entries per block (1024 threads x 4)
-__global__ void k_scan_blocks(const int* __restrict__ a, long long n, int* __restrict__ sums) {
-  __shared__ int red[32];
-  const long long b0 = static_cast<long long>(blockIdx.x) * kScanPer;
-  int s = 0;
-  for (int i = threadIdx.x; i < kScanPer; i += blockDim.x)
-    if (b0 + i < n) s += a[b0 + i];
-  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) sums[blockIdx.x] = v;
-  }
-}
-
-__global__ void k_scan_sums(int* __restrict__ sums, int nb, int* __restrict__ total) {
-  // single block: exclusive scan of nb block sums, sequential per thread chunk
-  __shared__ uint32_t sc[1024];
-  __shared__ uint32_t wt[32];
-  const int T = blockDim.x, tid = threadIdx.x;
-  const int per = (nb + T - 1) / T;
-  uint32_t my = 0;
-  for (int i = tid * per; i < min(nb, (tid + 1) * per); ++i) my += static_cast<uint32_t>(sums[i]);
-  sc[tid] = my;
-  __syncthreads();
-  block_exclusive_scan(sc, T, wt);
-  uint32_t run = sc[tid];
-  for (int i = tid * per; i < min(nb, (tid + 1) * per); ++i) {
-    const uint32_t v = static_cast<uint32_t>(sums[i]);
-    sums[i] = static_cast<int>(run);
-    run += v;
-  }
-  if (tid == T - 1) *total = static_cast<int>(sc[tid] + my);
-}
-
-__global__ void k_scan_apply(const int* __restrict__ a, long long n, const int* __restrict__ sums,
-                             int* __restrict__ out) {
-  __shared__ uint32_t sc[1024];
-  __shared__ uint32_t wt[32];
-  const long long b0 = static_cast<long long>(blockIdx.x) * kScanPer;
-  const int T = blockDim.x, tid = threadIdx.x;
-  constexpr int per = kScanPer / 1024;
-  int v[per];
-  uint32_t my = 0;
-#pragma unroll
-  for (int j = 0; j < per; ++j) {
-    const long long i = b0 + static_cast<long long>(tid) * per + j;
-    v[j] = i < n ? a[i] : 0;
-    my += static_cast<uint32_t>(v[j]);
-  }
-  sc[tid] = my;
-  __syncthreads();
-  block_exclusive_scan(sc, T, wt);
-  int run = sums[blockIdx.x] + static_cast<int>(sc[tid]);
-#pragma unroll
-  for (int j = 0; j < per; ++j) {
-    const long long i = b0 + static_cast<long long>(tid) * per + j;
-    if (i < n) out[i] = run;
-    run += v[j];
   }
 }
 
@@ -1033,9 +970,6 @@ struct DetectWs {
   float* vals;
   long long* vox0;
   int* nfft;
-  int* pair_cnt;
-  int* pair_off;
-  int* sums;
   int* ovf;
   CandRec* recs;
   int* count;            // [0] gathered values, [1] overflow pairs, [2] candidates
@@ -1061,9 +995,6 @@ DetectWs carve_detect(void* ws, size_t bytes, const DetectPlan& p, size_t* need)
   w.vals = c.take<float>(kGatherCap);
   w.vox0 = c.take<long long>(p.n_coarse);
   w.nfft = c.take<int>(p.n_coarse);
-  w.pair_cnt = c.take<int>(np);
-  w.pair_off = c.take<int>(np + 1);
-  w.sums = c.take<int>((np + kScanPer - 1) / kScanPer + 1);
   w.ovf = c.take<int>(np);
   w.recs = c.take<CandRec>(kCandCap);
   w.count = c.take<int>(4);
@@ -1557,56 +1488,49 @@ int detect_ctx_candidates(DetectCtx* d, float cut, const double* h_chan_freq_hz,
   const int image_size = d->image_size;
   const long long np = n_pairs_of(p);
   if (np > 0x7fffffffLL / 2) return OVRO_ERR_UNSUPPORTED;
+  // one pass: each (pixel, coarse) pair's detections are written to a range
+  // reserved by atomics; w.count[1] counts overflowing pairs, w.count[2] the
+  // detections
   OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, 4 * sizeof(int), st));
   const unsigned nms_blocks = static_cast<unsigned>((np + kNmsWarps - 1) / kNmsWarps);
   {
     OVRO_PROF("k_nms_warp", st);
-    k_nms_warp<<<nms_blocks, kNmsWarps * 32, 0, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, np, cut, 0,
-                                                       w.pair_cnt, w.pair_off, w.ovf, w.count + 1, w.recs, kCandCap);
+    k_nms_warp<<<nms_blocks, kNmsWarps * 32, 0, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, np, cut, w.ovf,
+                                                       w.count + 1, w.recs, kCandCap);
     OVRO_LAUNCH_CHECK();
   }
-  int n_ovf = 0;
-  OVRO_CUDA_TRY(cudaMemcpyAsync(&n_ovf, w.count + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int cnt[2] = {0, 0};
+  OVRO_CUDA_TRY(cudaMemcpyAsync(cnt, w.count + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   OVRO_CUDA_TRY(cudaStreamSynchronize(st));
-  int p2max = 32;
-  while (p2max < p.max_nc) p2max <<= 1;
-  const size_t big_sm = static_cast<size_t>(p2max) * 8 + 2 * static_cast<size_t>(p2max / 32) * 4 + 1056 * 4;
-  if (n_ovf > 0) {
+  if (cnt[0] > 0) {
+    int p2max = 32;
+    while (p2max < p.max_nc) p2max <<= 1;
+    const size_t big_sm = static_cast<size_t>(p2max) * 8 + 2 * static_cast<size_t>(p2max / 32) * 4 + 1056 * 4;
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_nms_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(big_sm)));
-    k_nms_big<<<n_ovf, 1024, big_sm, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, w.ovf, w.count + 1, p2max,
-                                           cut, 0, w.pair_cnt, w.pair_off, w.recs, kCandCap);
+    k_nms_big<<<cnt[0], 1024, big_sm, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, w.ovf, w.count + 1, p2max,
+                                            cut, w.recs, kCandCap);
     OVRO_LAUNCH_CHECK();
+    OVRO_CUDA_TRY(cudaMemcpyAsync(cnt, w.count + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    OVRO_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  const unsigned sblocks = static_cast<unsigned>((np + kScanPer - 1) / kScanPer);
-  k_scan_blocks<<<sblocks, 1024, 0, st>>>(w.pair_cnt, np, w.sums);
-  OVRO_LAUNCH_CHECK();
-  k_scan_sums<<<1, 1024, 0, st>>>(w.sums, static_cast<int>(sblocks), w.count + 2);
-  OVRO_LAUNCH_CHECK();
-  k_scan_apply<<<sblocks, 1024, 0, st>>>(w.pair_cnt, np, w.sums, w.pair_off);
-  OVRO_LAUNCH_CHECK();
-  {
-    OVRO_PROF("k_nms_warp", st);
-    k_nms_warp<<<nms_blocks, kNmsWarps * 32, 0, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, np, cut, 1,
-                                                       w.pair_cnt, w.pair_off, w.ovf, w.count + 1, w.recs, kCandCap);
-    OVRO_LAUNCH_CHECK();
-  }
-  if (n_ovf > 0) {
-    k_nms_big<<<n_ovf, 1024, big_sm, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, w.ovf, w.count + 1, p2max,
-                                           cut, 1, w.pair_cnt, w.pair_off, w.recs, kCandCap);
-    OVRO_LAUNCH_CHECK();
-  }
-  int total = 0;
-  OVRO_CUDA_TRY(cudaMemcpyAsync(&total, w.count + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
-  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+  const int total = cnt[1];
   *n_out = total;
-  const int nw = std::min(std::min(total, max_out), kCandCap);
-  if (nw > 0) {
+  const int nw = std::min(total, kCandCap);
+  if (nw > 0 && max_out > 0) {
     std::vector<CandRec> recs(nw);
     OVRO_CUDA_TRY(cudaMemcpyAsync(recs.data(), w.recs, nw * sizeof(CandRec), cudaMemcpyDeviceToHost, st));
     OVRO_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int q = 0; q < nw; ++q) {
-      const CandRec& d = recs[q];
+    // (pixel, coarse) pair order, stable: a counting sort on q = p n_coarse + c
+    const long long n_q = np;
+    std::vector<int> start(static_cast<size_t>(n_q) + 1, 0);
+    for (const CandRec& d : recs) ++start[static_cast<size_t>(d.p) * p.n_coarse + d.coarse + 1];
+    for (long long q = 0; q < n_q; ++q) start[q + 1] += start[q];
+    std::vector<int> order(nw);
+    for (int i = 0; i < nw; ++i) order[start[static_cast<size_t>(recs[i].p) * p.n_coarse + recs[i].coarse]++] = i;
+    const int nout = std::min(nw, max_out);
+    for (int q = 0; q < nout; ++q) {
+      const CandRec& d = recs[order[q]];
       ovro_candidate& o = h_out[q];
       const int pixel = p.pix[d.p];
       o.coarse = d.coarse;
