@@ -1375,6 +1375,10 @@ struct DetectCtx {
   uint32_t key0 = 0;
   int nb = 0;
   int n_chan = 0, image_size = 0;
+  // host staging of the candidate records and their ordering, kept across
+  // calls (their pages stay mapped)
+  std::vector<CandRec> recs;
+  std::vector<int> q_start, order;
 };
 
 size_t detect_ctx_workspace(int n_chan, int image_size, int n_coarse, const int32_t* h_nfft) {
@@ -1518,31 +1522,34 @@ int detect_ctx_candidates(DetectCtx* d, float cut, const double* h_chan_freq_hz,
   *n_out = total;
   const int nw = std::min(total, kCandCap);
   if (nw > 0 && max_out > 0) {
-    std::vector<CandRec> recs(nw);
+    std::vector<CandRec>& recs = d->recs;
+    if (recs.size() < static_cast<size_t>(nw)) recs.resize(nw);
     OVRO_CUDA_TRY(cudaMemcpyAsync(recs.data(), w.recs, nw * sizeof(CandRec), cudaMemcpyDeviceToHost, st));
     OVRO_CUDA_TRY(cudaStreamSynchronize(st));
     // (pixel, coarse) pair order, stable: a counting sort on q = p n_coarse + c
     const long long n_q = np;
-    std::vector<int> start(static_cast<size_t>(n_q) + 1, 0);
-    for (const CandRec& d : recs) ++start[static_cast<size_t>(d.p) * p.n_coarse + d.coarse + 1];
+    std::vector<int>& start = d->q_start;
+    start.assign(static_cast<size_t>(n_q) + 1, 0);
+    for (int i = 0; i < nw; ++i) ++start[static_cast<size_t>(recs[i].p) * p.n_coarse + recs[i].coarse + 1];
     for (long long q = 0; q < n_q; ++q) start[q + 1] += start[q];
-    std::vector<int> order(nw);
+    std::vector<int>& order = d->order;
+    if (order.size() < static_cast<size_t>(nw)) order.resize(nw);
     for (int i = 0; i < nw; ++i) order[start[static_cast<size_t>(recs[i].p) * p.n_coarse + recs[i].coarse]++] = i;
     const int nout = std::min(nw, max_out);
     for (int q = 0; q < nout; ++q) {
-      const CandRec& d = recs[order[q]];
+      const CandRec& r = recs[order[q]];
       ovro_candidate& o = h_out[q];
-      const int pixel = p.pix[d.p];
-      o.coarse = d.coarse;
-      o.fine = d.k;
-      o.chan = p.chan0[d.coarse] + d.k;
+      const int pixel = p.pix[r.p];
+      o.coarse = r.coarse;
+      o.fine = r.k;
+      o.chan = p.chan0[r.coarse] + r.k;
       o.row = pixel / image_size;
       o.col = pixel % image_size;
-      o.width = d.width;
-      o.snr = d.snr;
+      o.width = r.width;
+      o.snr = r.snr;
       o.pad_ = 0.f;
       o.freq_hz = h_chan_freq_hz[o.chan];
-      o.log10_p = d.log10_p;
+      o.log10_p = r.log10_p;
     }
   }
   if (total > max_out) return OVRO_ERR_CAPACITY;

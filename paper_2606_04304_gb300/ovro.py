@@ -582,11 +582,15 @@ class Pipeline:
         _cuda(volt, torch.uint8, "volt")
         if volt.numel() != self.n_coarse * self.n_time * self.n_input:
             raise ValueError("volt must be [n_coarse][n_time][2 n_ant] uint8")
-        out = np.zeros(max_out, CANDIDATE_DTYPE)
+        # one host buffer per pipeline, its pages touched once (a fresh array
+        # every run would fault its pages in again); the result is a copy
+        if getattr(self, "_out", None) is None or self._out.size != max_out:
+            self._out = np.zeros(max_out, CANDIDATE_DTYPE)
+        out = self._out
         n_out = ctypes.c_int(0)
         _check("ovro_pipeline_run", _lib.ovro_pipeline_run(self._h, _ptr(volt), out.ctypes.data_as(ctypes.c_void_p),
                                                            max_out, ctypes.byref(n_out), _stream(stream)))
-        return out[: n_out.value]
+        return out[: min(n_out.value, max_out)].copy()
 
     def stats(self):
         k = ctypes.c_longlong(0)
