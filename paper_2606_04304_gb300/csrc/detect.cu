@@ -301,8 +301,9 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restric
   const unsigned lt_mask = (1u << lane) - 1u;
   for (int p = blockIdx.x; p < n_valid; p += gridDim.x) {
     const float* zp = z + static_cast<long long>(p) * nc;
+#pragma unroll 4
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-      ka[k] = f2key(zp[k]);
+      ka[k] = f2key(__ldg(zp + k));
       ia[k] = static_cast<uint16_t>(k);
     }
     uint32_t* ks = ka; uint32_t* kd = kb;
@@ -551,9 +552,28 @@ k_mf(const float* __restrict__ zbuf, int n_valid, int nc, float* __restrict__ sn
   for (int p = blockIdx.x; p < n_valid; p += gridDim.x) {
     const float* zp = zbuf + static_cast<long long>(p) * nc;
     __syncthreads();
-    for (int i = threadIdx.x; i < n_s; i += blockDim.x) {
-      const int k = i - kMaxLo;
-      s[mf_slot(i)] = (k >= 0 && k < nc) ? zp[k] : 0.f;
+    // stage the spectrum at slots kMaxLo .. kMaxLo + nc - 1, zeros around it;
+    // 16-byte loads, several in flight per thread
+    if ((nc & 3) == 0 && (reinterpret_cast<uintptr_t>(zp) & 15) == 0) {
+      const float4* z4 = reinterpret_cast<const float4*>(zp);
+      const int n4 = nc >> 2;
+#pragma unroll 4
+      for (int v = threadIdx.x; v < n4; v += blockDim.x) {
+        const float4 q = __ldg(z4 + v);
+        const int i = kMaxLo + 4 * v;
+        s[mf_slot(i)] = q.x;
+        s[mf_slot(i + 1)] = q.y;
+        s[mf_slot(i + 2)] = q.z;
+        s[mf_slot(i + 3)] = q.w;
+      }
+      for (int i = threadIdx.x; i < kMaxLo; i += blockDim.x) s[mf_slot(i)] = 0.f;
+      for (int i = kMaxLo + nc + threadIdx.x; i < n_s; i += blockDim.x) s[mf_slot(i)] = 0.f;
+    } else {
+#pragma unroll 4
+      for (int i = threadIdx.x; i < n_s; i += blockDim.x) {
+        const int k = i - kMaxLo;
+        s[mf_slot(i)] = (k >= 0 && k < nc) ? __ldg(zp + k) : 0.f;
+      }
     }
     __syncthreads();
     for (int k0 = threadIdx.x * kVox; k0 < nc; k0 += blockDim.x * kVox) {
