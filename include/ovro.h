@@ -58,7 +58,8 @@ unsigned long long ovro_launch_count(void);
 /* Kernel tracing.  ovro_profile(1) clears the trace and starts recording a
  * CUDA event pair on the launch stream around every launch of the main
  * kernels (k_upchan, k_upchan_mr, k_xeng_tc, k_xeng_simt, k_grid_rows, k_fft_cols,
- * k_stats, k_ztrans, k_rank, k_walk, k_mf); ovro_profile(0) stops recording.
+ * k_stats, k_ztrans, k_rank, k_walk, k_median_sub, k_mf, k_nms_warp, k_vet_line,
+ * k_vet_fit, k_drift, k_scorer_fwd); ovro_profile(0) stops recording.
  * ovro_profile_query waits for the recorded launches of one kernel and
  * returns their summed device time and count. */
 int ovro_profile(int enable);

@@ -154,7 +154,7 @@ def profile_query(kernel: str):
     return ms.value, n.value
 
 
-TRACED_KERNELS = ("k_upchan", "k_upchan_mr", "k_vet_line", "k_vet_fit", "k_drift", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
+TRACED_KERNELS = ("k_upchan", "k_upchan_mr", "k_vet_line", "k_vet_fit", "k_drift", "k_scorer_fwd", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
                   "k_rank", "k_walk", "k_median_sub", "k_mf", "k_nms_warp")
 
 
