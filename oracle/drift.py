@@ -23,7 +23,10 @@ tens of Hz over 30 s for transmitters on close-in planets).  The readings here:
 4. Per (pixel, channel) the search keeps the largest SNR over the 2T - 1
    drifts, visited in the order 0, +1, -1, +2, -2, ...; a later drift
    replaces the kept one only when strictly larger.
-5. Candidates: SNR >= n_sigma (a fixed threshold), then Stage I's greedy
+5. Candidates: Benjamini-Hochberg on p = Q(SNR) over every in-horizon
+   (pixel, channel), m = in-horizon pixels x channels (the maximum over drifts
+   taken like Stage I's maximum over widths, with no correction for the
+   trials), or a fixed threshold SNR >= n_sigma; then Stage I's greedy
    non-maximum suppression along frequency per pixel with the line's width
    in the integrated spectrum, |d| + 1 channels, as its width
    (half-width max(1, floor((|d| + 1) / 2))).
@@ -84,8 +87,9 @@ def drift_sums(zsub: np.ndarray, c_lo: int, c_hi: int):
     return out, order
 
 
-def drift_search(zsub: np.ndarray, mask: np.ndarray, nfft_list, n_sigma: float):
-    """(snr [n_chan][N][N], drift [n_chan][N][N], candidates).
+def drift_search(zsub: np.ndarray, mask: np.ndarray, nfft_list, n_sigma: float = 10.0, mode: str = "fixed",
+                 alpha: float = 0.01):
+    """(snr [n_chan][N][N], drift [n_chan][N][N], candidates, drifts).
 
     Pixels below the horizon hold snr = -inf, drift 0.  Candidates are
     oracle.detect.Candidate records whose width is |d| + 1, with the signed
@@ -107,7 +111,7 @@ def drift_search(zsub: np.ndarray, mask: np.ndarray, nfft_list, n_sigma: float):
         dr[lo:hi] = bd
     snr[:, ~mask] = -np.inf
     dr[:, ~mask] = 0
-    sel = (snr >= n_sigma) & mask[None]
+    sel = OD.select(snr, mask, mode, alpha, n_sigma)
     cands = OD.nms(sel, snr, np.abs(dr) + 1, OD.chan_bounds_of(nfft_list))
     drifts = [int(dr[c.chan, c.row, c.col]) for c in cands]
     return snr, dr, cands, drifts

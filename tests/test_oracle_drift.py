@@ -135,3 +135,28 @@ def test_nms_suppresses_along_the_drifting_line():
 
 def test_subint_bounds():
     assert DR.subint_bounds(29, 4) == [(0, 7), (7, 7), (14, 7), (21, 7)]
+
+
+def test_bh_mode_is_stage_one_selection_on_the_drift_map():
+    # the drift search's BH step is Stage I's selection applied to the map of
+    # maxima over drifts: same p-values, m = in-horizon pixels x channels
+    from oracle import detect as OD
+    T, F, n = 8, 48, 8
+    g = np.random.default_rng(21)
+    z = g.normal(size=(T, F, n, n))
+    tab = DR.shift_table(T)
+    for t in range(T):
+        z[t, 20 + tab[5, t], 3, 4] += 3.0
+    mask = np.ones((n, n), bool)
+    mask[0, 0] = False
+    snr, dr, cands, drifts = DR.drift_search(z, mask, [F], mode="bh", alpha=0.05)
+    sel = OD.select(snr, mask, "bh", 0.05)
+    lp = OD.log_p(snr[:, mask].ravel())
+    order = np.argsort(lp, kind="stable")
+    k = OD.bh_threshold(lp[order], mask.sum() * F, 0.05)
+    assert k > 0 and sel.sum() == k
+    assert (3, 4) in {(c.row, c.col) for c in cands}
+    assert all(sel[c.chan, c.row, c.col] for c in cands)
+    # fixed mode keeps its meaning
+    _, _, c10, _ = DR.drift_search(z, mask, [F], 10.0)
+    assert all(c.snr >= 10.0 for c in c10)
