@@ -418,7 +418,10 @@ int ovro_vet(const float* d_img, const double* d_stats, int n_chan, int image_si
  * t - n/2) otherwise; channel f + shift for d >= 0, f - shift for d < 0.
  * A path counts only if its end f + d lies inside the coarse channel.
  * SNR = sum / sqrt(T), the largest over drifts visited 0, +1, -1, +2, ...
- * (strictly larger replaces).  Candidates: SNR >= n_sigma, then greedy NMS
+ * (strictly larger replaces).  Candidates: Benjamini-Hochberg on p = Q(SNR)
+ * over every in-horizon (pixel, channel), m = in-horizon pixels x channels
+ * (params->mode OVRO_DETECT_BH, params->alpha; decided bin by bin as Stage
+ * I's), or SNR >= params->nsigma (OVRO_DETECT_FIXED); then greedy NMS
  * along frequency per (pixel, coarse channel) with half-width
  * max(1, floor((|d| + 1) / 2)); records as ovro_candidate with width
  * = |d| + 1 (channels the line crosses) and the signed drift in
@@ -430,12 +433,13 @@ size_t ovro_drift_workspace_size(int n_chan, int image_size, int n_coarse, const
  * d_snr_or_null float [n_chan][N][N] (-inf below the horizon) and
  * d_drift_or_null int32 [n_chan][N][N] maps.  Synchronises stream.
  * OVRO_ERR_CAPACITY if more than max_out candidates (the first max_out are
- * written, *n_out holds the true count) or a (pixel, coarse channel) pair
- * holds more than 256 detections. */
+ * written, *n_out holds the true count), a (pixel, coarse channel) pair
+ * holds more than 256 detections, or an open histogram bin more than 2^22
+ * values. */
 int ovro_drift_search(const float* d_zp, int n_sub, int n_chan, int image_size, double cell_dircos, int n_coarse,
-                      const int32_t* h_nfft, const double* h_chan_freq_hz, float n_sigma, float* d_snr_or_null,
-                      int32_t* d_drift_or_null, ovro_candidate* h_out, int32_t* h_drift_out, int max_out,
-                      int* n_out, void* d_ws, size_t ws_bytes, void* stream);
+                      const int32_t* h_nfft, const double* h_chan_freq_hz, const ovro_detect_params* params,
+                      float* d_snr_or_null, int32_t* d_drift_or_null, ovro_candidate* h_out, int32_t* h_drift_out,
+                      int max_out, int* n_out, void* d_ws, size_t ws_bytes, void* stream);
 /* d_out int8 [n_chan][count][n_input][2] = spectra s0 .. s0 + count - 1 of
  * d_q int8 [n_chan][n_spec][n_input][2] (one sub-integration's block). */
 int ovro_spectra_slice(const int8_t* d_q, int n_chan, int n_spec, int n_input, int s0, int count, int8_t* d_out,

@@ -47,13 +47,25 @@ __global__ void k_fill_snr(float* __restrict__ snr, int8_t* __restrict__ dr, lon
   }
 }
 
-// shift table: st[d * T + t], d, t < T (Taylor paths)
+// Histogram bins of the SNR for the Benjamini-Hochberg step: the
+// order-preserving 32-bit key of the FP32 value shifted right by 16 (the
+// binning of ovro_snr_bin_key and ovro_bh_layout).
+constexpr int kDriftHistShift = 16;
+constexpr int kDriftMaxBins = 2048;
+
+// shift table: st[d * T + t], d, t < T (Taylor paths).  With ghist, every
+// voxel's best SNR at or above the floor of bin 0 is counted in its bin
+// (values above the top bin in the top bin).
 __global__ void __launch_bounds__(32 * kDriftWarps)
 k_drift(const float* __restrict__ zp, int T, long long chan_stride, long long sub_stride,
         const int* __restrict__ pix, int n_valid, const DriftChunk* __restrict__ chunks,
-        const int* __restrict__ shift_tab, float inv_sqrt_t, float* __restrict__ snr, int8_t* __restrict__ dr) {
+        const int* __restrict__ shift_tab, float inv_sqrt_t, float* __restrict__ snr, int8_t* __restrict__ dr,
+        uint32_t hist_key0, int n_bins, unsigned long long* __restrict__ ghist) {
   extern __shared__ __align__(16) float tile[];      // [T][W][32]
   __shared__ int st[kMaxSub * kMaxSub];
+  __shared__ uint32_t shist[kDriftMaxBins];
+  if (ghist)
+    for (int i = threadIdx.x; i < n_bins; i += blockDim.x) shist[i] = 0u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const DriftChunk ck = chunks[blockIdx.y];
   const int p = blockIdx.x * 32 + lane;
@@ -70,8 +82,7 @@ k_drift(const float* __restrict__ zp, int T, long long chan_stride, long long su
     tile[(t * W + j) * 32 + lane] = v;
   }
   __syncthreads();
-  if (p >= n_valid) return;
-  for (int o = warp; o < kTileF; o += kDriftWarps) {
+  for (int o = warp; o < kTileF && p < n_valid; o += kDriftWarps) {
     const int f = ck.f0 + o;
     if (f >= ck.c_hi) break;
     const int j0 = o + (T - 1);
@@ -94,6 +105,33 @@ k_drift(const float* __restrict__ zp, int T, long long chan_stride, long long su
     const long long idx = static_cast<long long>(f) * chan_stride + px;
     snr[idx] = best;
     dr[idx] = static_cast<int8_t>(bd);
+    if (ghist) {
+      const uint32_t kb = f2key(best) >> kDriftHistShift;
+      if (kb >= hist_key0) atomicAdd(&shist[min(kb - hist_key0, static_cast<uint32_t>(n_bins - 1))], 1u);
+    }
+  }
+  if (ghist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_bins; i += blockDim.x)
+      if (shist[i]) atomicAdd(ghist + i, static_cast<unsigned long long>(shist[i]));
+  }
+}
+
+// Values of histogram bin b of the in-horizon map (the top bin takes every
+// larger key), for the exact step-up inside an open bin.
+__global__ void k_drift_gather(const float* __restrict__ snr, long long chan_stride, const int* __restrict__ pix,
+                               int n_valid, int n_chan, uint32_t kb, int top, float* __restrict__ out, int cap,
+                               int* __restrict__ count) {
+  const long long n = static_cast<long long>(n_valid) * n_chan;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long f = i / n_valid, p = i - f * n_valid;
+    const float v = snr[f * chan_stride + pix[p]];
+    const uint32_t k = f2key(v) >> kDriftHistShift;
+    if (k == kb || (top && k > kb)) {
+      const int slot = atomicAdd(count, 1);
+      if (slot < cap) out[slot] = v;
+    }
   }
 }
 
@@ -210,7 +248,11 @@ double log10_q(double x) {
   return ln / std::log(10.0);
 }
 
+constexpr int kDriftGatherCap = 1 << 22;
+
 struct DriftWs {
+  unsigned long long* hist;
+  float* vals;
   int* pix;
   int* shift;
   DriftChunk* chunks;
@@ -229,6 +271,8 @@ DriftWs carve_drift(void* ws, size_t bytes, int n_chan, int image_size, int n_co
   Carver c(ws, bytes);
   const long long npix = static_cast<long long>(image_size) * image_size;
   DriftWs w;
+  w.hist = c.take<unsigned long long>(kDriftMaxBins);
+  w.vals = c.take<float>(kDriftGatherCap);
   w.pix = c.take<int>(npix);
   w.shift = c.take<int>(kMaxSub * kMaxSub);
   w.chunks = c.take<DriftChunk>(std::max<long long>(n_chunks, 1));
@@ -261,13 +305,21 @@ size_t ovro_drift_workspace_size(int n_chan, int image_size, int n_coarse, const
 }
 
 int ovro_drift_search(const float* d_zp, int n_sub, int n_chan, int image_size, double cell_dircos, int n_coarse,
-                      const int32_t* h_nfft, const double* h_chan_freq_hz, float n_sigma, float* d_snr_or_null,
-                      int32_t* d_drift_or_null, ovro_candidate* h_out, int32_t* h_drift_out, int max_out,
-                      int* n_out, void* d_ws, size_t ws_bytes, void* stream) {
+                      const int32_t* h_nfft, const double* h_chan_freq_hz, const ovro_detect_params* params,
+                      float* d_snr_or_null, int32_t* d_drift_or_null, ovro_candidate* h_out, int32_t* h_drift_out,
+                      int max_out, int* n_out, void* d_ws, size_t ws_bytes, void* stream) {
   using namespace ovro;
-  if (!d_zp || !h_nfft || !h_chan_freq_hz || !n_out || n_chan <= 0 || image_size <= 0 || n_coarse <= 0 ||
-      !(cell_dircos > 0.0) || max_out < 0 || (max_out > 0 && (!h_out || !h_drift_out)))
+  if (!d_zp || !h_nfft || !h_chan_freq_hz || !n_out || !params || n_chan <= 0 || image_size <= 0 ||
+      n_coarse <= 0 || !(cell_dircos > 0.0) || max_out < 0 || (max_out > 0 && (!h_out || !h_drift_out)))
     return OVRO_ERR_INVALID_ARG;
+  const bool bh = params->mode == OVRO_DETECT_BH;
+  if (!bh && params->mode != OVRO_DETECT_FIXED) return OVRO_ERR_INVALID_ARG;
+  uint32_t key0 = 0;
+  int nb = 0;
+  if (bh) {
+    if (int e = ovro_bh_layout(params, &key0, &nb)) return e;
+    if (nb > kDriftMaxBins) return OVRO_ERR_UNSUPPORTED;
+  }
   if (n_sub < 2 || n_sub > kMaxSub || (n_sub & (n_sub - 1))) return OVRO_ERR_UNSUPPORTED;
   *n_out = 0;
   std::vector<int> lo(n_coarse), hi(n_coarse);
@@ -308,6 +360,7 @@ int ovro_drift_search(const float* d_zp, int n_sub, int n_chan, int image_size, 
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.c_lo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.c_hi, hi.data(), hi.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), st));
+  if (bh) OVRO_CUDA_TRY(cudaMemsetAsync(w.hist, 0, kDriftMaxBins * sizeof(unsigned long long), st));
   k_fill_snr<<<4 * num_sms(), 256, 0, st>>>(w.snr, w.dr, nvox);
   OVRO_LAUNCH_CHECK();
   if (n_valid > 0) {
@@ -318,14 +371,52 @@ int ovro_drift_search(const float* d_zp, int n_sub, int n_chan, int image_size, 
       OVRO_PROF("k_drift", st);
       k_drift<<<grid, 32 * kDriftWarps, sm, st>>>(d_zp, n_sub, npix, nvox, w.pix, n_valid, w.chunks, w.shift,
                                                    static_cast<float>(1.0 / std::sqrt(static_cast<double>(n_sub))),
-                                                   w.snr, w.dr);
+                                                   w.snr, w.dr, key0, nb, bh ? w.hist : nullptr);
       OVRO_LAUNCH_CHECK();
+    }
+    // the cut: the fixed threshold, or Benjamini-Hochberg over every
+    // in-horizon (pixel, channel), decided bin by bin as in Stage I
+    float cut = static_cast<float>(params->nsigma);
+    if (bh) {
+      std::vector<unsigned long long> hist(nb);
+      OVRO_CUDA_TRY(cudaMemcpyAsync(hist.data(), w.hist, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                    st));
+      OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+      const double m = static_cast<double>(n_valid) * n_chan;
+      bool found = false;
+      for (int b = 0; b < nb && !found; ++b) {
+        float lo = 0.f;
+        unsigned long long above = 0;
+        const int v = ovro_bh_bin_verdict(hist.data(), nb, key0, m, params->alpha, b, &lo, &above);
+        if (v == 0 || v == 3) continue;
+        if (v == 1) {
+          cut = lo;
+          found = true;
+          break;
+        }
+        if (hist[b] > static_cast<unsigned long long>(kDriftGatherCap)) return OVRO_ERR_CAPACITY;
+        OVRO_CUDA_TRY(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), st));
+        k_drift_gather<<<4 * num_sms(), 256, 0, st>>>(w.snr, npix, w.pix, n_valid, n_chan, key0 + b, b == nb - 1,
+                                                     w.vals, kDriftGatherCap, w.counters + 2);
+        OVRO_LAUNCH_CHECK();
+        int nv = 0;
+        OVRO_CUDA_TRY(cudaMemcpyAsync(&nv, w.counters + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+        if (static_cast<unsigned long long>(nv) != hist[b]) return OVRO_ERR_CAPACITY;
+        std::vector<float> vals(nv);
+        OVRO_CUDA_TRY(cudaMemcpyAsync(vals.data(), w.vals, nv * sizeof(float), cudaMemcpyDeviceToHost, st));
+        OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+        std::sort(vals.begin(), vals.end(), std::greater<float>());
+        if (ovro_bh_resolve(vals.data(), nv, above, m, params->alpha, &cut)) found = true;
+      }
+      if (!found) cut = INFINITY;                     // nothing is rejected
+      OVRO_CUDA_TRY(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), st));
     }
     const long long pairs = static_cast<long long>(n_valid) * n_coarse;
     const long long blocks = (pairs + kDriftWarps - 1) / kDriftWarps;
     if (blocks > 0x7fffffffLL) return OVRO_ERR_UNSUPPORTED;
     k_drift_nms<<<static_cast<unsigned>(blocks), 32 * kDriftWarps, 0, st>>>(
-        w.snr, w.dr, npix, w.pix, n_valid, w.c_lo, w.c_hi, n_coarse, n_sigma, w.cands, kDriftCandCap, w.counters);
+        w.snr, w.dr, npix, w.pix, n_valid, w.c_lo, w.c_hi, n_coarse, cut, w.cands, kDriftCandCap, w.counters);
     OVRO_LAUNCH_CHECK();
   }
   // optional maps for the caller

@@ -105,7 +105,7 @@ def _load() -> ctypes.CDLL:
         "ovro_vet_workspace_size": (S, [I, I]),
         "ovro_vet": (I, [P, P, I, I, D, I, P, P, P, I, ctypes.c_float, P, P, P, S, P]),
         "ovro_drift_workspace_size": (S, [I, I, I, P]),
-        "ovro_drift_search": (I, [P, I, I, I, D, I, P, P, ctypes.c_float, P, P, P, P, I, P, P, S, P]),
+        "ovro_drift_search": (I, [P, I, I, I, D, I, P, P, P, P, P, P, P, I, P, P, S, P]),
         "ovro_spectra_slice": (I, [P, I, I, I, I, I, P, P]),
         "ovro_probe_accumulate": (I, [P, P]),
         "ovro_autotune": (I, [I]),
@@ -431,10 +431,14 @@ def spectra_slice(q: torch.Tensor, n_chan: int, n_spec: int, n_input: int, s0: i
     return out
 
 
-def drift_search(zp: torch.Tensor, cell: float, nfft: Sequence[int], freqs_hz, n_sigma: float,
-                 want_maps: bool = False, max_out: int = 1 << 20, stream=None):
+def drift_search(zp: torch.Tensor, cell: float, nfft: Sequence[int], freqs_hz, n_sigma: Optional[float] = None,
+                 want_maps: bool = False, max_out: int = 1 << 20, stream=None, params: Optional[DetectParams] = None):
     """zp float [T][n_chan][N][N] (high-passed standardised sub-integration cubes).
-    Returns (candidates CANDIDATE_DTYPE, signed drifts int32[, snr map, drift map])."""
+    n_sigma: a fixed threshold; otherwise params (default Benjamini-Hochberg,
+    alpha 0.01).  Returns (candidates CANDIDATE_DTYPE, signed drifts int32[, snr
+    map, drift map])."""
+    if params is None:
+        params = detect_params(mode=DETECT_FIXED, nsigma=n_sigma) if n_sigma is not None else detect_params()
     _cuda(zp, torch.float32, "zp")
     T, n_chan, n, _ = zp.shape
     nf = _host(nfft, np.int32)
@@ -448,7 +452,8 @@ def drift_search(zp: torch.Tensor, cell: float, nfft: Sequence[int], freqs_hz, n
     n_out = ctypes.c_int(0)
     _check("ovro_drift_search", _lib.ovro_drift_search(
         _ptr(zp), T, n_chan, n, float(cell), nf.size, nf.ctypes.data_as(ctypes.c_void_p),
-        fr.ctypes.data_as(ctypes.c_void_p), float(n_sigma), _ptr(snr), _ptr(drm), out.ctypes.data_as(ctypes.c_void_p),
+        fr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(params), _ptr(snr), _ptr(drm),
+        out.ctypes.data_as(ctypes.c_void_p),
         dr.ctypes.data_as(ctypes.c_void_p), max_out, ctypes.byref(n_out), _ptr(ws), ws.numel(), _stream(stream)))
     k = n_out.value
     return (out[:k], dr[:k], snr, drm) if want_maps else (out[:k], dr[:k])

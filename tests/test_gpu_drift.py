@@ -101,3 +101,22 @@ def test_drifting_tone_end_to_end(lib):
     _, _, rc, rdr = DR.drift_search(zsub.cpu().numpy().astype(np.float64), mask, cfg.nfft, 8.0)
     assert sorted((c.chan, c.row, c.col, dd) for c, dd in zip(rc, rdr)) == \
         sorted((int(c["chan"]), int(c["row"]), int(c["col"]), int(dd)) for c, dd in zip(cands, drifts))
+
+
+@pytest.mark.parametrize("T,alpha", [(4, 0.01), (8, 0.05)])
+def test_bh_mode_against_oracle(lib, T, alpha):
+    # Benjamini-Hochberg over the map of maxima over drifts, m = in-horizon
+    # pixels x channels, decided bin by bin on the GPU: the oracle's selection
+    n, nfft = 32, [96, 64]
+    cell = 2.0 / n
+    a = 12.0 / math.sqrt(T) + 1.0
+    tones = [(30, T - 1, 10, 12, a), (70, -(T // 2), 20, 9, a + 1), (100, 0, 16, 16, a + 2)]
+    z = _cube(T + 100, T, nfft, n, tones)
+    freqs = synth.fine_freqs_hz(nfft)
+    prm = lib.detect_params(alpha=alpha)
+    cands, drifts = lib.drift_search(torch.from_numpy(z).cuda(), cell, nfft, freqs, params=prm)
+    mask = OI.horizon_mask(n, cell)
+    _, _, rc, rdr = DR.drift_search(z.astype(np.float64), mask, nfft, mode="bh", alpha=alpha)
+    assert len(rc) > 0
+    got = sorted((int(x["chan"]), int(x["row"]), int(x["col"]), int(d)) for x, d in zip(cands, drifts))
+    assert got == sorted((x.chan, x.row, x.col, int(d)) for x, d in zip(rc, rdr))
