@@ -124,7 +124,6 @@ constexpr int kTcThreads = 128;
 constexpr uint32_t kLBO = 128;            // bytes between K-adjacent core matrices
 constexpr uint32_t kSBO = (kTcKc / 8) * 128;  // bytes between 8-row groups
 constexpr int kTcASmem = kTcM * kTcKc * 2;    // 16 KB
-constexpr int kTcBSmem = kTcN * kTcKc * 2;    // 32 KB
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s bound on any wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
