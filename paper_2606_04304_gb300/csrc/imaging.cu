@@ -222,7 +222,7 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
   float4* r_hdr = reinterpret_cast<float4*>(tw + G);                  // [kRecMax] (Vr, Vi, base, kv_rel)
   float2* r_wu = reinterpret_cast<float2*>(r_hdr + kRecMax);          // [kRecMax][kWuStride]
   float* r_wv = reinterpret_cast<float*>(r_wu + kRecMax * kWuStride); // [kRecMax][kWvStride]
-  __shared__ int n_home, n_rec;
+  __shared__ int n_home, n_rec[2];
   const int b = blockIdx.x, cb = blockIdx.y;
   const long long chan = ch0 + cb;
   for (int i = threadIdx.x; i < (2 * band_h * P) / 4; i += blockDim.x)
@@ -237,22 +237,38 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
   const int axis = threadIdx.x & 1;                  // 0: u, 1: v
   const int chunk = blockDim.x >> 1;
   const unsigned full = 0xffffffffu;
-  const int4* vis4 = reinterpret_cast<const int4*>(vis);
   int my_home = 0;
   const int e0 = band_off[b], e1 = band_off[b + 1];
-  for (int c0 = e0; c0 < e1; c0 += chunk) {
-    if (threadIdx.x == 0) n_rec = 0;
-    __syncthreads();
-    // ---- prepare: one visibility per thread pair
-    const int e = c0 + (threadIdx.x >> 1);
-    const bool valid = e < e1;
-    GridEntry en{};
-    if (valid) en = entries[e];
+  const int pair = threadIdx.x >> 1;
+  // the fields of a candidate entry one thread of a pair needs
+  struct Ent {
+    int bl, cross, a, bf;
+    float h, l;                                      // this thread's axis, float-float
+  };
+  auto load_ent = [&](int e) {
+    Ent x{};
+    if (e < e1) {
+      const int4 hd = __ldg(reinterpret_cast<const int4*>(entries + e));
+      const float2 d = __ldg(reinterpret_cast<const float2*>(&entries[e].dxh) + axis);
+      x.bl = hd.x; x.cross = hd.y; x.a = hd.z; x.bf = hd.w;
+      x.h = d.x; x.l = d.y;
+    }
+    return x;
+  };
+  // a chunk's keep test and the loads its records need, taken one chunk ahead
+  struct Keep {
+    int cu, cv, off;
+    bool use;
+    int2 q;                                          // XX (even thread) or YY (odd thread)
+    float2 ca, cb;                                   // calibration corrections
+  };
+  auto keep_test = [&](const Ent& en, bool valid) {
+    Keep k{};
     int cc = 0, off = 0;
     bool in = false;
     if (valid) {
       int pc;
-      if (!fast_rint_prod32(axis ? en.dyh : en.dxh, axis ? en.dyl : en.dxl, s, &pc)) {
+      if (!fast_rint_prod32(en.h, en.l, s, &pc)) {
         const Baseline B = base[en.cross];           // FP64 product of the definition
         const long long pl = __double2ll_rn(__dmul_rn(axis ? B.dy : B.dx, s.s));
         pc = static_cast<int>(pl > lim ? lim : (pl < -lim ? -lim : pl));
@@ -269,51 +285,63 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
     }
     const int cc_o = __shfl_xor_sync(full, cc, 1);
     const int in_o = __shfl_xor_sync(full, in ? 1 : 0, 1);   // every lane takes part
-    const bool keep = in && in_o;
-    const int cu = axis ? cc_o : cc, cv = axis ? cc : cc_o;
-    const int kv_home = G / 2 + cv;
+    const bool kp = in && in_o;
+    k.cu = axis ? cc_o : cc;
+    k.cv = axis ? cc : cc_o;
+    k.off = off;
+    const int kv_home = G / 2 + k.cv;
     const int kv_rel = kv_home - kHalfSup - row0;
-    const int ku0 = G / 2 + cu - kHalfSup;
-    if (keep && axis && kv_home >= row0 && kv_home < row0 + band_h) ++my_home;
-    const bool use = keep && kv_rel + kSupport > 0 && kv_rel < band_h;
+    if (kp && axis && kv_home >= row0 && kv_home < row0 + band_h) ++my_home;
+    k.use = kp && kv_rel + kSupport > 0 && kv_rel < band_h;
+    if (k.use) {
+      k.q = __ldg(reinterpret_cast<const int2*>(vis) + (chan * n_bl + en.bl) * 4 + axis * 3);
+      if (CAL && opt.gains != nullptr) {
+        const float2* gc = opt.gains + chan * opt.n_input;
+        k.ca = __ldg(gc + 2 * en.a + axis);
+        k.cb = __ldg(gc + 2 * (en.bf & 0xffff) + axis);
+      }
+    }
+    return k;
+  };
+  if (threadIdx.x == 0) n_rec[0] = 0;
+  Keep kn = keep_test(load_ent(e0 + pair), e0 + pair < e1);
+  Ent en = load_ent(e0 + chunk + pair);
+  __syncthreads();
+  int it = 0;
+  for (int c0 = e0; c0 < e1; c0 += chunk, ++it) {
+    // ---- records of this chunk: one visibility per thread pair
     // Stokes I = (XX + YY) / 2: XX on the even thread, YY on the odd one;
     // exact integer sums, or with the calibration corrections c_a conj(c_b)
     // applied per polarisation in FP32
+    const Keep k = kn;
     float fr, fi;
     if (!CAL || opt.gains == nullptr) {
-      int sr = 0, si = 0;
-      if (use) {
-        const int4 q = __ldg(vis4 + (chan * n_bl + en.bl) * 2 + axis);
-        sr = axis ? q.z : q.x;
-        si = axis ? q.w : q.y;
-      }
-      sr += __shfl_xor_sync(full, sr, 1);
-      si += __shfl_xor_sync(full, si, 1);
+      const int sr = k.q.x + __shfl_xor_sync(full, k.q.x, 1);
+      const int si = k.q.y + __shfl_xor_sync(full, k.q.y, 1);
       fr = static_cast<float>(sr);
       fi = static_cast<float>(si);
     } else {
       float pr = 0.f, pi = 0.f;
-      if (use) {
-        const int4 q = __ldg(vis4 + (chan * n_bl + en.bl) * 2 + axis);
-        const float vr = static_cast<float>(axis ? q.z : q.x), vi = static_cast<float>(axis ? q.w : q.y);
-        const float2* gc = opt.gains + chan * opt.n_input;
-        const float2 ca = __ldg(gc + 2 * en.a + axis), cbb = __ldg(gc + 2 * (en.bf & 0xffff) + axis);
-        const float gr = ca.x * cbb.x + ca.y * cbb.y, gi = ca.y * cbb.x - ca.x * cbb.y;
+      if (k.use) {
+        const float vr = static_cast<float>(k.q.x), vi = static_cast<float>(k.q.y);
+        const float gr = k.ca.x * k.cb.x + k.ca.y * k.cb.y, gi = k.ca.y * k.cb.x - k.ca.x * k.cb.y;
         pr = gr * vr - gi * vi;
         pi = gr * vi + gi * vr;
       }
       fr = pr + __shfl_xor_sync(full, pr, 1);
       fi = pi + __shfl_xor_sync(full, pi, 1);
     }
-    const unsigned m = __ballot_sync(full, use) & 0x55555555u;
+    const unsigned m = __ballot_sync(full, k.use) & 0x55555555u;
     int base_slot = 0;
-    if (lane == 0 && m) base_slot = atomicAdd(&n_rec, __popc(m));
+    if (lane == 0 && m) base_slot = atomicAdd(&n_rec[it & 1], __popc(m));
     base_slot = __shfl_sync(full, base_slot, 0);
-    if (use) {
+    if (k.use) {
       const int slot = base_slot + __popc(m & ((1u << (lane & ~1)) - 1u));
+      const int kv_rel = G / 2 + k.cv - kHalfSup - row0;
+      const int ku0 = G / 2 + k.cu - kHalfSup;
       float w[8];
 #pragma unroll
-      for (int t = 0; t < kSupport; ++t) w[t] = __ldg(tab + kHalfTab + (t - kHalfSup) * kQ - off);
+      for (int t = 0; t < kSupport; ++t) w[t] = __ldg(tab + kHalfTab + (t - kHalfSup) * kQ - k.off);
       w[7] = 0.0f;
       if (axis == 0) {
         // (-1)^ku centring sign; conj of Stokes I: the exp(+) transform is a
@@ -334,8 +362,13 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
       }
     }
     __syncthreads();
+    const int nr = n_rec[it & 1];
+    if (threadIdx.x == 0) n_rec[(it + 1) & 1] = 0;   // last read before the previous barrier
+    // ---- the next chunk's keep test, visibility loads and the entries after
+    // it, in flight while this chunk is swept
+    kn = keep_test(en, c0 + chunk + pair < e1);
+    en = load_ent(c0 + 2 * chunk + pair);
     // ---- sweep: one record per warp, 49 taps in four atomic instructions
-    const int nr = n_rec;
     const int tv = lane >> 2, tu = lane & 3;
     for (int rec = warp; rec < nr; rec += n_warps) {
       const float4 hd = r_hdr[rec];
@@ -400,61 +433,103 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
   }
 }
 
-// One complex value of the half-transformed grid in FP32.
-// (read-only path: h is not written while the column pass runs)
+// Two adjacent values (idx even) of the half-transformed grid in FP32.
 template <int S>
-__device__ __forceinline__ float2 load_h(const void* h, const float* hs, long long row, long long idx) {
+__device__ __forceinline__ void load_h2(const void* h, const float* hs, long long row, long long idx, float2& v0,
+                                        float2& v1) {
   if constexpr (S == kStoreF32) {
-    return __ldg(static_cast<const float2*>(h) + idx);
-  } else if constexpr (S == kStoreBF16) {
-    const unsigned raw = __ldg(static_cast<const unsigned*>(h) + idx);
-    __nv_bfloat162 b;
-    memcpy(&b, &raw, sizeof(b));
-    return __bfloat1622float2(b);
+    const float4 q = __ldg(reinterpret_cast<const float4*>(static_cast<const float2*>(h) + idx));
+    v0 = make_float2(q.x, q.y);
+    v1 = make_float2(q.z, q.w);
   } else {
-    const unsigned raw = __ldg(static_cast<const unsigned*>(h) + idx);
-    __half2 b;
-    memcpy(&b, &raw, sizeof(b));
-    const float2 v = __half22float2(b);
-    const float s = __ldg(hs + row);
-    return make_float2(v.x * s, v.y * s);
+    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(static_cast<const unsigned*>(h) + idx));
+    if constexpr (S == kStoreBF16) {
+      __nv_bfloat162 b0, b1;
+      memcpy(&b0, &raw.x, sizeof(b0));
+      memcpy(&b1, &raw.y, sizeof(b1));
+      v0 = __bfloat1622float2(b0);
+      v1 = __bfloat1622float2(b1);
+    } else {
+      __half2 b0, b1;
+      memcpy(&b0, &raw.x, sizeof(b0));
+      memcpy(&b1, &raw.y, sizeof(b1));
+      const float sc = __ldg(hs + row);
+      v0 = __half22float2(b0);
+      v1 = __half22float2(b1);
+      v0 = make_float2(v0.x * sc, v0.y * sc);
+      v1 = make_float2(v1.x * sc, v1.y * sc);
+    }
   }
 }
 
 // Column transforms of the N central columns and the image itself.
-// 1024 threads only for 16-bit storage at G = 2048 (8 columns per CTA)
+//
+// The image is the real part of the transform.  The real part of the DFT of a
+// column c is the DFT of its Hermitian part (c(k) + conj c(-k)) / 2 (indices
+// mod G), whose DFT is real; so two columns c1, c2 share one complex FFT of
+// d = h1 + i h2, with DFT Re DFT(c1) + i Re DFT(c2).  d is formed, doubled,
+// while the column pair is read (rows k and G - k together), and the output
+// scale takes the factor 1/2 back.  C columns per CTA, C / 2 transforms.
 template <int LOG2G, int S>
-__global__ void __launch_bounds__((S != kStoreF32 && LOG2G == 11) ? 1024 : 512)
+__global__ void __launch_bounds__(512, 2)
 k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, int cols_per_cta, int ch0,
            const float2* __restrict__ tw_g, const float* __restrict__ inv_corr,
            const uint8_t* __restrict__ mask, const int* __restrict__ kept, float* __restrict__ img) {
   constexpr int G = 1 << LOG2G;
   constexpr int LDP = band_pitch(G);
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* A = reinterpret_cast<float2*>(smem);        // [C][LDP]
-  float2* tw = A + cols_per_cta * LDP;
-  const int C = cols_per_cta;
+  const int C = cols_per_cta, CP = C / 2;
+  float2* A = reinterpret_cast<float2*>(smem);        // [C / 2][LDP]: packed column pairs
+  float2* tw = A + CP * LDP;
   const int cb = blockIdx.y;
   const int c0 = blockIdx.x * C;
   const long long hrow0 = static_cast<long long>(cb) * G;
   for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
-  for (int i = threadIdx.x; i < G * C; i += blockDim.x) {
-    const int r = i / C, c = i - r * C;
-    A[c * LDP + pad16(r)] = load_h<S>(h, hs, hrow0 + r, (hrow0 + r) * n_img + c0 + c);
+  // U items per thread in flight: the reads come from L2 and would otherwise
+  // wait one round trip each
+  constexpr int U = 4;
+  const int n_items = (G / 2 + 1) * CP;
+  for (int i0 = threadIdx.x; i0 < n_items; i0 += U * blockDim.x) {
+    float2 a[U], e[U], b[U], f[U];                    // c1(k), c2(k), c1(-k), c2(-k)
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n_items) {
+        const int k = i / CP, p = i - k * CP;
+        const int km = (G - k) & (G - 1);
+        load_h2<S>(h, hs, hrow0 + k, (hrow0 + k) * n_img + c0 + 2 * p, a[u], e[u]);
+        load_h2<S>(h, hs, hrow0 + km, (hrow0 + km) * n_img + c0 + 2 * p, b[u], f[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n_items) {
+        const int k = i / CP, p = i - k * CP;
+        const int km = (G - k) & (G - 1);
+        A[p * LDP + pad16(k)] =
+            make_float2((a[u].x + b[u].x) - (e[u].y - f[u].y), (a[u].y - b[u].y) + (e[u].x + f[u].x));
+        if (km != k)
+          A[p * LDP + pad16(km)] =
+              make_float2((b[u].x + a[u].x) - (f[u].y - e[u].y), (b[u].y - a[u].y) + (f[u].x + e[u].x));
+      }
+    }
   }
   __syncthreads();
   fft_rows_inplace<LOG2G>(A, LDP, tw);
   const long long chan = ch0 + cb;
   const int k = kept[chan];
-  const float norm = k > 0 ? 1.0f / static_cast<float>(k) : 0.0f;
+  const float norm = k > 0 ? 0.5f / static_cast<float>(k) : 0.0f;
   const int off = G / 2 - n_img / 2;
   float* out = img + chan * n_img * n_img;
+#pragma unroll 4
   for (int i = threadIdx.x; i < n_img * C; i += blockDim.x) {
     const int r = i / C, c = i - r * C;
     const int col = c0 + c;
     float v = 0.0f;
     if (mask[r * n_img + col]) {
-      v = A[c * LDP + pad16(off + r)].x * norm * inv_corr[r] * inv_corr[col];
+      const float2 z = A[(c >> 1) * LDP + pad16(off + r)];
+      v = (c & 1 ? z.y : z.x) * norm * inv_corr[r] * inv_corr[col];
       if ((r + col) & 1) v = -v;
     }
     out[static_cast<long long>(r) * n_img + col] = v;
@@ -506,10 +581,11 @@ ImgPlan make_plan(int n_ant, int n_chan, int n, int storage) {
   if (b > 64) b = 64;
   if (b > n_chan) b = n_chan;
   p.batch = static_cast<int>(b);
+  // an even number of columns per CTA (the column pass pairs them)
   int c = 8192 / p.g;
   // 16-bit storage: at least 8 columns per CTA, so each row segment the
   // column pass reads is a whole 32-byte sector
-  if (storage != kStoreF32 && c < 8 && 8 * p.g / 16 <= 1024) c = 8;
+  if (storage != kStoreF32 && c < 8 && 8 * p.g / 32 <= 512) c = 8;
   if (c > n) c = n;
   p.cols_per_cta = c;
   return p;
@@ -644,10 +720,10 @@ int launch_bands(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int3
     OVRO_LAUNCH_CHECK();
   }
   {
-    const size_t sm = static_cast<size_t>(p.cols_per_cta) * LDP * sizeof(float2) + G * sizeof(float2);
+    const size_t sm = static_cast<size_t>(p.cols_per_cta / 2) * LDP * sizeof(float2) + G * sizeof(float2);
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<L, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm)));
-    const int threads = p.cols_per_cta * G / 16;
+    const int threads = p.cols_per_cta * G / 32;
     dim3 grid(p.n / p.cols_per_cta, nb);
     OVRO_PROF("k_fft_cols", st);
     k_fft_cols<L, S><<<grid, threads, sm, st>>>(w.h, w.hs, p.n, p.cols_per_cta, ch0, w.tw, w.inv_corr, w.mask,
