@@ -1040,12 +1040,23 @@ int validate(int n_chan, int n, double cell, int n_coarse, const int32_t* nfft) 
 int run_stats_block(const float* img, int nc, double* s64, float* s32, const DetectPlan& p, const DetectWs& w,
                     cudaStream_t st) {
   const size_t base = 2048 * 4 + 64 * 4 + 8 * 4 + 2048 * 8;
-  const size_t sm = base + (p.stats_in_smem ? static_cast<size_t>(p.n_valid) * 4 : 0);
-  OVRO_CUDA_TRY(cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-  OVRO_PROF("k_stats", st);
-  k_stats<<<nc, 1024, sm, st>>>(img, w.pix, p.n_valid, p.npix, p.stats_in_smem ? 1 : 0, s64, s32);
-  OVRO_LAUNCH_CHECK();
-  return OVRO_OK;
+  // staged: the channel's in-horizon pixels copied to shared memory once (one
+  // CTA per SM); unstaged: every pass re-reads them through L2, and two CTAs
+  // share an SM, one loading while the other selects
+  auto stats = [&](int staged) -> int {
+    const size_t sm = base + (staged ? static_cast<size_t>(p.n_valid) * 4 : 0);
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    OVRO_PROF("k_stats", st);
+    k_stats<<<nc, 1024, sm, st>>>(img, w.pix, p.n_valid, p.npix, staged, s64, s32);
+    OVRO_LAUNCH_CHECK();
+    return OVRO_OK;
+  };
+  if (!p.stats_in_smem) return stats(0);
+  const std::string key = tune_key("k_stats", {p.n_valid, nc});
+  int staged = tuned(key, 1);
+  if (tuning(st))
+    if (int e = tune_pick(key, {1, 0}, stats, st, &staged)) return e;
+  return stats(staged);
 }
 
 // a9 + a10 for coarse block c, whose nfft[c] images start at img_block:
