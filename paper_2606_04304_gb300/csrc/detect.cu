@@ -254,27 +254,37 @@ __global__ void k_stats32(const double* __restrict__ s64, int n_chan, float* __r
 }
 
 // ------------------------------------------------- standardise + transpose
-// z[p][k] = (x[chan0 + k][pix[p]] - med) * inv, 32 x 32 tiles.
-__global__ void k_ztrans(const float* __restrict__ img, const int* __restrict__ pix, int n_valid,
-                         long long npix, int chan0, int nc, const float* __restrict__ stats32,
-                         float* __restrict__ z) {
-  __shared__ float t[32][33];
-  const int p0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+// z[p][k] = (x[chan0 + k][pix[p]] - med) * inv, tiles of 32 pixels x kZtK
+// channels (256 threads, kZtK / 8 reads in flight per thread).
+constexpr int kZtK = 64;
+__global__ void __launch_bounds__(256)
+k_ztrans(const float* __restrict__ img, const int* __restrict__ pix, int n_valid, long long npix, int chan0,
+         int nc, const float* __restrict__ stats32, float* __restrict__ z) {
+  __shared__ float t[kZtK][33];
+  const int p0 = blockIdx.x * 32, k0 = blockIdx.y * kZtK;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8
-  for (int j = ty; j < 32; j += 8) {
-    const int k = k0 + j, p = p0 + tx;
+  const int p = p0 + tx;
+  const long long px = p < n_valid ? pix[p] : 0;
+#pragma unroll
+  for (int jj = 0; jj < kZtK / 8; ++jj) {
+    const int j = ty + 8 * jj, k = k0 + j;
     float v = 0.f;
     if (k < nc && p < n_valid) {
       const int ch = chan0 + k;
-      const float x = img[static_cast<long long>(ch) * npix + pix[p]];
-      v = (x - stats32[2 * ch]) * stats32[2 * ch + 1];
+      const float x = __ldg(img + static_cast<long long>(ch) * npix + px);
+      v = (x - __ldg(stats32 + 2 * ch)) * __ldg(stats32 + 2 * ch + 1);
     }
     t[j][tx] = v;
   }
   __syncthreads();
-  for (int j = ty; j < 32; j += 8) {
-    const int p = p0 + j, k = k0 + tx;
-    if (p < n_valid && k < nc) z[static_cast<long long>(p) * nc + k] = t[tx][j];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int pp = p0 + ty + 8 * jj;
+#pragma unroll
+    for (int u = 0; u < kZtK / 32; ++u) {
+      const int k = k0 + 32 * u + tx;
+      if (pp < n_valid && k < nc) z[static_cast<long long>(pp) * nc + k] = t[32 * u + tx][ty + 8 * jj];
+    }
   }
 }
 
@@ -500,7 +510,26 @@ k_walk(uint32_t* __restrict__ steps, int n_valid, int nc, int h) {
 __global__ void k_median_sub(float* __restrict__ zbuf, const float* __restrict__ sv,
                              const uint32_t* __restrict__ steps, int n_valid, int nc, int h) {
   const int H = (h + 3) & ~3;
-  const int S = walk_stride(nc, h);
+  const int S = walk_stride(nc, h);                      // a multiple of 4, as is H
+  if ((nc & 3) == 0) {
+    // four channels per thread: 16-byte reads of z and of the rank words
+    const int nq = nc >> 2;
+    const long long n = static_cast<long long>(n_valid) * nq;
+    for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < n;
+         v += static_cast<long long>(gridDim.x) * blockDim.x) {
+      const int p = static_cast<int>(v / nq), q = static_cast<int>(v - static_cast<long long>(p) * nq);
+      const uint4 r = __ldg(reinterpret_cast<const uint4*>(steps + static_cast<long long>(p) * S + H) + q);
+      const float* svp = sv + static_cast<long long>(p) * nc;
+      float4* zq = reinterpret_cast<float4*>(zbuf + static_cast<long long>(p) * nc) + q;
+      float4 x = *zq;
+      x.x -= 0.5f * (__ldg(svp + (r.x & 0xffffu)) + __ldg(svp + (r.x >> 16)));
+      x.y -= 0.5f * (__ldg(svp + (r.y & 0xffffu)) + __ldg(svp + (r.y >> 16)));
+      x.z -= 0.5f * (__ldg(svp + (r.z & 0xffffu)) + __ldg(svp + (r.z >> 16)));
+      x.w -= 0.5f * (__ldg(svp + (r.w & 0xffffu)) + __ldg(svp + (r.w >> 16)));
+      *zq = x;
+    }
+    return;
+  }
   const long long n = static_cast<long long>(n_valid) * nc;
   for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < n;
        v += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -1053,7 +1082,7 @@ int run_stats_block(const float* img, int nc, double* s64, float* s32, const Det
   };
   if (!p.stats_in_smem) return stats(0);
   const std::string key = tune_key("k_stats", {p.n_valid, nc});
-  int staged = tuned(key, 1);
+  int staged = tuned(key, 0);                       // L2 reads won at 256^2 x 8192 channels
   if (tuning(st))
     if (int e = tune_pick(key, {1, 0}, stats, st, &staged)) return e;
   return stats(staged);
@@ -1066,7 +1095,7 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
   const int nsm = num_sms();
   const int nc = p.nfft[c];
   {
-    dim3 g((p.n_valid + 31) / 32, (nc + 31) / 32);
+    dim3 g((p.n_valid + 31) / 32, (nc + kZtK - 1) / kZtK);
     OVRO_PROF("k_ztrans", st);
     k_ztrans<<<g, 256, 0, st>>>(img_block, w.pix, p.n_valid, p.npix, 0, nc, w.stats32 + 2LL * p.chan0[c], w.zbuf);
     OVRO_LAUNCH_CHECK();
