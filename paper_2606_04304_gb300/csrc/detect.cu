@@ -730,20 +730,30 @@ k_nms_warp(const float* __restrict__ snr, const uint8_t* __restrict__ width, con
   uint8_t* S = st[warp];
   int n = 0;
   bool over = false;
-  for (int k0 = 0; k0 < nc; k0 += 32) {
-    const int k = k0 + lane;
-    const float v = k < nc ? snr[base + k] : -INFINITY;
-    const bool hit = v >= cut;
-    const unsigned m = __ballot_sync(full, hit);
-    if (!m) continue;
-    if (n + __popc(m) > kNmsCap) { over = true; break; }
-    if (hit) {
-      const int i = n + __popc(m & lt);
-      K[i] = (static_cast<uint32_t>(k) << 8) | width[base + k];
-      V[i] = v;
-      S[i] = 0;
+  // kNmsAhead chunks of 32 channels per iteration, their reads issued together
+  constexpr int kNmsAhead = 8;
+  for (int k0 = 0; k0 < nc && !over; k0 += 32 * kNmsAhead) {
+    float v[kNmsAhead];
+#pragma unroll
+    for (int u = 0; u < kNmsAhead; ++u) {
+      const int k = k0 + 32 * u + lane;
+      v[u] = k < nc ? __ldg(snr + base + k) : -INFINITY;
     }
-    n += __popc(m);
+#pragma unroll
+    for (int u = 0; u < kNmsAhead; ++u) {
+      const int k = k0 + 32 * u + lane;
+      const bool hit = v[u] >= cut;
+      const unsigned m = __ballot_sync(full, hit);
+      if (!m) continue;
+      if (n + __popc(m) > kNmsCap) { over = true; break; }
+      if (hit) {
+        const int i = n + __popc(m & lt);
+        K[i] = (static_cast<uint32_t>(k) << 8) | width[base + k];
+        V[i] = v[u];
+        S[i] = 0;
+      }
+      n += __popc(m);
+    }
   }
   if (over) {
     if (lane == 0) ovf[atomicAdd(counters, 1)] = static_cast<int>(q);   // for k_nms_big
