@@ -129,8 +129,8 @@ def _kernel_ms(fn, names, reps=3):
 
 def next_row_measurements(volt, cfg, n_kept_vis, kern, steps, dev, vis_sub, pos, freqs):
     """Outside the timed step: the mixed-radix upchannelizer at the paper's
-    N = 2400, the drift search, the vetting stage, and the gridder against the
-    measured ceiling of its accumulation pattern."""
+    N = 2400, the X-engine at K = 299, the drift search, the vetting stage, and
+    the gridder against the measured ceiling of its accumulation pattern."""
     import torch
     from paper_2606_04304_gb300 import ovro
     hbm = _peaks()[0]
@@ -146,6 +146,23 @@ def next_row_measurements(volt, cfg, n_kept_vis, kern, steps, dev, vis_sub, pos,
     out["upchan_2400"] = {"workload": "352 antennas, 1 coarse channel, N = 2400, 10 s (K = 100)", "ms": ms,
                           "samples_per_s": samples / (ms * 1e-3), "achieved_GBs": gbs, "frac_hbm": gbs / hbm,
                           "bytes_per_sample": 3}
+    # the X-engine where it can be tensor-bound: K = 299 spectra per
+    # integration (the paper's), 352 antennas, 512 channels of random int8
+    n_chan_x, k_x = 512, 299
+    gq = torch.Generator(device=dev).manual_seed(7)
+    q = torch.randint(-127, 128, (n_chan_x * k_x * cfg.n_input * 2,), generator=gq, device=dev,
+                      dtype=torch.int16).to(torch.int8)
+    vis_x = torch.empty((n_chan_x, ovro.n_baselines(cfg.n_ant), 4, 2), dtype=torch.int32, device=dev)
+    ms = _kernel_ms(lambda: ovro.correlate(q, cfg.n_ant, n_chan_x, k_x, ovro.XENG_TC, out=vis_x), ["k_xeng_tc"])
+    pairs = cfg.n_input * (cfg.n_input + 1) // 2
+    tops = n_chan_x * pairs * 8 * k_x / (ms * 1e-3) / 1e12
+    gbs = (vis_x.numel() * 4 + q.numel()) / (ms * 1e-3) / 1e9
+    out["xengine_k299"] = {"workload": "352 antennas, 512 channels, K = 299, random int8",
+                           "ms": ms, "achieved_TOPS": tops, "peak_TFLOPS": _peaks()[1], "frac_tensor": tops / _peaks()[1],
+                           "achieved_GBs": gbs, "frac_hbm": gbs / hbm,
+                           "ops": "8 per input pair (i <= j of 704 inputs) per spectrum",
+                           "note": "int8 values carried exactly in FP16 tcgen05 MMAs (FP16 and BF16 dense rates are equal)"}
+    del q, vis_x
     # drift search: T = 8 sub-integration cubes of 1024 channels, 256^2
     T, nc, N = 8, 1024, cfg.image_size
     g = torch.Generator(device=dev).manual_seed(5)

@@ -207,28 +207,37 @@ k_xeng_tc(const int8_t* __restrict__ q, int n_ant, int n_spec, int n_tiles, int 
     const int J = I + p;
     const int8_t* qc = q + static_cast<long long>(ch) * n_spec * n_input * 2;
 
-    for (int s0 = 0; s0 < n_spec; s0 += kTcSpecPerChunk) {
-      // ---- operands: A row t = X_{I*128+t}; B rows 2t, 2t+1 = X_j, Z_j, j = J*128+t
-      const int ia = I * kTcM + tid;
-      const int ib = J * kTcInputsN + tid;
-#pragma unroll 4
+    // ---- operands: A row t = X_{I*128+t}; B rows 2t, 2t+1 = X_j, Z_j, j = J*128+t.
+    // A chunk's 2 x 32 int8 pairs per thread are read with one round trip, and
+    // the next chunk's reads are issued while this chunk's MMAs run.
+    const int ia = I * kTcM + tid;
+    const int ib = J * kTcInputsN + tid;
+    uint32_t va[kTcSpecPerChunk], vb[kTcSpecPerChunk];   // (re, im) int8 pairs, 16 bits used
+    auto read_chunk = [&](int s0) {
+#pragma unroll
       for (int ss = 0; ss < kTcSpecPerChunk; ++ss) {
         const int s = s0 + ss;
-        char2 xa = make_char2(0, 0), xb = make_char2(0, 0);
-        if (s < n_spec) {
-          const char2* row = reinterpret_cast<const char2*>(qc + static_cast<long long>(s) * n_input * 2);
-          if (ia < n_input) xa = row[ia];
-          if (ib < n_input) xb = row[ib];
-        }
-        const __half2 ha = __halves2half2(__short2half_rn(xa.x), __short2half_rn(xa.y));
-        const __half2 hx = __halves2half2(__short2half_rn(xb.x), __short2half_rn(xb.y));
-        const __half2 hz = __halves2half2(__short2half_rn(static_cast<short>(-xb.y)), __short2half_rn(xb.x));
+        const uint16_t* row = reinterpret_cast<const uint16_t*>(qc + static_cast<long long>(s) * n_input * 2);
+        va[ss] = (s < n_spec && ia < n_input) ? __ldg(row + ia) : 0u;
+        vb[ss] = (s < n_spec && ib < n_input) ? __ldg(row + ib) : 0u;
+      }
+    };
+    read_chunk(0);
+    for (int s0 = 0; s0 < n_spec; s0 += kTcSpecPerChunk) {
+#pragma unroll
+      for (int ss = 0; ss < kTcSpecPerChunk; ++ss) {
+        const short ar = static_cast<signed char>(va[ss] & 0xffu), ai = static_cast<signed char>(va[ss] >> 8);
+        const short br = static_cast<signed char>(vb[ss] & 0xffu), bi = static_cast<signed char>(vb[ss] >> 8);
+        const __half2 ha = __halves2half2(__short2half_rn(ar), __short2half_rn(ai));
+        const __half2 hx = __halves2half2(__short2half_rn(br), __short2half_rn(bi));
+        const __half2 hz = __halves2half2(__short2half_rn(static_cast<short>(-bi)), __short2half_rn(br));
         *reinterpret_cast<__half2*>(sA + op_offset(tid, 2 * ss)) = ha;
         *reinterpret_cast<__half2*>(sB + op_offset(2 * tid, 2 * ss)) = hx;
         *reinterpret_cast<__half2*>(sB + op_offset(2 * tid + 1, 2 * ss)) = hz;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
+      if (s0 + kTcSpecPerChunk < n_spec) read_chunk(s0 + kTcSpecPerChunk);
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);

@@ -7,6 +7,7 @@ few GB on the device:
     python -m paper_2606_04304_gb300.profile_cases imaging     # 256 channels, 256^2 images
     python -m paper_2606_04304_gb300.profile_cases detection   # 128^2 x 8192-channel cube
     python -m paper_2606_04304_gb300.profile_cases xengine     # 512 channels, K = 29
+    python -m paper_2606_04304_gb300.profile_cases xengine299  # 128 channels, K = 299
     python -m paper_2606_04304_gb300.profile_cases upchan2400  # N = 2400, 704 inputs, 2 s
     python -m paper_2606_04304_gb300.profile_cases drift       # T = 8 x 512 channels x 128^2
 
@@ -51,6 +52,15 @@ def xengine(repeats: int = 3) -> None:
         ovro.correlate(q, n_ant, n_chan, k, ovro.XENG_TC)
 
 
+def xengine299(repeats: int = 3) -> None:
+    n_ant, n_chan, k = 352, 128, 299
+    g = torch.Generator(device="cuda").manual_seed(0)
+    q = torch.randint(-127, 128, (n_chan * k * 2 * n_ant * 2,), generator=g, device="cuda",
+                      dtype=torch.int16).to(torch.int8)
+    for _ in range(repeats):
+        ovro.correlate(q, n_ant, n_chan, k, ovro.XENG_TC)
+
+
 def upchan2400(repeats: int = 3) -> None:
     g = torch.Generator(device="cuda").manual_seed(0)
     volt = torch.randint(0, 256, (1, 48_000, 704), generator=g, device="cuda", dtype=torch.int32).to(torch.uint8)
@@ -66,7 +76,8 @@ def drift(repeats: int = 2) -> None:
         ovro.drift_search(zsub, 2.0 / 128, [512], freqs, 12.0)
 
 
-CASES = {"imaging": imaging, "detection": detection, "xengine": xengine, "upchan2400": upchan2400, "drift": drift}
+CASES = {"imaging": imaging, "detection": detection, "xengine": xengine, "xengine299": xengine299, "upchan2400": upchan2400,
+         "drift": drift}
 
 
 def main(argv) -> int:

@@ -19,7 +19,7 @@ def _oracle(q, n_ant, chans):
 
 
 @pytest.mark.parametrize("n_ant,k", [(1, 1), (2, 5), (3, 29), (16, 64), (17, 29), (64, 32), (65, 33),
-                                     (130, 7), (200, 29), (384, 29), (383, 17)])
+                                     (130, 7), (200, 29), (384, 29), (383, 17), (352, 299)])
 def test_random_exact(lib, n_ant, k):
     g = np.random.default_rng(n_ant * 1000 + k)
     n_chan = 5
