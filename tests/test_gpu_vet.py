@@ -1,7 +1,6 @@
 """GPU parity: Stage I re-evaluation and Stage II vetting (ovro_vet) against
 the oracle on synthetic cubes with compact, extended and weak lines, noisy
 images and candidates at the edges; and end to end on the tiny workload."""
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,7 @@ import pytest
 import torch
 
 import synth
-from oracle import upchan as OU, xengine as OX
+from oracle import xengine as OX
 
 pytestmark = pytest.mark.gpu
 

@@ -1,7 +1,6 @@
 """Pins for the X-engine oracle (Section 2.1): brute force, Hermitian symmetry,
 autocorrelation = summed power, unit-modulus phase-only visibilities."""
 import numpy as np
-import pytest
 
 from oracle import xengine as X
 
