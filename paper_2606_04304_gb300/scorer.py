@@ -7,7 +7,7 @@ passed in.
 
 The scorer proposes which Stage I triggers to keep; the plain threshold
 detector remains the fallback and the reference its recall and false-alarm
-rate are judged against.
+rate are measured against.
 """
 from __future__ import annotations
 
