@@ -155,7 +155,8 @@ int ovro_upchan_ex(const uint8_t* d_volt, int n_input, int n_coarse, int64_t n_t
  * 704 inputs x 64 coarse channels); larger calls return OVRO_ERR_CAPACITY and
  * launch nothing.  Allocates nothing (no cudaMalloc/cudaFree).  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every
+ * that device current; make that first call before any stream capture.  A
+ * failed lookup is not kept: the next call on that device tries again.  Every
  * call reuses the same array (what must start at zero is cleared by each
  * call), so calls that overlap on the GPU -- different streams, or different
  * host threads, on one device -- race and must be serialised by the caller. */
@@ -179,7 +180,8 @@ int ovro_upchan_noalloc(const uint8_t* d_volt, int n_input, int n_coarse, int64_
  *           every partial sum stays below 2^24);
  *           OVRO_XENG_FP32: plain FP32 SIMT accumulation (same exactness
  *           bound).  Both are bit-exact integer results.
- * Errors:   OVRO_ERR_OVERFLOW if 2 * 127^2 * n_spec >= 2^24 (n_spec > 520),
+ * Errors:   OVRO_ERR_OVERFLOW if 2 * 128^2 * n_spec >= 2^24 (n_spec > 511):
+ *           the bound holds for any int8 input, -128 included,
  *           OVRO_ERR_UNSUPPORTED if n_ant > 4096.
  * ------------------------------------------------------------------------- */
 enum { OVRO_XENG_TC = 0, OVRO_XENG_FP32 = 1 };

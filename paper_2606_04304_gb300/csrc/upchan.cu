@@ -637,22 +637,26 @@ constexpr size_t kNoAllocScratchBytes = 1u << 20;   // 1 MiB
 static __device__ __align__(256) unsigned char g_upchan_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices];
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices];
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices];     // device address per device, once found
 
-// Device address of the scratch array for the current device, looked up once
-// per device (host code must not use the symbol itself as a device address).
+// Device address of the scratch array for the current device (host code must
+// not use the symbol itself as a device address).  Only a successful lookup
+// is kept: after a failure (say, a first call made during a stream capture)
+// the next call looks again.
 int noalloc_scratch(void** out) {
   int dev = 0;
   OVRO_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return OVRO_ERR_UNSUPPORTED;
-  std::call_once(g_scratch_once[dev], [dev] {
-    g_scratch_err[dev] = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_upchan_scratch);
-  });
-  if (g_scratch_err[dev] != cudaSuccess) {
-    set_last_error("cudaGetSymbolAddress(g_upchan_scratch)", g_scratch_err[dev]);
-    return OVRO_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_upchan_scratch);
+    if (e != cudaSuccess) {
+      set_last_error("cudaGetSymbolAddress(g_upchan_scratch)", e);
+      return OVRO_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = p;
   }
   *out = g_scratch_ptr[dev];
   return OVRO_OK;

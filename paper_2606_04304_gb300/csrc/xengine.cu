@@ -10,8 +10,9 @@
 //  * k_xeng_tc: 5th-generation tensor cores.  sm_103a has no integer MMA
 //    (tcgen05 .kind::i8 is rejected by ptxas for this target), so the int8
 //    values are carried exactly in FP16 operands and accumulated in FP32 in
-//    tensor memory; with |q| <= 127 every partial sum stays an integer below
-//    2^24 for K <= 520, so the result is exact.  The Hermitian product becomes
+//    tensor memory; every int8 value has |q| <= 128, so each spectrum adds at
+//    most 2 * 128^2 = 2^15 to a sum and every partial sum stays an integer
+//    below 2^24 for K <= 511: the result is exact.  The Hermitian product becomes
 //    one real GEMM: A row i = X_i = (re_i(s), im_i(s))_s, B rows 2j, 2j+1 =
 //    X_j and Z_j = (-im_j(s), re_j(s))_s, so D[i][2j] = Re V_ij and
 //    D[i][2j+1] = Im V_ij land as adjacent TMEM columns.  One CTA per SM pair
@@ -529,7 +530,8 @@ int correlate_enqueue(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec,
   if (!d_fine_q || !d_vis || n_ant <= 0 || n_chan <= 0 || n_spec <= 0) return OVRO_ERR_INVALID_ARG;
   if (mode != OVRO_XENG_TC && mode != OVRO_XENG_FP32) return OVRO_ERR_INVALID_ARG;
   if (n_ant > 4096) return OVRO_ERR_UNSUPPORTED;
-  if (2LL * 127 * 127 * n_spec >= (1LL << 24)) return OVRO_ERR_OVERFLOW;
+  // any int8 input (-128 included): partial sums below 2 * 128^2 * K < 2^24
+  if (2LL * 128 * 128 * n_spec >= (1LL << 24)) return OVRO_ERR_OVERFLOW;
   if (reinterpret_cast<uintptr_t>(d_vis) % 16 != 0 || reinterpret_cast<uintptr_t>(d_fine_q) % 2 != 0)
     return OVRO_ERR_INVALID_ARG;
   const int n_input = 2 * n_ant;

@@ -17,6 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libovro.so")
 
 OVRO_OK = 0
+(ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_OVERFLOW,
+ ERR_CAPACITY) = -1, -2, -3, -4, -5, -6, -7
 XENG_TC, XENG_FP32 = 0, 1
 STORE_FP32, STORE_BF16, STORE_FP16 = 0, 1, 2
 DETECT_BH, DETECT_FIXED = 0, 1

@@ -33,19 +33,31 @@ def test_random_exact(lib, n_ant, k):
     assert np.array_equal(fp, ref)
 
 
-@pytest.mark.parametrize("k", [29, 260, 520])
+@pytest.mark.parametrize("k", [29, 260, 511])
 def test_worst_case_magnitudes(lib, k):
-    # +-127 everywhere: partial sums reach 2 * 127^2 * K (< 2^24 up to K = 520)
+    # -128 and 127 everywhere, input 0 all -128: partial sums reach 2 * 128^2 * K,
+    # below 2^24 up to K = 511, the largest K the call accepts
     n_ant, n_chan = 24, 2
     g = np.random.default_rng(k)
-    q = (g.integers(0, 2, (n_chan, k, 2 * n_ant, 2)) * 254 - 127).astype(np.int8)
-    q[0] = -127
+    q = (g.integers(0, 2, (n_chan, k, 2 * n_ant, 2)) * 255 - 128).astype(np.int8)
+    q[:, :, 0, :] = -128
     d = torch.from_numpy(q).cuda()
     tc = lib.correlate(d, n_ant, n_chan, k, lib.XENG_TC).cpu().numpy()
     fp = lib.correlate(d, n_ant, n_chan, k, lib.XENG_FP32).cpu().numpy()
     ref = _oracle(q, n_ant, range(n_chan))
     assert np.array_equal(tc, ref) and np.array_equal(fp, ref)
-    assert np.abs(ref).max() == 2 * 127 * 127 * k
+    assert np.abs(ref).max() == 2 * 128 * 128 * k
+
+
+@pytest.mark.parametrize("mode", ["tc", "fp32"])
+def test_accumulation_bound_rejected(lib, mode):
+    # K = 512 could reach 2^24 with -128 inputs: refused before any launch
+    n_ant, n_chan, k = 4, 1, 512
+    d = torch.zeros((n_chan, k, 2 * n_ant, 2), dtype=torch.int8, device="cuda")
+    md = lib.XENG_TC if mode == "tc" else lib.XENG_FP32
+    with pytest.raises(lib.OvroError) as e:
+        lib.correlate(d, n_ant, n_chan, k, md)
+    assert e.value.status == lib.ERR_OVERFLOW
 
 
 def test_full_array_sampled_channels(lib):

@@ -72,9 +72,8 @@ def test_unit_modulus_point_source():
 
 
 def test_worst_case_fits_int32():
-    # +-127 everywhere: |V| <= 2 * 127^2 * K, below 2^31 up to K ~ 66,000; below 2^24 up to K = 520
-    k = 520
-    q = np.full((2, k, 2), -127, np.int8)
-    q[1, :, 1] = 127
+    # -128 everywhere: |V| <= 2 * 128^2 * K, below 2^31 up to K ~ 65,000; below 2^24 up to K = 511
+    k = 511
+    q = np.full((2, k, 2), -128, np.int8)
     vre, vim = X.full_matrix(q)
-    assert np.abs(vre).max() == 2 * 127 * 127 * k < 2 ** 24
+    assert np.abs(vre).max() == 2 * 128 * 128 * k < 2 ** 24

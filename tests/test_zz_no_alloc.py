@@ -52,7 +52,9 @@ def test_noalloc_matches_workspace_entry_point(lib):
 def test_noalloc_rejects_oversized_call(lib):
     fn = _fn(lib)
     nf = (ctypes.c_int32 * 1)(1024)
-    # 46,000 inputs x 1 coarse channel needs more than the fixed 1 MiB of scratch
-    st = fn(ctypes.c_void_p(256), 46000, 1, 4096, nf, None, ctypes.c_void_p(256), None, None)
+    # 46,000 inputs x 1 coarse channel needs more than the fixed 1 MiB of scratch;
+    # no device buffers are passed: the size check comes first, and were it ever
+    # skipped the upchannelizer would refuse the null pointers without launching
+    st = fn(None, 46000, 1, 4096, nf, None, None, None, None)
     assert st == -7
     assert b"scratch" in lib.lib().ovro_last_error()
