@@ -57,18 +57,13 @@ int ovro_version(void);
 unsigned long long ovro_launch_count(void);
 /* Kernel tracing.  ovro_profile(1) clears the trace and starts recording a
  * CUDA event pair on the launch stream around every launch of the main
- * kernels (k_upchan, k_upchan_mr, k_xeng_tc, k_xeng_simt, k_grid_rows, k_fft_cols,
- * k_stats, k_ztrans, k_rank, k_walk, k_median_sub, k_mf, k_nms_warp, k_vet_line,
+ * kernels (k_upchan, k_upchan_mr, k_xeng_tc, k_xeng_simt, k_grid_prep, k_grid_tiles, k_fft_rows,
+ * k_fft_cols, k_stats, k_ztrans, k_rank, k_walk, k_median_sub, k_mf, k_nms_warp, k_vet_line,
  * k_vet_fit, k_drift, k_scorer_fwd); ovro_profile(0) stops recording.
  * ovro_profile_query waits for the recorded launches of one kernel and
  * returns their summed device time and count. */
 int ovro_profile(int enable);
 int ovro_profile_query(const char* kernel, double* total_ms, int* launches);
-/* Measured ceiling of the gridder's accumulation on this GPU (a measurement
- * aid): the taps per second of k_grid_rows's shared-memory atomic pattern
- * (one 7x7 record per warp into a 32-row FP32 band) with no other work.
- * Allocates 4 bytes, synchronises stream. */
-int ovro_probe_accumulate(double* h_gtaps_per_s, void* stream);
 
 /* -------------------------------------------------------------------------
  * a1-a3  Unpack + FFT upchannelizer + 8-bit requantisation
@@ -299,7 +294,7 @@ typedef struct {
   int32_t row, col;       /* pixel */
   int32_t width;          /* matched-filter width, channels */
   float snr;              /* matched-filter SNR */
-  float pad_;
+  float score;            /* keep probability from the learned scorer (0 without one) */
   double freq_hz;         /* sky frequency of the channel */
   double log10_p;         /* log10 of the one-sided Gaussian p-value */
 } ovro_candidate;
@@ -310,16 +305,40 @@ int ovro_default_widths(int32_t* h_out_or_null);
 
 size_t ovro_detect_workspace_size(int n_chan, int image_size, int n_coarse,
                                   const int32_t* h_nfft);
+/* The learned candidate scorer as a stage of the search (a13; no
+ * counterpart in the paper, which keeps or drops Stage I triggers by
+ * threshold alone).  With a scorer, ovro_detect takes its triggers from the
+ * fixed threshold trigger_nsigma (the relaxed Stage I cut; NMS included),
+ * scores each trigger's cutout of the high-passed cube with the network of
+ * ovro_scorer_forward, and returns the triggers whose keep probability
+ * sigmoid(logit) is at least keep_prob, that probability in each record's
+ * score.  d_ws (ws_bytes >= ovro_scorer_detect_workspace_size(...)) holds the
+ * high-passed cube, the triggers and the cutouts: caller-owned scratch, bound
+ * for the call only.  OVRO_ERR_CAPACITY when more than max_triggers triggers
+ * pass the relaxed cut. */
+typedef struct {
+  const void* d_w_bf16;   /* ovro_scorer_n_params() BF16 weights (device) */
+  double trigger_nsigma;  /* relaxed fixed threshold proposing triggers (e.g. 5) */
+  float keep_prob;        /* keep a trigger when its probability >= keep_prob */
+  int max_triggers;       /* capacity of the scratch */
+  void* d_ws;
+  size_t ws_bytes;
+} ovro_scorer;
+size_t ovro_scorer_detect_workspace_size(int n_chan, int image_size, int n_coarse, int max_triggers);
+
 /* d_img     float [n_chan][N][N] images (ovro_grid_image output layout).
  * h_nfft    [n_coarse] channels per coarse channel (sum = n_chan).
  * h_chan_freq_hz [n_chan] sky frequencies (for the candidate records).
+ * scorer_or_null  NULL: the plain threshold detector (params' mode); else
+ *           the scorer stage above replaces the threshold.
  * h_out     host array of max_out candidates, ordered by (row, col, chan);
  *           *n_out = number found.  OVRO_ERR_CAPACITY if more than max_out
  *           (the first max_out are written, *n_out holds the true count). */
 int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dircos,
                 int n_coarse, const int32_t* h_nfft, const double* h_chan_freq_hz,
-                const ovro_detect_params* params, ovro_candidate* h_out, int max_out,
-                int* n_out, void* d_ws, size_t ws_bytes, void* stream);
+                const ovro_detect_params* params, const ovro_scorer* scorer_or_null,
+                ovro_candidate* h_out, int max_out, int* n_out, void* d_ws, size_t ws_bytes,
+                void* stream);
 
 /* Stage-isolated pieces of ovro_detect (same workspace), for inspection and
  * testing.  Layouts are the caller's:
@@ -587,6 +606,18 @@ int ovro_pipeline_bind(ovro_pipeline* pl, void* d_ws, size_t ws_bytes, void* str
  * disabled. */
 int ovro_pipeline_run(ovro_pipeline* pl, const uint8_t* d_volt, ovro_candidate* h_out, int max_out,
                       int* n_out, void* stream);
+/* The device part of one integration only (everything before the
+ * threshold; graph replay as ovro_pipeline_run; synchronises stream).  The
+ * integration's SNR histogram, bin values and NMS at a cut are then read
+ * through the search view below -- for a threshold decided across several
+ * pipelines, one per GPU (Section 2.4's single Benjamini-Hochberg family over
+ * every shard's tests). */
+int ovro_pipeline_run_device(ovro_pipeline* pl, const uint8_t* d_volt, void* stream);
+/* A search handle over the pipeline's whole-integration search (layout,
+ * histogram, bin values, candidates as the ovro_search_* calls).  It borrows
+ * the pipeline's workspace: valid while the pipeline stays bound; release it
+ * with ovro_search_destroy, which leaves the pipeline untouched. */
+int ovro_pipeline_search(ovro_pipeline* pl, ovro_search** out);
 /* Fine channels in the integration and their sky frequencies (host array of
  * that length, or NULL to query the count). */
 int ovro_pipeline_channels(const ovro_pipeline* pl, double* h_freq_or_null);

@@ -1518,6 +1518,17 @@ int detect_ctx_coarse(DetectCtx* d, int c, const float* d_img_block, cudaStream_
   return run_filter_coarse(c, d_img_block, p, d->w, d->key0, d->nb, nullptr, st);
 }
 
+// a8-a10 for coarse channel c, also scattering z' into d_zp [n_chan][N][N].
+int detect_ctx_coarse_zp(DetectCtx* d, int c, const float* d_img_block, float* d_zp, cudaStream_t st) {
+  if (!d || !d_img_block || c < 0 || c >= d->p.n_coarse) return OVRO_ERR_INVALID_ARG;
+  const DetectPlan& p = d->p;
+  if (p.n_valid == 0) return OVRO_OK;
+  const long long off = 2LL * p.chan0[c];
+  if (int e = run_stats_block(d_img_block, p.nfft[c], d->w.stats64 + off, d->w.stats32 + off, p, d->w, st))
+    return e;
+  return run_filter_coarse(c, d_img_block, p, d->w, d->key0, d->nb, d_zp, st);
+}
+
 // The search's SNR histogram (synchronises; checks the device status word).
 int detect_ctx_histogram(DetectCtx* d, std::vector<unsigned long long>& hist, cudaStream_t st) {
   hist.assign(d->nb, 0ull);
@@ -1617,7 +1628,7 @@ int detect_ctx_candidates(DetectCtx* d, float cut, const double* h_chan_freq_hz,
       o.col = pixel % image_size;
       o.width = r.width;
       o.snr = r.snr;
-      o.pad_ = 0.f;
+      o.score = 0.f;
       o.freq_hz = h_chan_freq_hz[o.chan];
       o.log10_p = r.log10_p;
     }
@@ -1643,16 +1654,118 @@ void detect_ctx_free(DetectCtx* d) { delete d; }
 
 }  // namespace ovro
 
+namespace ovro {
+
+// Scratch of the scored search (the caller's scorer workspace).
+struct ScoredWs {
+  float* zp;          // [n_chan][N][N] high-passed standardised cube
+  int32_t* trig;      // [max_triggers][3] (channel, row, col)
+  float* x;           // [kScoreBatch][1600] cutouts
+  float* logit;       // [max_triggers]
+  void* sws;          // scorer kernels' own workspace (batch kScoreBatch)
+  size_t sws_bytes;
+};
+constexpr int kScoreBatch = 1024;
+constexpr int kCutout = 64 * 25;
+
+ScoredWs carve_scored(void* ws, int n_chan, int npix, int n_coarse, int max_triggers, size_t* need) {
+  Carver c(ws, ~static_cast<size_t>(0));
+  ScoredWs w;
+  w.zp = c.take<float>(static_cast<size_t>(n_chan) * npix);
+  w.trig = c.take<int32_t>(static_cast<size_t>(std::max(1, max_triggers)) * 3);
+  w.x = c.take<float>(static_cast<size_t>(kScoreBatch) * kCutout);
+  w.logit = c.take<float>(std::max(1, max_triggers));
+  w.sws_bytes = ovro_scorer_workspace_size(kScoreBatch, n_coarse);
+  w.sws = c.take<unsigned char>(w.sws_bytes);
+  *need = c.used;
+  return w;
+}
+
+// a8-a12 with the learned scorer (spec addition): the fixed threshold
+// trigger_nsigma proposes triggers (NMS included), each trigger's cutout of
+// the high-passed cube is scored, and those whose keep probability is at least
+// keep_prob are returned with it.
+int detect_scored(const float* d_img, int n_chan, int image_size, double cell, int n_coarse, const int32_t* h_nfft,
+                  const double* h_freq, const ovro_detect_params& params, const ovro_scorer& sc,
+                  ovro_candidate* h_out, int max_out, int* n_out, void* d_ws, size_t ws_bytes, cudaStream_t st) {
+  if (!sc.d_w_bf16 || !(sc.trigger_nsigma > 0.0) || sc.max_triggers <= 0 || !sc.d_ws) return OVRO_ERR_INVALID_ARG;
+  if (!(sc.keep_prob >= 0.0f && sc.keep_prob <= 1.0f)) return OVRO_ERR_INVALID_ARG;
+  ovro_detect_params trig_prm = params;
+  trig_prm.mode = OVRO_DETECT_FIXED;
+  trig_prm.nsigma = sc.trigger_nsigma;
+  DetectCtx* d = nullptr;
+  if (int e = detect_ctx_init(&d, n_chan, image_size, cell, n_coarse, h_nfft, &trig_prm, d_ws, ws_bytes)) return e;
+  size_t need = 0;
+  ScoredWs w = carve_scored(sc.d_ws, n_chan, d->p.npix, n_coarse, sc.max_triggers, &need);
+  if (int e = check_workspace(sc.d_ws, sc.ws_bytes, need)) {
+    detect_ctx_free(d);
+    return e;
+  }
+  std::vector<ovro_candidate> trig(static_cast<size_t>(sc.max_triggers));
+  int n_trig = 0;
+  int e = detect_ctx_upload(d, st);
+  if (!e) e = detect_ctx_begin(d, st);
+  if (!e) {
+    const cudaError_t ce = cudaMemsetAsync(w.zp, 0, sizeof(float) * static_cast<size_t>(n_chan) * d->p.npix, st);
+    if (ce != cudaSuccess) {
+      set_last_error("cudaMemsetAsync", ce);
+      e = OVRO_ERR_CUDA;
+    }
+  }
+  for (int c = 0; c < n_coarse && !e; ++c) {
+    const float* blk = d_img + static_cast<long long>(d->p.chan0[c]) * d->p.npix;
+    e = detect_ctx_coarse_zp(d, c, blk, w.zp, st);
+  }
+  if (!e) e = detect_ctx_finish(d, h_freq, trig.data(), sc.max_triggers, &n_trig, st);
+  detect_ctx_free(d);
+  if (e) return e;
+  if (n_trig == 0) return OVRO_OK;
+  std::vector<int32_t> t3(static_cast<size_t>(n_trig) * 3);
+  for (int i = 0; i < n_trig; ++i) {
+    t3[3 * i] = trig[i].chan;
+    t3[3 * i + 1] = trig[i].row;
+    t3[3 * i + 2] = trig[i].col;
+  }
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.trig, t3.data(), t3.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  for (int b0 = 0; b0 < n_trig; b0 += kScoreBatch) {
+    const int nb = std::min(kScoreBatch, n_trig - b0);
+    if (int e2 = ovro_scorer_cutouts(w.zp, n_chan, image_size, n_coarse, h_nfft, w.trig + 3 * b0, nb, w.x, w.sws,
+                                     w.sws_bytes, st))
+      return e2;
+    if (int e2 = ovro_scorer_forward(sc.d_w_bf16, w.x, nb, w.logit + b0, w.sws, w.sws_bytes, st)) return e2;
+  }
+  std::vector<float> logit(n_trig);
+  OVRO_CUDA_TRY(cudaMemcpyAsync(logit.data(), w.logit, n_trig * sizeof(float), cudaMemcpyDeviceToHost, st));
+  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+  int n = 0;
+  for (int i = 0; i < n_trig; ++i) {
+    const double pk = 1.0 / (1.0 + std::exp(-static_cast<double>(logit[i])));
+    if (pk < sc.keep_prob) continue;
+    if (n < max_out) {
+      h_out[n] = trig[i];
+      h_out[n].score = static_cast<float>(pk);
+    }
+    ++n;
+  }
+  *n_out = n;
+  return n > max_out ? OVRO_ERR_CAPACITY : OVRO_OK;
+}
+
+}  // namespace ovro
+
 extern "C" {
 
 int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dircos, int n_coarse,
                 const int32_t* h_nfft, const double* h_chan_freq_hz, const ovro_detect_params* params,
-                ovro_candidate* h_out, int max_out, int* n_out, void* d_ws, size_t ws_bytes,
-                void* stream) {
+                const ovro_scorer* scorer_or_null, ovro_candidate* h_out, int max_out, int* n_out, void* d_ws,
+                size_t ws_bytes, void* stream) {
   using namespace ovro;
   if (!d_img || !params || !n_out || (max_out > 0 && !h_out) || max_out < 0 || !h_chan_freq_hz)
     return OVRO_ERR_INVALID_ARG;
   *n_out = 0;
+  if (scorer_or_null)
+    return detect_scored(d_img, n_chan, image_size, cell_dircos, n_coarse, h_nfft, h_chan_freq_hz, *params,
+                         *scorer_or_null, h_out, max_out, n_out, d_ws, ws_bytes, as_stream(stream));
   DetectCtx* d = nullptr;
   if (int e = detect_ctx_init(&d, n_chan, image_size, cell_dircos, n_coarse, h_nfft, params, d_ws, ws_bytes))
     return e;
@@ -1666,10 +1779,19 @@ int ovro_detect(const float* d_img, int n_chan, int image_size, double cell_dirc
   return e;
 }
 
+size_t ovro_scorer_detect_workspace_size(int n_chan, int image_size, int n_coarse, int max_triggers) {
+  if (n_chan <= 0 || image_size <= 0 || n_coarse <= 0 || max_triggers <= 0) return 0;
+  size_t need = 0;
+  ovro::carve_scored(nullptr, n_chan, image_size * image_size, n_coarse, max_triggers, &need);
+  return need;
+}
+
 // ---- sharded search (Section 2.4 threshold over several shards)
 struct ovro_search {
   ovro::DetectCtx* d = nullptr;
+  bool owned = true;             // false: a view of a pipeline's search
 };
+
 
 int ovro_search_create(int n_chan, int image_size, double cell_dircos, int n_coarse, const int32_t* h_nfft,
                        const ovro_detect_params* params, void* d_ws, size_t ws_bytes, void* stream,
@@ -1687,7 +1809,7 @@ int ovro_search_create(int n_chan, int image_size, double cell_dircos, int n_coa
     detect_ctx_free(d);
     return e;
   }
-  *out = new ovro_search{d};
+  *out = new ovro_search{d, true};
   return OVRO_OK;
 }
 
@@ -1744,7 +1866,7 @@ int ovro_search_candidates(ovro_search* s, float cut, const double* h_chan_freq_
 
 void ovro_search_destroy(ovro_search* s) {
   if (!s) return;
-  ovro::detect_ctx_free(s->d);
+  if (s->owned) ovro::detect_ctx_free(s->d);
   delete s;
 }
 
@@ -1764,3 +1886,5 @@ int ovro_bh_resolve(const float* h_vals_desc, long long n, unsigned long long ab
 uint32_t ovro_snr_bin_key(float snr) { return ovro::host_f2key(snr) >> ovro::kHistShift; }
 
 }  // extern "C"
+
+ovro_search* ovro::search_view(ovro::DetectCtx* d) { return new ovro_search{d, false}; }

@@ -458,7 +458,7 @@ int ovro_drift_search(const float* d_zp, int n_sub, int n_chan, int image_size, 
     o.col = pix[d.p] % n;
     o.width = std::abs(d.drift) + 1;
     o.snr = d.snr;
-    o.pad_ = 0.0f;
+    o.score = 0.0f;
     o.freq_hz = h_chan_freq_hz[d.chan];
     o.log10_p = log10_q(static_cast<double>(d.snr));
     h_drift_out[i] = d.drift;

@@ -15,14 +15,19 @@
 //      reflection), with a separable 7 x 7 prolate-spheroidal kernel.  The uv
 //      position of a baseline moves by a fraction of a cell across a call's
 //      channels, so the host lists, once per call, the baselines that can
-//      touch each band of grid rows; k_grid_rows then works on one
-//      (channel, band): exact uv, keep test, shared-memory atomics into the
-//      band, and the band's row FFTs in place.
+//      touch each 4 x 8-cell tile of the grid; k_grid_tiles gives every tile
+//      to one warp whose 32 lanes are 32 adjacent channels: each lane takes
+//      the tile's records for its own channel (exact uv, keep test, weights)
+//      and accumulates the tile in registers, so no cell is written by two
+//      threads and there are no atomics.  k_fft_rows transforms the rows.
 //  a7  The uv grid is padded by 2 (G = 2N cells a side, du = 1 / (G cell)) and
 //      the image is the central N x N of its transform, as padded imagers do:
 //      the horizon then sits where the kernel's transform is still > 0.25, so
-//      the grid correction does not amplify FP32 round-off.  k_grid_rows keeps
-//      only the N central columns of its row transforms; k_fft_cols
+//      the grid correction does not amplify FP32 round-off.  The image is
+//      the real part of the transform, i.e. the transform of the grid's
+//      Hermitian part, whose row transforms come in conjugate pairs: k_fft_rows
+//      forms that part, transforms rows 0 .. G/2 only and keeps the N central
+//      columns; k_fft_cols
 //      transforms those columns, keeps the N central rows, and applies the
 //      (-1)^(r+c) centring sign, normalisation, grid correction and horizon
 //      mask while writing the image.  The (-1)^(ku+kv) centring sign is
@@ -180,222 +185,271 @@ struct GridOpts {
 
 // Row pitch of a shared-memory grid band: G + G/16 pad slots, rounded so the
 // pitch is 7 (mod 16) float2 -- consecutive rows then start 14 banks apart and
-// the 7 rows of one kernel footprint, or 16 consecutive transposed columns, hit
-// distinct banks.
+// 16 consecutive transposed columns hit distinct banks.
 __host__ __device__ constexpr int band_pitch(int g) { return (g + g / 16) + ((7 - (g + g / 16) % 16) + 16) % 16; }
 
-// Gridding records per chunk (one per prepared visibility).
-constexpr int kRecMax = 512;
-constexpr int kWuStride = 5;       // float2 per record: (w_t, w_{t+4}), t < 4; odd word stride
-constexpr int kWvStride = 9;       // floats per record: w_t, t < 8 (w_7 = 0)
+// Gridding tiles.  A warp owns a kTileV x kTileU tile of grid cells for 32
+// consecutive channels, one channel per lane, and keeps the tile's 32 complex
+// accumulators of its channel in registers.  Every lane of a warp takes the
+// same visibility record at the same time; across 32 adjacent fine channels a
+// baseline's uv position moves by far less than a cell, so the lanes' centre
+// cells agree (or differ by one) and their table reads hit the same words.
+// No two warps write the same (cell, channel): there are no atomics.
+constexpr int kTileV = 4, kTileU = 8;          // cells per warp tile (rows, columns)
+constexpr int kLanes = 32;                     // channels per warp
 
-// Planar row pitch of a band during gridding: G + 4 floats, so that the 7 rows
-// x 4 columns of one footprint quarter fall in 28 distinct banks.
-__host__ __device__ constexpr int planar_pitch(int g) { return g + 4; }
+// Tiles cover the rows G/2 .. G-1 (v >= 0) of the grid's Hermitian part only
+// (the rows below are the conjugate reflection).
+__host__ __device__ constexpr int n_tiles_u(int g) { return g / kTileU; }
+__host__ __device__ constexpr int n_tiles(int g) { return (g / 2 / kTileV) * (g / kTileU); }
 
-// One band of grid rows of one channel: grid in shared memory, row FFTs in
-// place, central N columns written to h ([batch][G][N]).  The band's candidate
-// list is taken in chunks of blockDim/2 visibilities; a pair of threads
-// prepares one (exact u on the even thread, exact v on the odd one, the keep
-// test, the seven separable weights of each axis with the centring sign, and
-// Stokes I), then every warp takes whole records: lane (tv, tu) = (lane / 4,
-// lane % 4) adds taps (tv, tu) and (tv, tu + 4) of the 7 x 7 footprint.  The
-// band is held as two real planes during gridding (every atomic of a warp hits
-// its own bank) and in the interleaved, padded FFT layout afterwards; the
-// first FFT pass converts.
-template <int LOG2G, int S, bool CAL>
-__global__ void __launch_bounds__(1024)
-k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_off,
-            const int32_t* __restrict__ vis, long long n_bl, const Baseline* __restrict__ base,
-            const ChanScale* __restrict__ cs, const float* __restrict__ tab,
-            const float2* __restrict__ tw_g, int ch0, int n_img, int band_h,
-            int* __restrict__ kept, void* __restrict__ h, float* __restrict__ hs, GridOpts opt) {
+// Weights of the separable kernel indexed by (d, off): a tap d cells from the
+// centre cell of a position whose offset from that cell is off / Q weighs
+// C(d - off / Q) when |d| <= 3 and 0 otherwise.  The table holds every d in
+// [-kTabD, kTabD] at stride Q + 1, so (d, off) -> (d + kTabD) (Q + 1) + Q / 2 - off
+// is one-to-one over off in [-Q/2, Q/2] (d = 3 at off = -Q/2 and d = 4 at
+// off = Q/2 land on different entries) and a tile's weights are plain loads at
+// fixed strides from one base, with no range tests.
+constexpr int kTabD = kHalfSup + kTileU - 1;              // 10: offsets a tile column can take
+constexpr int kTabStride = kQ + 1;
+constexpr int kTabXLen = (2 * kTabD + 1) * kTabStride;
+
+// Per-channel record of one listed baseline, prepared once per channel group
+// by k_grid_prep: its exact rounded position p = rint(u Q), rint(v Q) and its
+// value in the Hermitian part of the grid, conj(Stokes I) / 2, or V = 0 when
+// the visibility is not gridded in that channel.  Layout [group][listed][32].
+struct PrepRec {
+  int pu, pv;
+  float vr, vi;
+};
+constexpr int kMirror = 1 << 31;    // tile list flag: grid the record's mirror (-u, -v, conj V)
+constexpr int kPrepPerWarp = 8;     // listed baselines per warp of k_grid_prep
+
+// a5 and the Stokes I of a6 for one channel group: a warp's lanes are the
+// group's 32 channels; for each of its listed baselines a lane decides the
+// exact rounded position (float-float, FP64 when that cannot decide), the keep
+// test (centre cell inside the grid's margin; the uv range when it must be
+// decided per channel), reads XX and YY and stores the record -- the image is
+// the real part of the transform, i.e. the transform of the grid's Hermitian
+// part H = (G + conj G(-u, -v)) / 2, so the record carries half of
+// conj(Stokes I) = conj(XX + YY) / 4 (the exp(+) transform is a forward FFT of
+// the conjugated grid); calibration corrections c_a conj(c_b) are applied per
+// polarisation in FP32 when given.  Kept visibilities are counted per channel.
+template <int LOG2G, bool CAL>
+__global__ void __launch_bounds__(256)
+k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* __restrict__ vis, long long n_bl,
+            const Baseline* __restrict__ base, const ChanScale* __restrict__ cs, int ch0, int nb,
+            int* __restrict__ kept, PrepRec* __restrict__ prep, GridOpts opt) {
   constexpr int G = 1 << LOG2G;
-  constexpr int LDP = band_pitch(G);
-  constexpr int P = planar_pitch(G);
-  static_assert(P <= LDP, "planar band fits in the FFT layout");
-  extern __shared__ __align__(16) unsigned char smem[];
-  float2* band = reinterpret_cast<float2*>(smem);                     // [band_h][LDP] (FFT layout)
-  float* pre = reinterpret_cast<float*>(smem);                        // [band_h][P]   (gridding)
-  float* pim = pre + band_h * P;
-  float2* tw = band + band_h * LDP;                                   // [G]
-  float4* r_hdr = reinterpret_cast<float4*>(tw + G);                  // [kRecMax] (Vr, Vi, base, kv_rel)
-  float2* r_wu = reinterpret_cast<float2*>(r_hdr + kRecMax);          // [kRecMax][kWuStride]
-  float* r_wv = reinterpret_cast<float*>(r_wu + kRecMax * kWuStride); // [kRecMax][kWvStride]
-  __shared__ int n_home, n_rec[2];
-  const int b = blockIdx.x, cb = blockIdx.y;
-  const long long chan = ch0 + cb;
-  for (int i = threadIdx.x; i < (2 * band_h * P) / 4; i += blockDim.x)
-    reinterpret_cast<float4*>(pre)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
-  if (threadIdx.x == 0) n_home = 0;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int group = blockIdx.y;
+  const int i0 = gw * kPrepPerWarp;
+  if (i0 >= n_listed) return;
+  const int i1 = min(n_listed, i0 + kPrepPerWarp);
+  const int cb = group * kLanes + lane;
+  const bool active = cb < nb;
+  const long long chan = ch0 + (active ? cb : nb - 1);
   const ChanScale s = cs[chan];
-  const int row0 = b * band_h;
   const int cmax = G / 2 - kHalfSup - 1;
   const int lim = (cmax + 1) * kQ;                     // < 2^21
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-  const int axis = threadIdx.x & 1;                  // 0: u, 1: v
-  const int chunk = blockDim.x >> 1;
-  const unsigned full = 0xffffffffu;
-  int my_home = 0;
-  const int e0 = band_off[b], e1 = band_off[b + 1];
-  const int pair = threadIdx.x >> 1;
-  // the fields of a candidate entry one thread of a pair needs
-  struct Ent {
-    int bl, cross, a, bf;
-    float h, l;                                      // this thread's axis, float-float
-  };
-  auto load_ent = [&](int e) {
-    Ent x{};
-    if (e < e1) {
-      const int4 hd = __ldg(reinterpret_cast<const int4*>(entries + e));
-      const float2 d = __ldg(reinterpret_cast<const float2*>(&entries[e].dxh) + axis);
-      x.bl = hd.x; x.cross = hd.y; x.a = hd.z; x.bf = hd.w;
-      x.h = d.x; x.l = d.y;
+  const int2* vis2 = reinterpret_cast<const int2*>(vis) + chan * n_bl * 4;
+  const float2* gc = (CAL && opt.gains != nullptr) ? opt.gains + chan * opt.n_input : nullptr;
+  PrepRec* out = prep + (static_cast<long long>(group) * n_listed) * kLanes + lane;
+  int n_kept = 0;
+  // two baselines ahead: their entries and visibility loads are in flight
+  GridEntry en = listed[i0];
+  int2 xx = __ldg(vis2 + static_cast<long long>(en.bl) * 4), yy = __ldg(vis2 + static_cast<long long>(en.bl) * 4 + 3);
+  GridEntry e1 = i0 + 1 < i1 ? listed[i0 + 1] : en;
+  for (int i = i0; i < i1; ++i) {
+    const int2 x1 = __ldg(vis2 + static_cast<long long>(e1.bl) * 4), y1 = __ldg(vis2 + static_cast<long long>(e1.bl) * 4 + 3);
+    const GridEntry e2 = i + 2 < i1 ? listed[i + 2] : e1;
+    int pu, pv;
+    if (!fast_rint_prod32(en.dxh, en.dxl, s, &pu)) {
+      const long long pl = __double2ll_rn(__dmul_rn(base[en.cross].dx, s.s));
+      pu = static_cast<int>(pl > lim ? lim : (pl < -lim ? -lim : pl));
     }
-    return x;
-  };
-  // a chunk's keep test and the loads its records need, taken one chunk ahead
-  struct Keep {
-    int cu, cv, off;
-    bool use;
-    int2 q;                                          // XX (even thread) or YY (odd thread)
-    float2 ca, cb;                                   // calibration corrections
-  };
-  auto keep_test = [&](const Ent& en, bool valid) {
-    Keep k{};
-    int cc = 0, off = 0;
-    bool in = false;
-    if (valid) {
-      int pc;
-      if (!fast_rint_prod32(en.h, en.l, s, &pc)) {
-        const Baseline B = base[en.cross];           // FP64 product of the definition
-        const long long pl = __double2ll_rn(__dmul_rn(axis ? B.dy : B.dx, s.s));
-        pc = static_cast<int>(pl > lim ? lim : (pl < -lim ? -lim : pl));
-      }
-      if (pc > -lim && pc < lim) {
-        centre_cell32(pc, cc, off);
-        in = cc <= cmax && cc >= -cmax;
-      }
-      // baselines straddling an edge of the uv range: decide in FP64, L * (nu / c)
-      if (CAL && axis == 0 && (en.bf & kCheckUv)) {
-        const double lam = __dmul_rn(opt.blen[en.cross], s.nu_c);
-        in = in && lam >= opt.uv_min && lam < opt.uv_max;
-      }
+    if (!fast_rint_prod32(en.dyh, en.dyl, s, &pv)) {
+      const long long pl = __double2ll_rn(__dmul_rn(base[en.cross].dy, s.s));
+      pv = static_cast<int>(pl > lim ? lim : (pl < -lim ? -lim : pl));
     }
-    const int cc_o = __shfl_xor_sync(full, cc, 1);
-    const int in_o = __shfl_xor_sync(full, in ? 1 : 0, 1);   // every lane takes part
-    const bool kp = in && in_o;
-    k.cu = axis ? cc_o : cc;
-    k.cv = axis ? cc : cc_o;
-    k.off = off;
-    const int kv_home = G / 2 + k.cv;
-    const int kv_rel = kv_home - kHalfSup - row0;
-    if (kp && axis && kv_home >= row0 && kv_home < row0 + band_h) ++my_home;
-    k.use = kp && kv_rel + kSupport > 0 && kv_rel < band_h;
-    if (k.use) {
-      k.q = __ldg(reinterpret_cast<const int2*>(vis) + (chan * n_bl + en.bl) * 4 + axis * 3);
-      if (CAL && opt.gains != nullptr) {
-        const float2* gc = opt.gains + chan * opt.n_input;
-        k.ca = __ldg(gc + 2 * en.a + axis);
-        k.cb = __ldg(gc + 2 * (en.bf & 0xffff) + axis);
-      }
+    bool keep = pu > -lim && pu < lim && pv > -lim && pv < lim;
+    if (keep) {
+      int cu, cv, o;
+      centre_cell32(pu, cu, o);
+      centre_cell32(pv, cv, o);
+      keep = cu <= cmax && cu >= -cmax && cv <= cmax && cv >= -cmax;
     }
-    return k;
-  };
-  if (threadIdx.x == 0) n_rec[0] = 0;
-  Keep kn = keep_test(load_ent(e0 + pair), e0 + pair < e1);
-  Ent en = load_ent(e0 + chunk + pair);
-  __syncthreads();
-  int it = 0;
-  for (int c0 = e0; c0 < e1; c0 += chunk, ++it) {
-    // ---- records of this chunk: one visibility per thread pair
-    // Stokes I = (XX + YY) / 2: XX on the even thread, YY on the odd one;
-    // exact integer sums, or with the calibration corrections c_a conj(c_b)
-    // applied per polarisation in FP32
-    const Keep k = kn;
-    float fr, fi;
-    if (!CAL || opt.gains == nullptr) {
-      const int sr = k.q.x + __shfl_xor_sync(full, k.q.x, 1);
-      const int si = k.q.y + __shfl_xor_sync(full, k.q.y, 1);
-      fr = static_cast<float>(sr);
-      fi = static_cast<float>(si);
-    } else {
-      float pr = 0.f, pi = 0.f;
-      if (k.use) {
-        const float vr = static_cast<float>(k.q.x), vi = static_cast<float>(k.q.y);
-        const float gr = k.ca.x * k.cb.x + k.ca.y * k.cb.y, gi = k.ca.y * k.cb.x - k.ca.x * k.cb.y;
-        pr = gr * vr - gi * vi;
-        pi = gr * vi + gi * vr;
-      }
-      fr = pr + __shfl_xor_sync(full, pr, 1);
-      fi = pi + __shfl_xor_sync(full, pi, 1);
+    if (CAL && (en.bf & kCheckUv)) {
+      const double lam = __dmul_rn(opt.blen[en.cross], s.nu_c);
+      keep = keep && lam >= opt.uv_min && lam < opt.uv_max;
     }
-    const unsigned m = __ballot_sync(full, k.use) & 0x55555555u;
-    int base_slot = 0;
-    if (lane == 0 && m) base_slot = atomicAdd(&n_rec[it & 1], __popc(m));
-    base_slot = __shfl_sync(full, base_slot, 0);
-    if (k.use) {
-      const int slot = base_slot + __popc(m & ((1u << (lane & ~1)) - 1u));
-      const int kv_rel = G / 2 + k.cv - kHalfSup - row0;
-      const int ku0 = G / 2 + k.cu - kHalfSup;
-      float w[8];
-#pragma unroll
-      for (int t = 0; t < kSupport; ++t) w[t] = __ldg(tab + kHalfTab + (t - kHalfSup) * kQ - k.off);
-      w[7] = 0.0f;
-      if (axis == 0) {
-        // (-1)^ku centring sign; conj of Stokes I: the exp(+) transform is a
-        // forward FFT of conj(G)
-#pragma unroll
-        for (int t = 0; t < kSupport; ++t)
-          if ((ku0 + t) & 1) w[t] = -w[t];
-        r_hdr[slot] = make_float4(0.5f * fr, -0.5f * fi, __int_as_float(kv_rel * P + ku0), __int_as_float(kv_rel));
-#pragma unroll
-        for (int t = 0; t < 4; ++t) r_wu[slot * kWuStride + t] = make_float2(w[t], w[t + 4]);
+    PrepRec r{lim, lim, 0.0f, 0.0f};
+    if (keep) {
+      float vr, vi;
+      if (!CAL || gc == nullptr) {
+        vr = 0.25f * static_cast<float>(xx.x + yy.x);
+        vi = -0.25f * static_cast<float>(xx.y + yy.y);
       } else {
-        const int kv0 = row0 + kv_rel;               // (-1)^kv centring sign
+        const int a = en.a, b = en.bf & 0xffff;
+        float pr = 0.f, pi = 0.f;
 #pragma unroll
-        for (int t = 0; t < kSupport; ++t)
-          if ((kv0 + t) & 1) w[t] = -w[t];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) r_wv[slot * kWvStride + t] = w[t];
+        for (int pol = 0; pol < 2; ++pol) {
+          const float2 ca = __ldg(gc + 2 * a + pol), cbv = __ldg(gc + 2 * b + pol);
+          const int2 q = pol ? yy : xx;
+          const float qr = static_cast<float>(q.x), qi = static_cast<float>(q.y);
+          const float gr = ca.x * cbv.x + ca.y * cbv.y, gi = ca.y * cbv.x - ca.x * cbv.y;
+          pr += gr * qr - gi * qi;
+          pi += gr * qi + gi * qr;
+        }
+        vr = 0.25f * pr;
+        vi = -0.25f * pi;
       }
+      r = PrepRec{pu, pv, vr, vi};
+      ++n_kept;
     }
-    __syncthreads();
-    const int nr = n_rec[it & 1];
-    if (threadIdx.x == 0) n_rec[(it + 1) & 1] = 0;   // last read before the previous barrier
-    // ---- the next chunk's keep test, visibility loads and the entries after
-    // it, in flight while this chunk is swept
-    kn = keep_test(en, c0 + chunk + pair < e1);
-    en = load_ent(c0 + 2 * chunk + pair);
-    // ---- sweep: one record per warp, 49 taps in four atomic instructions
-    const int tv = lane >> 2, tu = lane & 3;
-    for (int rec = warp; rec < nr; rec += n_warps) {
-      const float4 hd = r_hdr[rec];
-      const float2 wp = r_wu[rec * kWuStride + tu];
-      const float wv = r_wv[rec * kWvStride + tv];
-      const int row = __float_as_int(hd.w) + tv;
-      if (tv < kSupport && static_cast<unsigned>(row) < static_cast<unsigned>(band_h)) {
-        const int a = __float_as_int(hd.z) + tv * P + tu;
-        const float w0 = wv * wp.x;
-        atomicAdd(pre + a, w0 * hd.x);
-        atomicAdd(pim + a, w0 * hd.y);
-        if (tu < kSupport - 4) {
-          const float w1 = wv * wp.y;
-          atomicAdd(pre + a + 4, w1 * hd.x);
-          atomicAdd(pim + a + 4, w1 * hd.y);
+    reinterpret_cast<int4*>(out)[static_cast<long long>(i) * kLanes] =
+        make_int4(r.pu, r.pv, __float_as_int(r.vr), __float_as_int(r.vi));
+    en = e1;
+    e1 = e2;
+    xx = x1;
+    yy = y1;
+  }
+  if (active && n_kept) atomicAdd(kept + chan, n_kept);
+}
+
+// Gridding of one channel batch into the Hermitian part of the grid, rows
+// G/2 .. G-1 (v >= 0; a record whose footprint lies below is listed as its
+// mirror, one straddling row G/2 as both).  Work items are (group of 32
+// channels, warp tile) pairs, group-major, the tiles of a group taken from the
+// longest list to the shortest; every warp of the persistent grid (one CTA of
+// kGridWarps warps per SM) takes items kGridWarps * gridDim.x apart, so each
+// warp starts on a heavy tile and ends on light ones.  The gap-indexed weight table sits in shared memory,
+// loaded once per CTA.  For every list entry of its tile, a lane reads its
+// channel's prepared record (one 16-byte load, the warp's 32 lanes
+// contiguous), mirrors it if flagged, takes the centre cells and the tile's 4
+// row and 8 column weights of the separable kernel, and adds the products into
+// its accumulators; list entries are read three records ahead, records two.
+// The tile is written with the (-1)^(row + col) centring sign as two real
+// planes, grid [batch][2][G/2][G] (row j - G/2).
+constexpr int kGridWarps = 16;
+constexpr size_t kTileSmem = static_cast<size_t>(kTabXLen) * sizeof(float);
+
+template <int LOG2G>
+__global__ void __launch_bounds__(kGridWarps * 32, 1)
+k_grid_tiles(const int* __restrict__ tile_idx, const int* __restrict__ tile_off, const int* __restrict__ tile_order,
+             const PrepRec* __restrict__ prep, int n_listed, const float* __restrict__ tabx_g, int nb,
+             float* __restrict__ grid) {
+  constexpr int G = 1 << LOG2G;
+  constexpr int NTU = n_tiles_u(G);
+  constexpr int NT = n_tiles(G);
+  constexpr long long PLANE = static_cast<long long>(G / 2) * G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* tabx = reinterpret_cast<float*>(smem);
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kTabXLen / 4; i += blockDim.x)
+    reinterpret_cast<float4*>(tabx)[i] = __ldg(reinterpret_cast<const float4*>(tabx_g) + i);
+  for (int i = (kTabXLen / 4) * 4 + threadIdx.x; i < kTabXLen; i += blockDim.x) tabx[i] = __ldg(tabx_g + i);
+  __syncthreads();
+  const int n_groups = (nb + kLanes - 1) / kLanes;
+  const long long n_items = static_cast<long long>(n_groups) * NT;
+  const int stride = gridDim.x * kGridWarps;
+#pragma unroll 1
+  for (long long item = static_cast<long long>(blockIdx.x) * kGridWarps + warp; item < n_items; item += stride) {
+    const int g = static_cast<int>(item / NT);
+    const int tile = __ldg(tile_order + (item - static_cast<long long>(g) * NT));
+    const int cb = g * kLanes + lane;                 // channel within the batch
+    const PrepRec* pg = prep + static_cast<long long>(g) * n_listed * kLanes + lane;
+    const int tv = tile / NTU, tu = tile - tv * NTU;
+    const int r0 = G / 2 + tv * kTileV, c0 = tu * kTileU;
+    const int e0 = tile_off[tile], e1 = tile_off[tile + 1];
+    float acr[kTileV][kTileU], aci[kTileV][kTileU];
+#pragma unroll
+    for (int i = 0; i < kTileV; ++i)
+#pragma unroll
+      for (int j = 0; j < kTileU; ++j) acr[i][j] = aci[i][j] = 0.0f;
+    auto index = [&](int e) { return e < e1 ? __ldg(tile_idx + e) : 0; };
+    auto record = [&](int ent) {
+      const int4 v = __ldg(reinterpret_cast<const int4*>(pg + static_cast<long long>(ent & ~kMirror) * kLanes));
+      if (ent & kMirror) return PrepRec{-v.x, -v.y, __int_as_float(v.z), -__int_as_float(v.w)};
+      return PrepRec{v.x, v.y, __int_as_float(v.z), __int_as_float(v.w)};
+    };
+    int i2 = index(e0 + 2);
+    PrepRec rc = record(index(e0)), r1 = record(index(e0 + 1));
+#pragma unroll 1
+    for (int e = e0; e < e1; ++e) {
+      // records e + 1 and e + 2 in flight; list entry e + 3 in flight
+      const PrepRec r2 = record(i2);
+      i2 = index(e + 3);
+      int cu, offu, cv, offv;
+      centre_cell32(rc.pu, cu, offu);
+      centre_cell32(rc.pv, cv, offv);
+      int dv0 = r0 - (G / 2 + cv), du0 = c0 - (G / 2 + cu);   // offsets of the tile's first row / column
+      const bool touch = dv0 <= kHalfSup && dv0 >= -(kHalfSup + kTileV - 1) && du0 <= kHalfSup &&
+                         du0 >= -(kHalfSup + kTileU - 1);
+      if (__any_sync(full, touch)) {
+        float vr = rc.vr, vi = rc.vi;
+        if (!touch) {
+          // a lane whose footprint misses the tile adds zeros; its table
+          // reads stay inside the table
+          vr = vi = 0.0f;
+          dv0 = du0 = 0;
+          offu = offv = 0;
+        }
+        const float* bu = tabx + (du0 + kTabD) * kTabStride + kQ / 2 - offu;
+        const float* bv = tabx + (dv0 + kTabD) * kTabStride + kQ / 2 - offv;
+        float wv[kTileV], wu[kTileU];
+#pragma unroll
+        for (int i = 0; i < kTileV; ++i) wv[i] = bv[i * kTabStride];
+#pragma unroll
+        for (int j = 0; j < kTileU; ++j) wu[j] = bu[j * kTabStride];
+#pragma unroll
+        for (int i = 0; i < kTileV; ++i) {
+          const float br = wv[i] * vr, bi = wv[i] * vi;
+#pragma unroll
+          for (int j = 0; j < kTileU; ++j) {
+            acr[i][j] = fmaf(br, wu[j], acr[i][j]);
+            aci[i][j] = fmaf(bi, wu[j], aci[i][j]);
+          }
+        }
+      }
+      rc = r1;
+      r1 = r2;
+    }
+    // ---- the tile, with the centring sign (r0 and c0 are even)
+    if (cb < nb) {
+      float* gr = grid + static_cast<long long>(cb) * 2 * PLANE;
+      float* gi = gr + PLANE;
+#pragma unroll
+      for (int i = 0; i < kTileV; ++i) {
+        float vr[kTileU], vi[kTileU];
+#pragma unroll
+        for (int j = 0; j < kTileU; ++j) {
+          const bool neg = (i + j) & 1;
+          vr[j] = neg ? -acr[i][j] : acr[i][j];
+          vi[j] = neg ? -aci[i][j] : aci[i][j];
+        }
+        const long long row = r0 + i - G / 2;
+        float4* pr = reinterpret_cast<float4*>(gr + row * G + c0);
+        float4* pi = reinterpret_cast<float4*>(gi + row * G + c0);
+#pragma unroll
+        for (int j = 0; j < kTileU / 4; ++j) {
+          pr[j] = make_float4(vr[4 * j], vr[4 * j + 1], vr[4 * j + 2], vr[4 * j + 3]);
+          pi[j] = make_float4(vi[4 * j], vi[4 * j + 1], vi[4 * j + 2], vi[4 * j + 3]);
         }
       }
     }
-    __syncthreads();
   }
-  if (my_home) atomicAdd(&n_home, my_home);
-  __syncthreads();
-  if (threadIdx.x == 0 && n_home) atomicAdd(kept + chan, n_home);
-  fft_rows_inplace<LOG2G>(band, LDP, tw, pre, pim, P);
-  // central N columns of each transformed row, in the storage format
+}
+
+// The central N columns of the row transforms of a band of rows in shared
+// memory, into the half-transformed grid h ([batch][G][N]) in its storage format.
+template <int G, int LDP, int S>
+__device__ __forceinline__ void store_band(const float2* band, int band_h, int n_img, long long hrow0, void* h,
+                                           float* hs) {
+  // band_h: the rows to store (the first rows of the band)
   const int offc = G / 2 - n_img / 2;
-  const long long hrow0 = static_cast<long long>(cb) * G + row0;
   if constexpr (S == kStoreF32) {
     float2* hb = static_cast<float2*>(h) + hrow0 * n_img;
     for (int i = threadIdx.x; i < band_h * n_img; i += blockDim.x) {
@@ -433,6 +487,52 @@ k_grid_rows(const GridEntry* __restrict__ entries, const int* __restrict__ band_
   }
 }
 
+// Row pitch (floats) of the two real planes of a band staged in shared
+// memory: G + 4, 16-byte rows (the planes overlap the FFT layout, which the
+// first Stockham pass only writes after all its reads).
+__host__ __device__ constexpr int planar_pitch(int g) { return g + 4; }
+
+// Rows of the half-transformed grid kept per channel: the gridded plane is the
+// Hermitian part H of the grid on its rows j = G/2 .. G-1; the row transforms
+// of H satisfy R(G - j, k) = conj R(j, k), and row 0 is empty (no footprint
+// reaches it), so these G/2 rows carry everything the column pass needs.
+__host__ __device__ constexpr int half_rows(int g) { return g / 2; }
+
+// Row transforms of one band of rows of the gridded half plane of one channel:
+// the two real planes are staged in shared memory with 16-byte loads (all in
+// flight at once), the first Stockham pass reads them, the rest run in place;
+// the central N columns go to h ([batch][G/2][N], row j - G/2).
+template <int LOG2G, int S>
+__global__ void __launch_bounds__(1024)
+k_fft_rows(const float* __restrict__ grid, const float2* __restrict__ tw_g, int n_img, int band_h,
+           void* __restrict__ h, float* __restrict__ hs) {
+  constexpr int G = 1 << LOG2G;
+  constexpr int LDP = band_pitch(G);
+  constexpr int P = planar_pitch(G);
+  static_assert(2 * P <= 2 * LDP, "planar band fits in the FFT layout");
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* band = reinterpret_cast<float2*>(smem);     // [band_h][LDP]
+  float* pre = reinterpret_cast<float*>(smem);        // [band_h][P] (staging)
+  float* pim = pre + band_h * P;
+  float2* tw = band + band_h * LDP;                   // [G]
+  const int b = blockIdx.x, cb = blockIdx.y;
+  const int row0 = b * band_h;
+  for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
+  const long long plane4 = static_cast<long long>(half_rows(G)) * G / 4;
+  const float4* src = reinterpret_cast<const float4*>(grid) + static_cast<long long>(cb) * 2 * plane4 +
+                      static_cast<long long>(row0) * (G / 4);
+  constexpr int RQ = G / 4;                           // float4 per row
+  for (int i = threadIdx.x; i < 2 * band_h * RQ; i += blockDim.x) {
+    const int pl = i / (band_h * RQ), k = i - pl * band_h * RQ;
+    const int r = k / RQ, c = k - r * RQ;
+    const float4 v = __ldg(src + pl * plane4 + static_cast<long long>(r) * RQ + c);
+    *reinterpret_cast<float4*>((pl ? pim : pre) + r * P + 4 * c) = v;
+  }
+  __syncthreads();
+  fft_rows_inplace<LOG2G>(band, LDP, tw, pre, pim, P);
+  store_band<G, LDP, S>(band, band_h, n_img, static_cast<long long>(cb) * half_rows(G) + row0, h, hs);
+}
+
 // Two adjacent values (idx even) of the half-transformed grid in FP32.
 template <int S>
 __device__ __forceinline__ void load_h2(const void* h, const float* hs, long long row, long long idx, float2& v0,
@@ -464,12 +564,12 @@ __device__ __forceinline__ void load_h2(const void* h, const float* hs, long lon
 
 // Column transforms of the N central columns and the image itself.
 //
-// The image is the real part of the transform.  The real part of the DFT of a
-// column c is the DFT of its Hermitian part (c(k) + conj c(-k)) / 2 (indices
-// mod G), whose DFT is real; so two columns c1, c2 share one complex FFT of
-// d = h1 + i h2, with DFT Re DFT(c1) + i Re DFT(c2).  d is formed, doubled,
-// while the column pair is read (rows k and G - k together), and the output
-// scale takes the factor 1/2 back.  C columns per CTA, C / 2 transforms.
+// The row transforms are of the Hermitian part of the grid, so every column c
+// satisfies c(-k) = conj c(k) and its DFT is real: two columns c1, c2 share
+// one complex FFT of d = c1 + i c2, whose DFT is DFT(c1) + i DFT(c2).  Rows
+// G/2 .. G-1 are read; rows G/2 - r are their conjugates and row 0 is empty.
+// d is formed doubled and the output scale takes the factor 1/2 back.  C
+// columns per CTA, C / 2 transforms.
 template <int LOG2G, int S>
 __global__ void __launch_bounds__(512, 2)
 k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, int cols_per_cta, int ch0,
@@ -483,35 +583,32 @@ k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, 
   float2* tw = A + CP * LDP;
   const int cb = blockIdx.y;
   const int c0 = blockIdx.x * C;
-  const long long hrow0 = static_cast<long long>(cb) * G;
+  const long long hrow0 = static_cast<long long>(cb) * half_rows(G);
   for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
   // U items per thread in flight: the reads come from L2 and would otherwise
   // wait one round trip each
   constexpr int U = 4;
-  const int n_items = (G / 2 + 1) * CP;
+  const int n_items = half_rows(G) * CP;
+  for (int p = threadIdx.x; p < CP; p += blockDim.x) A[p * LDP] = make_float2(0.0f, 0.0f);   // row 0: empty
   for (int i0 = threadIdx.x; i0 < n_items; i0 += U * blockDim.x) {
-    float2 a[U], e[U], b[U], f[U];                    // c1(k), c2(k), c1(-k), c2(-k)
+    float2 a[U], e[U];                                // c1, c2 at row j = G/2 + r
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * blockDim.x;
       if (i < n_items) {
-        const int k = i / CP, p = i - k * CP;
-        const int km = (G - k) & (G - 1);
-        load_h2<S>(h, hs, hrow0 + k, (hrow0 + k) * n_img + c0 + 2 * p, a[u], e[u]);
-        load_h2<S>(h, hs, hrow0 + km, (hrow0 + km) * n_img + c0 + 2 * p, b[u], f[u]);
+        const int r = i / CP, p = i - r * CP;
+        load_h2<S>(h, hs, hrow0 + r, (hrow0 + r) * n_img + c0 + 2 * p, a[u], e[u]);
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * blockDim.x;
       if (i < n_items) {
-        const int k = i / CP, p = i - k * CP;
-        const int km = (G - k) & (G - 1);
-        A[p * LDP + pad16(k)] =
-            make_float2((a[u].x + b[u].x) - (e[u].y - f[u].y), (a[u].y - b[u].y) + (e[u].x + f[u].x));
-        if (km != k)
-          A[p * LDP + pad16(km)] =
-              make_float2((b[u].x + a[u].x) - (f[u].y - e[u].y), (b[u].y - a[u].y) + (f[u].x + e[u].x));
+        const int r = i / CP, p = i - r * CP;
+        const int j = G / 2 + r, jm = G / 2 - r;      // rows j and G - j
+        // d = 2 (c1 + i c2); at G - j the columns are conjugated
+        A[p * LDP + pad16(j)] = make_float2(2.0f * (a[u].x - e[u].y), 2.0f * (a[u].y + e[u].x));
+        if (r > 0) A[p * LDP + pad16(jm)] = make_float2(2.0f * (a[u].x + e[u].y), 2.0f * (e[u].x - a[u].y));
       }
     }
   }
@@ -560,7 +657,7 @@ __global__ void k_counts_out(const int* __restrict__ kept, int n_chan, int32_t* 
 
 // ---------------------------------------------------------------- planning
 struct ImgPlan {
-  int n, g, log2g, band_h, n_bands, batch, cols_per_cta, storage;
+  int n, g, log2g, band_h, batch, cols_per_cta, storage;
   long long n_cross;
 };
 
@@ -570,15 +667,18 @@ ImgPlan make_plan(int n_ant, int n_chan, int n, int storage) {
   p.storage = storage;
   p.g = kPad * n;
   p.log2g = ilog2(p.g);
-  // 16384 complex values per band: one CTA of 1024 threads per SM, and each
-  // 7-row footprint spills into a second band only (7 - 1) / band_h of the time
-  p.band_h = 16384 / p.g < p.g ? 16384 / p.g : p.g;
-  p.n_bands = p.g / p.band_h;
+  // row transforms: 8192 complex values per band, 512-thread CTAs (several
+  // per SM, so one band's loads overlap another's transforms)
+  p.band_h = 8192 / p.g < p.g / 2 ? 8192 / p.g : p.g / 2;
   p.n_cross = static_cast<long long>(n_ant) * (n_ant - 1) / 2;
-  const long long h_bytes = 8LL * p.g * n;           // half-transformed grid of one channel
-  long long b = (64LL << 20) / h_bytes;
-  if (b < 1) b = 1;
-  if (b > 64) b = 64;
+  // channels per launch: whole groups of 32 (one per lane of a tile warp);
+  // the gridded half planes, the prepared records and the half-transformed
+  // grids of a batch together up to about 256 MB (the autotuner picks among
+  // this and its halves down to 32 channels)
+  const long long per = 4LL * p.g * p.g + 4LL * p.g * n + 16LL * std::max<long long>(1, p.n_cross);
+  long long b = ((256LL << 20) / per) / kLanes * kLanes;
+  if (b < kLanes) b = kLanes;
+  if (b > 256) b = 256;
   if (b > n_chan) b = n_chan;
   p.batch = static_cast<int>(b);
   // an even number of columns per CTA (the column pass pairs them)
@@ -593,6 +693,7 @@ ImgPlan make_plan(int n_ant, int n_chan, int n, int storage) {
 
 struct ImgWs {
   float* tab;
+  float* tabx;       // [kTabXLen] weights by (tap offset, position offset)
   float* inv_corr;
   float2* tw;
   uint8_t* mask;
@@ -601,43 +702,53 @@ struct ImgWs {
   Baseline* base;
   ChanScale* cs;
   int* kept;
-  int* band_off;
-  GridEntry* entries;
+  GridEntry* listed; // baselines that can be gridded in some channel of the call
+  int* tile_off;     // [n_tiles + 1]
+  int* tile_order;   // [n_tiles] tiles by descending list length
+  int* tile_idx;     // per tile: indices into listed
   double* blen;      // [n_cross] baseline lengths (metres)
+  PrepRec* prep;     // [batch groups][n_cross][32] prepared records
+  float* grid;       // [batch][2][G][G] gridded planes (re, im)
   void* h;           // [batch][G][N] complex in the storage format
   float* hs;         // [batch][G] row scales (FP16 storage)
+  int n_listed = 0;
 };
 
-// Candidate entries: each cross baseline once per band it can touch (at most
-// 2 for 7-row footprints in >= 4-row bands... bounded by n_bands in general).
-long long entry_capacity(const ImgPlan& p) {
-  const long long per = std::min<long long>(p.n_bands, kSupport + 2);
-  return std::max<long long>(1, p.n_cross * per);
-}
+// Tile list entries: each listed baseline once per warp tile its footprint, or
+// its mirror's, can touch in the gridded half plane in some channel of the
+// call.  Over a coarse channel a footprint moves by at most a cell, so a
+// baseline touches 6 tiles of 4 x 8 (a footprint straddling row G/2 up to 6
+// more through its mirror; at most 16 when its centre moves by a few cells).
+constexpr int kEntriesPerBaseline = 16;
+long long entry_capacity(const ImgPlan& p) { return std::max<long long>(1, p.n_cross * kEntriesPerBaseline); }
 
 ImgWs carve_img(void* ws, size_t bytes, const ImgPlan& p, int n_ant, int n_chan, size_t* need) {
   Carver c(ws, bytes);
   ImgWs w;
+  const size_t nx = p.n_cross > 0 ? static_cast<size_t>(p.n_cross) : 1;
   w.tab = c.take<float>(kTabLen);
+  w.tabx = c.take<float>(kTabXLen);
   w.inv_corr = c.take<float>(p.n);
   w.tw = c.take<float2>(p.g);
   w.mask = c.take<uint8_t>(static_cast<size_t>(p.n) * p.n);
   w.ant = c.take<double>(static_cast<size_t>(n_ant) * 3);
   w.freq = c.take<double>(n_chan);
-  w.base = c.take<Baseline>(p.n_cross > 0 ? p.n_cross : 1);
+  w.base = c.take<Baseline>(nx);
   w.cs = c.take<ChanScale>(n_chan);
   w.kept = c.take<int>(n_chan);
-  w.band_off = c.take<int>(p.n_bands + 1);
-  w.entries = c.take<GridEntry>(entry_capacity(p));
-  w.blen = c.take<double>(p.n_cross > 0 ? p.n_cross : 1);
-  w.h = c.take<float2>(static_cast<size_t>(p.batch) * p.g * p.n);
-  w.hs = c.take<float>(static_cast<size_t>(p.batch) * p.g);
+  w.listed = c.take<GridEntry>(nx);
+  w.tile_off = c.take<int>(n_tiles(p.g) + 1);
+  w.tile_order = c.take<int>(n_tiles(p.g));
+  w.tile_idx = c.take<int>(entry_capacity(p));
+  w.blen = c.take<double>(nx);
+  w.prep = c.take<PrepRec>(static_cast<size_t>((p.batch + kLanes - 1) / kLanes) * nx * kLanes);
+  w.grid = c.take<float>(static_cast<size_t>(p.batch) * 2 * half_rows(p.g) * p.g);
+  w.h = c.take<float2>(static_cast<size_t>(p.batch) * half_rows(p.g) * p.n);
+  w.hs = c.take<float>(static_cast<size_t>(p.batch) * half_rows(p.g));
   *need = c.used;
   return w;
 }
 
-// Host: which baselines can touch which band of grid rows for any channel of
-// the call (u, v scale linearly with frequency; one cell of margin).
 // Baseline length in metres, sqrt(dx^2 + dy^2) in FP64 (host code is built
 // without FMA contraction, so this rounds like the definition).
 double baseline_length(const double* ant, int a, int b) {
@@ -646,27 +757,46 @@ double baseline_length(const double* ant, int a, int b) {
   return std::sqrt(x2 + y2);
 }
 
+// Centre cell of a rounded position p (1/Q cells): p / Q rounded half away from zero.
+long long centre_cell_host(long long p) {
+  const long long c = (std::llabs(p) + kQ / 2) / kQ;
+  return p < 0 ? -c : c;
+}
+
+// Host: which baselines can touch which warp tile in some channel of the call.
+// The channel scales s_nu Q are computed exactly as the device computes them
+// (k_chan_scale), and p = rint(dx s) is monotone in s, so the centre cells of
+// every channel lie between those at the smallest and the largest scale.
 void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double* freq, int n_chan,
-                   double cell, double uv_min, double uv_max, std::vector<GridEntry>& out, std::vector<int>& off) {
+                   double cell, double uv_min, double uv_max, std::vector<GridEntry>& listed,
+                   std::vector<int>& idx, std::vector<int>& off) {
   const double du = 1.0 / (static_cast<double>(p.g) * cell);
-  double fmin = freq[0], fmax = freq[0];
-  for (int f = 1; f < n_chan; ++f) {
+  double s_lo = HUGE_VAL, s_hi = -HUGE_VAL, fmin = freq[0], fmax = freq[0];
+  for (int f = 0; f < n_chan; ++f) {
+    const double sq = (freq[f] / (kCLight * du)) * static_cast<double>(kQ);
+    s_lo = std::min(s_lo, sq);
+    s_hi = std::max(s_hi, sq);
     fmin = std::min(fmin, freq[f]);
     fmax = std::max(fmax, freq[f]);
   }
-  const double s_lo = fmin / (kCLight * du), s_hi = fmax / (kCLight * du);   // cells per metre
   const bool uv_cut = uv_min > 0.0 || std::isfinite(uv_max);
   const double w_lo = fmin / kCLight, w_hi = fmax / kCLight;                  // wavelengths per metre
-  const int cmax = p.g / 2 - kHalfSup - 1;
-  std::vector<std::vector<GridEntry>> bands(p.n_bands);
+  const long long cmax = p.g / 2 - kHalfSup - 1;
+  const int ntu = n_tiles_u(p.g), nt = n_tiles(p.g);
+  std::vector<std::vector<int>> tiles(nt);
+  auto cells = [&](double d, long long& lo, long long& hi) {
+    const long long a = centre_cell_host(std::llrint(d * s_lo)), b = centre_cell_host(std::llrint(d * s_hi));
+    lo = std::max(std::min(a, b), -cmax);
+    hi = std::min(std::max(a, b), cmax);
+    return lo <= hi;
+  };
+  listed.clear();
   long long cross = 0;
   for (int a = 0; a < n_ant; ++a)
     for (int b = a + 1; b < n_ant; ++b, ++cross) {
       const double dx = ant[3 * a] - ant[3 * b], dy = ant[3 * a + 1] - ant[3 * b + 1];
-      const double u0 = std::min(dx * s_lo, dx * s_hi), u1 = std::max(dx * s_lo, dx * s_hi);
-      const double v0 = std::min(dy * s_lo, dy * s_hi), v1 = std::max(dy * s_lo, dy * s_hi);
-      // can the centre cell ever satisfy |c0| <= cmax?
-      if (u0 > cmax + 1.5 || u1 < -cmax - 1.5 || v0 > cmax + 1.5 || v1 < -cmax - 1.5) continue;
+      long long u0, u1, v0, v1;
+      if (!cells(dx, u0, u1) || !cells(dy, v0, v1)) continue;       // never on the grid
       // uv range: decided here when every channel of the call agrees (with a
       // relative margin), per channel on the device otherwise
       bool check = false;
@@ -676,10 +806,6 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
         if (l1 < uv_min * (1.0 - eps) || l0 >= uv_max * (1.0 + eps)) continue;      // always outside
         check = !(l0 >= uv_min * (1.0 + eps) && l1 < uv_max * (1.0 - eps));       // not always inside
       }
-      int r_lo = p.g / 2 + static_cast<int>(std::floor(v0)) - 1 - kHalfSup;
-      int r_hi = p.g / 2 + static_cast<int>(std::ceil(v1)) + 1 + kHalfSup;
-      r_lo = std::max(r_lo, 0);
-      r_hi = std::min(r_hi, p.g - 1);
       GridEntry e;
       e.bl = static_cast<int>(a * static_cast<long long>(n_ant) - static_cast<long long>(a) * (a - 1) / 2 + (b - a));
       e.cross = static_cast<int>(cross);
@@ -689,34 +815,67 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
       e.dxl = static_cast<float>(dx - static_cast<double>(e.dxh));
       e.dyh = static_cast<float>(dy);
       e.dyl = static_cast<float>(dy - static_cast<double>(e.dyh));
-      for (int bd = r_lo / p.band_h; bd <= r_hi / p.band_h; ++bd) bands[bd].push_back(e);
+      const int li = static_cast<int>(listed.size());
+      listed.push_back(e);
+      // footprint rows / columns over the call (centre +- 3 cells), of the
+      // record and of its mirror, within the gridded rows G/2 .. G-1
+      auto add = [&](long long vl, long long vh, long long ul, long long uh, int flag) {
+        const int r_lo = static_cast<int>(std::max<long long>(p.g / 2, p.g / 2 + vl - kHalfSup));
+        const int r_hi = static_cast<int>(p.g / 2 + vh + kHalfSup);
+        if (r_hi < r_lo) return;
+        const int c_lo = static_cast<int>(p.g / 2 + ul - kHalfSup), c_hi = static_cast<int>(p.g / 2 + uh + kHalfSup);
+        for (int tv = (r_lo - p.g / 2) / kTileV; tv <= (r_hi - p.g / 2) / kTileV; ++tv)
+          for (int tu = c_lo / kTileU; tu <= c_hi / kTileU; ++tu) tiles[tv * ntu + tu].push_back(li | flag);
+      };
+      add(v0, v1, u0, u1, 0);
+      add(-v1, -v0, -u1, -u0, kMirror);
     }
-  out.clear();
-  off.assign(p.n_bands + 1, 0);
-  for (int bd = 0; bd < p.n_bands; ++bd) {
-    off[bd] = static_cast<int>(out.size());
-    out.insert(out.end(), bands[bd].begin(), bands[bd].end());
+  idx.clear();
+  off.assign(nt + 1, 0);
+  for (int t = 0; t < nt; ++t) {
+    off[t] = static_cast<int>(idx.size());
+    idx.insert(idx.end(), tiles[t].begin(), tiles[t].end());
   }
-  off[p.n_bands] = static_cast<int>(out.size());
+  off[nt] = static_cast<int>(idx.size());
 }
 
 template <int L, int S>
-int launch_bands(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int32_t* vis, long long n_bl, int ch0,
+int launch_batch(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int32_t* vis, long long n_bl, int ch0,
                  int nb, float* img, cudaStream_t st) {
   constexpr int G = 1 << L;
   constexpr int LDP = band_pitch(G);
   {
-    const size_t sm = static_cast<size_t>(p.band_h) * LDP * sizeof(float2) + G * sizeof(float2) +
-                      kRecMax * (sizeof(float4) + kWuStride * sizeof(float2) + kWvStride * sizeof(float));
     // calibration corrections or a uv range select the variant that applies them
     const bool cal = o.gains != nullptr || o.uv_min > 0.0 || std::isfinite(o.uv_max);
-    auto kern = cal ? k_grid_rows<L, S, true> : k_grid_rows<L, S, false>;
-    OVRO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    const int n_groups = (nb + kLanes - 1) / kLanes;
+    if (w.n_listed > 0) {
+      dim3 grid((w.n_listed + 8 * kPrepPerWarp - 1) / (8 * kPrepPerWarp), n_groups);
+      OVRO_PROF("k_grid_prep", st);
+      if (cal)
+        k_grid_prep<L, true><<<grid, 256, 0, st>>>(w.listed, w.n_listed, vis, n_bl, w.base, w.cs, ch0, nb, w.kept,
+                                                   w.prep, o);
+      else
+        k_grid_prep<L, false><<<grid, 256, 0, st>>>(w.listed, w.n_listed, vis, n_bl, w.base, w.cs, ch0, nb, w.kept,
+                                                    w.prep, o);
+      OVRO_LAUNCH_CHECK();
+    }
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid_tiles<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kTileSmem)));
+    const long long items = static_cast<long long>(n_groups) * n_tiles(G);
+    const long long ctas = std::min<long long>(num_sms(), (items + kGridWarps - 1) / kGridWarps);
+    OVRO_PROF("k_grid_tiles", st);
+    k_grid_tiles<L><<<static_cast<unsigned>(ctas), kGridWarps * 32, kTileSmem, st>>>(
+        w.tile_idx, w.tile_off, w.tile_order, w.prep, w.n_listed, w.tabx, nb, w.grid);
+    OVRO_LAUNCH_CHECK();
+  }
+  {
+    const size_t sm = static_cast<size_t>(p.band_h) * LDP * sizeof(float2) + G * sizeof(float2);
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<L, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm)));
     const int threads = p.band_h * G / 16;
-    dim3 grid(p.n_bands, nb);
-    OVRO_PROF("k_grid_rows", st);
-    kern<<<grid, threads, sm, st>>>(w.entries, w.band_off, vis, n_bl, w.base, w.cs, w.tab, w.tw, ch0, p.n, p.band_h,
-                                    w.kept, w.h, w.hs, o);
+    dim3 grid(half_rows(G) / p.band_h, nb);
+    OVRO_PROF("k_fft_rows", st);
+    k_fft_rows<L, S><<<grid, threads, sm, st>>>(w.grid, w.tw, p.n, p.band_h, w.h, w.hs);
     OVRO_LAUNCH_CHECK();
   }
   {
@@ -737,14 +896,14 @@ template <int L>
 int launch_storage(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int32_t* vis, long long n_bl, int ch0,
                    int nb, float* img, cudaStream_t st) {
   switch (p.storage) {
-    case kStoreF32: return launch_bands<L, kStoreF32>(p, w, o, vis, n_bl, ch0, nb, img, st);
-    case kStoreBF16: return launch_bands<L, kStoreBF16>(p, w, o, vis, n_bl, ch0, nb, img, st);
-    case kStoreF16: return launch_bands<L, kStoreF16>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case kStoreF32: return launch_batch<L, kStoreF32>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case kStoreBF16: return launch_batch<L, kStoreBF16>(p, w, o, vis, n_bl, ch0, nb, img, st);
+    case kStoreF16: return launch_batch<L, kStoreF16>(p, w, o, vis, n_bl, ch0, nb, img, st);
     default: return OVRO_ERR_INVALID_ARG;
   }
 }
 
-int run_bands(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int32_t* vis, long long n_bl, int ch0,
+int run_batch(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int32_t* vis, long long n_bl, int ch0,
               int nb, float* img, cudaStream_t st) {
   switch (p.log2g) {
     case 5: return launch_storage<5>(p, w, o, vis, n_bl, ch0, nb, img, st);
@@ -758,7 +917,7 @@ int run_bands(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int32_t
   }
 }
 
-int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_ant,
+int upload_common(const ImgPlan& p, ImgWs& w, int n_ant, const double* h_ant,
                   const double* h_freq, int n_chan, double cell, cudaStream_t st,
                   double uv_min = 0.0, double uv_max = HUGE_VAL) {
   const KernelTables& kt = kernel_tables();
@@ -766,10 +925,11 @@ int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_a
   grid_correction(p.n, p.g, corr);
   std::vector<float> inv(p.n);
   for (int i = 0; i < p.n; ++i) inv[i] = static_cast<float>(1.0 / corr[i]);
-  std::vector<GridEntry> entries;
-  std::vector<int> off;
-  build_entries(p, n_ant, h_ant, h_freq, n_chan, cell, uv_min, uv_max, entries, off);
-  if (static_cast<long long>(entries.size()) > entry_capacity(p)) return OVRO_ERR_CAPACITY;
+  std::vector<GridEntry> listed;
+  std::vector<int> idx, off;
+  build_entries(p, n_ant, h_ant, h_freq, n_chan, cell, uv_min, uv_max, listed, idx, off);
+  if (static_cast<long long>(idx.size()) > entry_capacity(p)) return OVRO_ERR_CAPACITY;
+  w.n_listed = static_cast<int>(listed.size());
   std::vector<double> blen(p.n_cross > 0 ? p.n_cross : 1, 0.0);
   {
     long long x = 0;
@@ -779,15 +939,27 @@ int upload_common(const ImgPlan& p, const ImgWs& w, int n_ant, const double* h_a
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.blen, blen.data(), blen.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.tab, kt.table32.data(), kTabLen * sizeof(float),
                                 cudaMemcpyHostToDevice, st));
+  std::vector<float> tabx(kTabXLen, 0.0f);
+  for (int d = -kHalfSup; d <= kHalfSup; ++d)
+    for (int off = -kQ / 2; off <= kQ / 2; ++off)
+      tabx[(d + kTabD) * kTabStride + kQ / 2 - off] = kt.table32[kHalfTab + d * kQ - off];
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.tabx, tabx.data(), kTabXLen * sizeof(float), cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.inv_corr, inv.data(), p.n * sizeof(float), cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.ant, h_ant, static_cast<size_t>(n_ant) * 3 * sizeof(double),
                                 cudaMemcpyHostToDevice, st));
   OVRO_CUDA_TRY(cudaMemcpyAsync(w.freq, h_freq, static_cast<size_t>(n_chan) * sizeof(double),
                                 cudaMemcpyHostToDevice, st));
-  OVRO_CUDA_TRY(cudaMemcpyAsync(w.band_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  if (!entries.empty())
-    OVRO_CUDA_TRY(cudaMemcpyAsync(w.entries, entries.data(), entries.size() * sizeof(GridEntry),
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.tile_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  std::vector<int> order(off.size() - 1);
+  for (size_t t = 0; t < order.size(); ++t) order[t] = static_cast<int>(t);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+  OVRO_CUDA_TRY(cudaMemcpyAsync(w.tile_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!listed.empty())
+    OVRO_CUDA_TRY(cudaMemcpyAsync(w.listed, listed.data(), listed.size() * sizeof(GridEntry),
                                   cudaMemcpyHostToDevice, st));
+  if (!idx.empty())
+    OVRO_CUDA_TRY(cudaMemcpyAsync(w.tile_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   // host->device copies from pageable memory are staged before cudaMemcpyAsync
   // returns, so the temporaries above may go out of scope
   k_twiddle_img<<<(p.g + 255) / 256, 256, 0, st>>>(w.tw, p.g);
@@ -882,7 +1054,7 @@ int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_
     OVRO_CUDA_TRY(cudaMemsetAsync(g->w.kept, 0, g->n_chan * sizeof(int), st));
     for (int ch0 = 0; ch0 < g->n_chan; ch0 += batch) {
       const int nb = g->n_chan - ch0 < batch ? g->n_chan - ch0 : batch;
-      if (int e = run_bands(p, g->w, o, d_vis, n_bl, ch0, nb, d_img, st)) return e;
+      if (int e = run_batch(p, g->w, o, d_vis, n_bl, ch0, nb, d_img, st)) return e;
     }
     return OVRO_OK;
   };
@@ -890,7 +1062,12 @@ int grid_ctx_enqueue(GridCtx* g, const int32_t* d_vis, float* d_img, int32_t* d_
   int batch = std::min(p.batch, std::max(1, tuned(key, p.batch)));
   if (tuning(st)) {
     std::vector<int> cands;
-    for (int b = p.batch; b >= 1 && cands.size() < 4; b /= 2) cands.push_back(b);
+    // whole groups of 32 channels (or the call's channels, if fewer)
+    for (int b = p.batch; cands.size() < 4; b /= 2) {
+      const int c = b >= kLanes ? b / kLanes * kLanes : b;
+      if (cands.empty() || c < cands.back()) cands.push_back(c);
+      if (c <= kLanes) break;
+    }
     if (int e = tune_pick(key, cands, all, st, &batch)) return e;
   }
   if (int e = all(batch)) return e;

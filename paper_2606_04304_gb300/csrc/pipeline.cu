@@ -271,6 +271,37 @@ int ovro_pipeline_run(ovro_pipeline* pl, const uint8_t* d_volt, ovro_candidate* 
   return e;
 }
 
+int ovro_pipeline_run_device(ovro_pipeline* pl, const uint8_t* d_volt, void* stream) {
+  using namespace ovro;
+  if (!pl || !d_volt) return OVRO_ERR_INVALID_ARG;
+  if (!pl->ws || !pl->det) return OVRO_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  unsigned long long n_dev = 0;
+  if (pl->use_graph && !tuning(st)) {
+    if (!pl->exec || pl->graph_volt != d_volt || pl->graph_traced != profiling())
+      if (int e = capture(pl, d_volt)) return e;
+    OVRO_CUDA_TRY(cudaGraphLaunch(pl->exec, st));
+    add_launches(pl->graph_kernels);
+    n_dev = pl->graph_kernels;
+  } else {
+    const unsigned long long l0 = ovro_launch_count();
+    if (int e = enqueue_device(pl, d_volt, st)) return e;
+    n_dev = ovro_launch_count() - l0;
+  }
+  pl->kernels_per_run = n_dev;
+  if (pl->xeng_mode == OVRO_XENG_TC) return ovro_correlate_status(st);   // synchronises
+  OVRO_CUDA_TRY(cudaStreamSynchronize(st));
+  return OVRO_OK;
+}
+
+int ovro_pipeline_search(ovro_pipeline* pl, ovro_search** out) {
+  if (!pl || !out) return OVRO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!pl->det) return OVRO_ERR_WORKSPACE;
+  *out = ovro::search_view(pl->det);
+  return OVRO_OK;
+}
+
 int ovro_pipeline_stats(const ovro_pipeline* pl, long long* kernels_per_run, int* graph_live) {
   if (!pl) return OVRO_ERR_INVALID_ARG;
   if (kernels_per_run) *kernels_per_run = static_cast<long long>(pl->kernels_per_run);

@@ -51,6 +51,8 @@ int detect_ctx_upload(DetectCtx* d, cudaStream_t st);
 int detect_ctx_begin(DetectCtx* d, cudaStream_t st);
 // a8-a10 for coarse channel c: d_img_block holds that channel's nfft[c] images.
 int detect_ctx_coarse(DetectCtx* d, int c, const float* d_img_block, cudaStream_t st);
+// The same, also scattering the high-passed cube z' into d_zp [n_chan][N][N].
+int detect_ctx_coarse_zp(DetectCtx* d, int c, const float* d_img_block, float* d_zp, cudaStream_t st);
 // a11-a12 (synchronises): candidates in (pixel, coarse, channel) order.
 int detect_ctx_finish(DetectCtx* d, const double* h_chan_freq_hz, ovro_candidate* h_out, int max_out, int* n_out,
                       cudaStream_t st);
@@ -62,5 +64,7 @@ int detect_ctx_candidates(DetectCtx* d, float cut, const double* h_chan_freq_hz,
                           int* n_out, cudaStream_t st);
 void detect_ctx_layout(const DetectCtx* d, uint32_t* key0, int* n_bins, long long* n_tests);
 void detect_ctx_free(DetectCtx* d);
+// A search handle over an existing context that ovro_search_destroy does not free.
+ovro_search* search_view(DetectCtx* d);
 
 }  // namespace ovro

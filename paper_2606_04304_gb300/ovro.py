@@ -40,12 +40,12 @@ class DetectParams(ctypes.Structure):
 class Candidate(ctypes.Structure):
     _fields_ = [("coarse", ctypes.c_int32), ("fine", ctypes.c_int32), ("chan", ctypes.c_int32),
                 ("row", ctypes.c_int32), ("col", ctypes.c_int32), ("width", ctypes.c_int32),
-                ("snr", ctypes.c_float), ("pad_", ctypes.c_float), ("freq_hz", ctypes.c_double),
+                ("snr", ctypes.c_float), ("score", ctypes.c_float), ("freq_hz", ctypes.c_double),
                 ("log10_p", ctypes.c_double)]
 
 
 CANDIDATE_DTYPE = np.dtype([("coarse", "<i4"), ("fine", "<i4"), ("chan", "<i4"), ("row", "<i4"),
-                            ("col", "<i4"), ("width", "<i4"), ("snr", "<f4"), ("pad_", "<f4"),
+                            ("col", "<i4"), ("width", "<i4"), ("snr", "<f4"), ("score", "<f4"),
                             ("freq_hz", "<f8"), ("log10_p", "<f8")])
 
 
@@ -73,7 +73,8 @@ def _load() -> ctypes.CDLL:
         "ovro_grid_image_ex": (I, [P, I, P, P, I, I, D, P, P, P, P, S, P]),
         "ovro_default_widths": (I, [P]),
         "ovro_detect_workspace_size": (S, [I, I, I, P]),
-        "ovro_detect": (I, [P, I, I, D, I, P, P, P, P, I, P, P, S, P]),
+        "ovro_detect": (I, [P, I, I, D, I, P, P, P, P, P, I, P, P, S, P]),
+        "ovro_scorer_detect_workspace_size": (S, [I, I, I, I]),
         "ovro_detect_stats": (I, [P, I, I, D, P, P, S, P]),
         "ovro_detect_filter": (I, [P, P, I, I, D, I, P, P, P, P, P, P, S, P]),
         "ovro_scorer_n_params": (I, []),
@@ -109,7 +110,8 @@ def _load() -> ctypes.CDLL:
         "ovro_drift_workspace_size": (S, [I, I, I, P]),
         "ovro_drift_search": (I, [P, I, I, I, D, I, P, P, P, P, P, P, P, I, P, P, S, P]),
         "ovro_spectra_slice": (I, [P, I, I, I, I, I, P, P]),
-        "ovro_probe_accumulate": (I, [P, P]),
+        "ovro_pipeline_run_device": (I, [P, P, P]),
+        "ovro_pipeline_search": (I, [P, P]),
         "ovro_autotune": (I, [I]),
         "ovro_tune_get": (I, [ctypes.c_char_p, P]),
         "ovro_tune_set": (I, [ctypes.c_char_p, I]),
@@ -141,13 +143,6 @@ def profile(enable: bool) -> None:
     _check("ovro_profile", _lib.ovro_profile(1 if enable else 0))
 
 
-def probe_accumulate(stream=None) -> float:
-    """Measured ceiling of the gridder's shared-memory accumulation, taps/s."""
-    v = ctypes.c_double(0.0)
-    _check("ovro_probe_accumulate", _lib.ovro_probe_accumulate(ctypes.byref(v), _stream(stream)))
-    return v.value * 1e9
-
-
 def profile_query(kernel: str):
     """(summed device ms, launches) of one traced kernel."""
     ms = ctypes.c_double(0.0)
@@ -156,7 +151,7 @@ def profile_query(kernel: str):
     return ms.value, n.value
 
 
-TRACED_KERNELS = ("k_upchan", "k_upchan_mr", "k_vet_line", "k_vet_fit", "k_drift", "k_scorer_fwd", "k_xeng_tc", "k_xeng_simt", "k_grid_rows", "k_fft_cols", "k_stats", "k_ztrans",
+TRACED_KERNELS = ("k_upchan", "k_upchan_mr", "k_vet_line", "k_vet_fit", "k_drift", "k_scorer_fwd", "k_xeng_tc", "k_xeng_simt", "k_grid_prep", "k_grid_tiles", "k_fft_rows", "k_fft_cols", "k_stats", "k_ztrans",
                   "k_rank", "k_walk", "k_median_sub", "k_mf", "k_nms_warp")
 
 
@@ -350,9 +345,28 @@ def detect_workspace_size(n_chan: int, image_size: int, nfft: Sequence[int]) -> 
     return _lib.ovro_detect_workspace_size(n_chan, image_size, len(nf), nf.ctypes.data_as(ctypes.c_void_p))
 
 
+class ScorerParams(ctypes.Structure):
+    _fields_ = [("d_w_bf16", ctypes.c_void_p), ("trigger_nsigma", ctypes.c_double), ("keep_prob", ctypes.c_float),
+                ("max_triggers", ctypes.c_int), ("d_ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t)]
+
+
+class DetectScorer:
+    """The learned scorer as a stage of detect(): BF16 weights (a torch bf16
+    tensor of scorer_n_params() values), the relaxed trigger threshold and
+    the keep probability."""
+
+    def __init__(self, w_bf16: torch.Tensor, trigger_nsigma: float = 5.0, keep_prob: float = 0.5,
+                 max_triggers: int = 1 << 20):
+        _cuda(w_bf16, torch.bfloat16, "w_bf16")
+        self.w_bf16, self.trigger_nsigma, self.keep_prob = w_bf16, float(trigger_nsigma), float(keep_prob)
+        self.max_triggers = int(max_triggers)
+
+
 def detect(img: torch.Tensor, cell: float, nfft: Sequence[int], freqs_hz, params: Optional[DetectParams] = None,
-           max_out: int = 1 << 20, ws: Optional[torch.Tensor] = None, stream=None) -> np.ndarray:
-    """Stage I search; returns a structured array of candidates (CANDIDATE_DTYPE)."""
+           max_out: int = 1 << 20, ws: Optional[torch.Tensor] = None, scorer: Optional[DetectScorer] = None,
+           stream=None) -> np.ndarray:
+    """Stage I search; returns a structured array of candidates (CANDIDATE_DTYPE).
+    With a scorer, its relaxed triggers are kept by the network's probability."""
     _cuda(img, torch.float32, "img")
     n_chan, n, _ = img.shape
     nf = _host(nfft, np.int32)
@@ -360,10 +374,16 @@ def detect(img: torch.Tensor, cell: float, nfft: Sequence[int], freqs_hz, params
     prm = params or detect_params()
     need = detect_workspace_size(n_chan, n, nf)
     ws = ws if ws is not None and ws.numel() >= need else workspace(need, img.device)
+    sp = None
+    if scorer is not None:
+        sws = workspace(_lib.ovro_scorer_detect_workspace_size(n_chan, n, len(nf), scorer.max_triggers), img.device)
+        sp = ScorerParams(scorer.w_bf16.data_ptr(), scorer.trigger_nsigma, scorer.keep_prob, scorer.max_triggers,
+                          sws.data_ptr(), sws.numel())
     out = np.zeros(max_out, CANDIDATE_DTYPE)
     n_out = ctypes.c_int(0)
     st = _lib.ovro_detect(_ptr(img), n_chan, n, float(cell), len(nf), nf.ctypes.data_as(ctypes.c_void_p),
                           fr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm),
+                          None if sp is None else ctypes.byref(sp),
                           out.ctypes.data_as(ctypes.c_void_p), max_out, ctypes.byref(n_out), _ptr(ws),
                           ws.numel(), _stream(stream))
     _check("ovro_detect", st)
@@ -569,8 +589,9 @@ class Pipeline:
         self._ant = _host(ant_enu_m, np.float64).reshape(-1, 3)
         if self._hz.size != self._nf.size or self._ant.shape[0] != n_ant:
             raise ValueError("nfft / coarse_hz / ant_enu_m sizes disagree")
+        self.params = params or detect_params()
         cfg = PipelineConfig(n_ant, self._nf.size, self._nf.ctypes.data, self._hz.ctypes.data, int(n_time),
-                             self._ant.ctypes.data, image_size, float(cell), xeng_mode, params or detect_params(),
+                             self._ant.ctypes.data, image_size, float(cell), xeng_mode, self.params,
                              1 if use_graph else 0)
         h = ctypes.c_void_p()
         _check("ovro_pipeline_create", _lib.ovro_pipeline_create(ctypes.byref(cfg), ctypes.byref(h)))
@@ -598,6 +619,20 @@ class Pipeline:
         _check("ovro_pipeline_run", _lib.ovro_pipeline_run(self._h, _ptr(volt), out.ctypes.data_as(ctypes.c_void_p),
                                                            max_out, ctypes.byref(n_out), _stream(stream)))
         return out[: min(n_out.value, max_out)].copy()
+
+    def run_device(self, volt: torch.Tensor, stream=None) -> None:
+        """The device part of one integration (before the threshold); read the
+        search with search() and threshold it, possibly across shards."""
+        _cuda(volt, torch.uint8, "volt")
+        if volt.numel() != self.n_coarse * self.n_time * self.n_input:
+            raise ValueError("volt must be [n_coarse][n_time][2 n_ant] uint8")
+        _check("ovro_pipeline_run_device", _lib.ovro_pipeline_run_device(self._h, _ptr(volt), _stream(stream)))
+
+    def search(self) -> "Search":
+        """The whole integration's search (a view; valid while the pipeline lives)."""
+        h = ctypes.c_void_p()
+        _check("ovro_pipeline_search", _lib.ovro_pipeline_search(self._h, ctypes.byref(h)))
+        return Search._view(h, self._nf, self.params, owner=self)
 
     def stats(self):
         k = ctypes.c_longlong(0)
@@ -664,8 +699,19 @@ class Search:
             n_chan, image_size, float(cell), self._nf.size, self._nf.ctypes.data_as(ctypes.c_void_p),
             ctypes.byref(self.params), _ptr(self.ws), self.ws.numel(), _stream(stream), ctypes.byref(h)))
         self._h = h
+        self._layout()
+
+    @classmethod
+    def _view(cls, h, nfft, params, owner):
+        s = cls.__new__(cls)
+        s._nf, s.params, s._h, s._owner = nfft, params, h, owner
+        s._layout()
+        return s
+
+    def _layout(self):
         k0, nb, nt = ctypes.c_uint32(0), ctypes.c_int(0), ctypes.c_longlong(0)
-        _check("ovro_search_layout", _lib.ovro_search_layout(h, ctypes.byref(k0), ctypes.byref(nb), ctypes.byref(nt)))
+        _check("ovro_search_layout", _lib.ovro_search_layout(self._h, ctypes.byref(k0), ctypes.byref(nb),
+                                                             ctypes.byref(nt)))
         self.key0, self.n_bins, self.n_tests = int(k0.value), int(nb.value), int(nt.value)
 
     def reset(self, stream=None):

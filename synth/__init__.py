@@ -16,6 +16,7 @@ from .workloads import (  # noqa: F401
     coarse_centre_hz,
     fine_freqs_hz,
     generate,
+    generate_parallel,
     make_config,
     pack_nibbles,
     pfb_prototype,

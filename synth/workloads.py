@@ -359,3 +359,24 @@ def make_config(name: str, **over) -> Config:
 
 
 CONFIGS = ("tiny", "full", "batched", "precision", "scorer", "scorer_train")
+
+
+def _generate_one(args):
+    cfg, c = args
+    return generate(cfg, coarse=[c])[0]
+
+
+def generate_parallel(cfg: Config, workers: Optional[int] = None) -> np.ndarray:
+    """generate(cfg) with the coarse channels drawn in parallel (spawned
+    processes; every slice comes from its own counter-based substreams, so the
+    bytes are those of generate)."""
+    import multiprocessing as mp
+    import os
+    workers = workers or min(cfg.n_coarse, os.cpu_count() or 1)
+    if workers <= 1 or cfg.n_coarse == 1:
+        return generate(cfg)
+    out = np.empty((cfg.n_coarse, cfg.n_time, cfg.n_input), dtype=np.uint8)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for c, v in enumerate(pool.imap(_generate_one, [(cfg, c) for c in range(cfg.n_coarse)])):
+            out[c] = v
+    return out

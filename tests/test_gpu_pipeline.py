@@ -172,3 +172,23 @@ def test_pipeline_with_3_5_smooth_lengths(lib):
     oref = OD.detect(img.cpu().numpy().astype(np.float64), mask, cfg.nfft)
     assert {(int(c["chan"]), int(c["row"]), int(c["col"])) for c in got} == {(c.chan, c.row, c.col) for c in oref}
     pl.close()
+
+
+def test_device_run_and_search_view_equal_run(lib, case):
+    # the device part alone, then the threshold through the pipeline's search
+    # view (the per-shard path of a multi-GPU run, here with one shard) gives
+    # the candidates of the whole run
+    from paper_2606_04304_gb300 import sharded
+    cfg, volt, pos, img, ref = case
+    pl = _pipeline(lib, cfg, pos, use_graph=True)
+    first = pl.run(volt)
+    pl.run_device(volt)
+    s = pl.search()
+    assert s.n_tests == int(OI.horizon_mask(cfg.image_size, cfg.cell).sum()) * cfg.n_chan_total
+    got = sharded.sharded_detect(s, pl.channels())
+    _same(got, ref)
+    _same(first, ref)
+    s.close()
+    again = pl.run(volt)                          # the pipeline is untouched by the view
+    _same(again, ref)
+    pl.close()

@@ -65,3 +65,31 @@ def test_gain_over_plain_detector(trained):
           f"with {fa_plain} false alarms, scorer {rec_sc} at the same false alarms")
     assert auc_sc > auc_snr + 0.15
     assert rec_sc > rec_plain
+
+
+def test_scorer_stage_of_detect(lib, trained):
+    # ovro_detect with the scorer: the relaxed 5-sigma triggers whose keep
+    # probability under the BF16-served network is >= 0.5, scored in the
+    # library; against the oracle's forward pass (FP64 at the BF16 weights) on
+    # the same triggers' cutouts
+    from oracle import scorer as S
+    s, _ = trained
+    cfg = synth.make_config("scorer_train", seed=2000)
+    volt = synth.generate(cfg)
+    pos = synth.antenna_positions(cfg)
+    freqs = synth.fine_freqs_hz(cfg.nfft)
+    cube = SC.run_pipeline(volt, cfg.nfft, cfg.n_ant, pos, freqs, cfg.image_size, cfg.cell)
+    trig = SC.candidates(cube, 5.0)
+    got = lib.detect(cube.img, cfg.cell, cfg.nfft, freqs, scorer=lib.DetectScorer(s.w_bf16, 5.0, 0.5))
+    x = SC.cutouts(cube, trig).cpu().numpy().astype(np.float64)
+    theta = s.w_bf16.to(torch.float64).cpu().numpy()
+    logit, _ = S.forward(theta, x)
+    p = 1.0 / (1.0 + np.exp(-logit))
+    key = lambda c: (int(c["chan"]), int(c["row"]), int(c["col"]))
+    want = {key(c): pk for c, pk in zip(trig, p) if pk >= 0.5}
+    have = {key(c): float(c["score"]) for c in got}
+    near = {key(c) for c, pk in zip(trig, p) if abs(pk - 0.5) < 1e-4}
+    assert set(have) - near == set(want) - near
+    for k, v in have.items():
+        assert abs(v - want.get(k, v)) < 1e-4
+    assert 0 < len(have) < len(trig)

@@ -34,3 +34,8 @@ def test_batched_mix():
     cfg = synth.make_config("batched")
     assert len(cfg.nfft) == 32 and set(cfg.nfft) <= {1024, 4096, 16384}
     assert len(cfg.tones) == 20
+
+
+def test_parallel_generation_is_identical():
+    cfg = synth.make_config("tiny")
+    assert np.array_equal(synth.generate_parallel(cfg, workers=2), synth.generate(cfg))
