@@ -970,6 +970,9 @@ int window_channels(double df, double span) {
   return w;
 }
 
+constexpr int kGatherCap = 1 << 23;     // values of the open histogram bins (exact BH step-up), at least
+constexpr int kCandCap = 1 << 21;       // candidates written by the NMS kernels, at least
+
 struct DetectPlan {
   int n, n_coarse, n_chan;
   long long npix;
@@ -981,6 +984,8 @@ struct DetectPlan {
   int max_steps = 0;
   int n_valid = 0;
   bool stats_in_smem = false;
+  int gather_cap = 0;          // values of the open histogram bins gathered at once
+  int cand_cap = 0;            // candidate records written by the NMS kernels
 };
 
 DetectPlan make_plan(int n_chan, int n, double cell, int n_coarse, const int32_t* nfft,
@@ -1009,12 +1014,15 @@ DetectPlan make_plan(int n_chan, int n, double cell, int n_coarse, const int32_t
     c0 += nfft[c];
   }
   p.stats_in_smem = (static_cast<size_t>(p.n_valid) * 4 + 8192 + 256 + 32 + 16384) <= 231000;
+  // the capacities grow with the search: a search of few spectra per channel
+  // (skewed noise images) can pass about one test in a thousand
+  const long long grow = std::min<long long>(p.n_vox / 512, 1LL << 26);
+  p.gather_cap = static_cast<int>(std::max<long long>(kGatherCap, grow));
+  p.cand_cap = static_cast<int>(std::max<long long>(kCandCap, grow));
   return p;
 }
 
 constexpr int kMaxBins = 2048;
-constexpr int kGatherCap = 1 << 23;     // values of one histogram bin (exact BH step-up)
-constexpr int kCandCap = 1 << 21;       // candidates written by the NMS kernels
 
 struct DetectWs {
   int* pix;
@@ -1051,11 +1059,11 @@ DetectWs carve_detect(void* ws, size_t bytes, const DetectPlan& p, size_t* need)
   w.snr = c.take<float>(static_cast<size_t>(p.n_vox));
   w.width = c.take<uint8_t>(static_cast<size_t>(p.n_vox));
   w.hist = c.take<unsigned long long>(kMaxBins);
-  w.vals = c.take<float>(kGatherCap);
+  w.vals = c.take<float>(p.gather_cap);
   w.vox0 = c.take<long long>(p.n_coarse);
   w.nfft = c.take<int>(p.n_coarse);
   w.ovf = c.take<int>(np);
-  w.recs = c.take<CandRec>(kCandCap);
+  w.recs = c.take<CandRec>(p.cand_cap);
   w.count = c.take<int>(4);
   w.want = c.take<uint8_t>(kMaxBins);
   *need = c.used;
@@ -1261,13 +1269,13 @@ int gather_bin(const DetectWs& w, const DetectPlan& p, uint32_t key0, int nb, in
                cudaStream_t st) {
   const int nsm = num_sms();
   OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, sizeof(int), st));
-  k_gather_bin<<<8 * nsm, 256, 0, st>>>(w.snr, p.n_vox, key0 + b, b == nb - 1 ? 1 : 0, w.vals, kGatherCap,
+  k_gather_bin<<<8 * nsm, 256, 0, st>>>(w.snr, p.n_vox, key0 + b, b == nb - 1 ? 1 : 0, w.vals, p.gather_cap,
                                         w.count);
   OVRO_LAUNCH_CHECK();
   int nv = 0;
   OVRO_CUDA_TRY(cudaMemcpyAsync(&nv, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
   OVRO_CUDA_TRY(cudaStreamSynchronize(st));
-  if (nv > kGatherCap) return OVRO_ERR_CAPACITY;
+  if (nv > p.gather_cap) return OVRO_ERR_CAPACITY;
   v.resize(nv);
   if (nv) OVRO_CUDA_TRY(cudaMemcpy(v.data(), w.vals, nv * sizeof(float), cudaMemcpyDeviceToHost));
   return OVRO_OK;
@@ -1314,13 +1322,13 @@ int bh_cut(const std::vector<unsigned long long>& hist, uint32_t key0, int nb, d
     }
   }
   std::vector<std::vector<float>> bins(nb);
-  const bool one_pass = n_open > 1 && open_total <= static_cast<unsigned long long>(kGatherCap);
+  const bool one_pass = n_open > 1 && open_total <= static_cast<unsigned long long>(p.gather_cap);
   if (one_pass) {
     std::vector<uint8_t> want(nb, 0);
     for (int b = 0; b < b1; ++b) want[b] = verdict[b] == 2;
     OVRO_CUDA_TRY(cudaMemcpyAsync(w.want, want.data(), nb, cudaMemcpyHostToDevice, st));
     OVRO_CUDA_TRY(cudaMemsetAsync(w.count, 0, sizeof(int), st));
-    k_gather_bins<<<8 * num_sms(), 256, 0, st>>>(w.snr, p.n_vox, key0, nb, w.want, w.vals, kGatherCap, w.count);
+    k_gather_bins<<<8 * num_sms(), 256, 0, st>>>(w.snr, p.n_vox, key0, nb, w.want, w.vals, p.gather_cap, w.count);
     OVRO_LAUNCH_CHECK();
     int nv = 0;
     OVRO_CUDA_TRY(cudaMemcpyAsync(&nv, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1340,7 +1348,7 @@ int bh_cut(const std::vector<unsigned long long>& hist, uint32_t key0, int nb, d
     if (verdict[b] != 2) continue;
     std::vector<float>& vals = bins[b];
     if (!one_pass) {
-      if (hist[b] > static_cast<unsigned long long>(kGatherCap)) return OVRO_ERR_CAPACITY;
+      if (hist[b] > static_cast<unsigned long long>(p.gather_cap)) return OVRO_ERR_CAPACITY;
       if (int e = gather_bin(w, p, key0, nb, b, vals, st)) return e;
     }
     if (static_cast<unsigned long long>(vals.size()) != hist[b]) return OVRO_ERR_CAPACITY;
@@ -1581,7 +1589,7 @@ int detect_ctx_candidates(DetectCtx* d, float cut, const double* h_chan_freq_hz,
   {
     OVRO_PROF("k_nms_warp", st);
     k_nms_warp<<<nms_blocks, kNmsWarps * 32, 0, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, np, cut, w.ovf,
-                                                       w.count + 1, w.recs, kCandCap);
+                                                       w.count + 1, w.recs, p.cand_cap);
     OVRO_LAUNCH_CHECK();
   }
   int cnt[2] = {0, 0};
@@ -1594,14 +1602,14 @@ int detect_ctx_candidates(DetectCtx* d, float cut, const double* h_chan_freq_hz,
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_nms_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(big_sm)));
     k_nms_big<<<cnt[0], 1024, big_sm, st>>>(w.snr, w.width, w.vox0, w.nfft, p.n_coarse, w.ovf, w.count + 1, p2max,
-                                            cut, w.recs, kCandCap);
+                                            cut, w.recs, p.cand_cap);
     OVRO_LAUNCH_CHECK();
     OVRO_CUDA_TRY(cudaMemcpyAsync(cnt, w.count + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     OVRO_CUDA_TRY(cudaStreamSynchronize(st));
   }
   const int total = cnt[1];
   *n_out = total;
-  const int nw = std::min(total, kCandCap);
+  const int nw = std::min(total, p.cand_cap);
   if (nw > 0 && max_out > 0) {
     std::vector<CandRec>& recs = d->recs;
     if (recs.size() < static_cast<size_t>(nw)) recs.resize(nw);
@@ -1634,7 +1642,7 @@ int detect_ctx_candidates(DetectCtx* d, float cut, const double* h_chan_freq_hz,
     }
   }
   if (total > max_out) return OVRO_ERR_CAPACITY;
-  return total > kCandCap ? OVRO_ERR_CAPACITY : OVRO_OK;
+  return total > p.cand_cap ? OVRO_ERR_CAPACITY : OVRO_OK;
 }
 
 int detect_ctx_bin_values(DetectCtx* d, int b, std::vector<float>& v, cudaStream_t st) {
