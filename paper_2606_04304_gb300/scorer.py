@@ -51,6 +51,29 @@ def run_pipeline(volt: np.ndarray, nfft: Sequence[int], n_ant: int, pos: np.ndar
     return Cube(img, zp, list(nfft), freqs, cell)
 
 
+def run_pipeline_streamed(volt: np.ndarray, nfft: Sequence[int], n_ant: int, pos: np.ndarray, freqs: np.ndarray,
+                          image_size: int, cell: float) -> Cube:
+    """As run_pipeline, one coarse channel at a time through one visibility
+    buffer (the whole integration's visibilities need not fit on the device)."""
+    n_coarse, n_time, n_input = volt.shape
+    n_chan = int(sum(nfft))
+    img = torch.empty((n_chan, image_size, image_size), dtype=torch.float32, device="cuda")
+    vis = torch.empty((max(nfft), ovro.n_baselines(n_ant), 4, 2), dtype=torch.int32, device="cuda")
+    c0 = 0
+    for c, n in enumerate(nfft):
+        d = torch.from_numpy(np.ascontiguousarray(volt[c:c + 1])).cuda()
+        k = n_time // n
+        q, _ = ovro.upchan(d, [n])
+        ovro.correlate(q, n_ant, n, k, ovro.XENG_TC, out=vis[:n])
+        ovro.grid_image(vis[:n], pos, freqs[c0:c0 + n], image_size, cell, out=img[c0:c0 + n])
+        c0 += n
+    del vis
+    bounds = np.concatenate([[0], np.cumsum(nfft)])
+    stats = torch.cat([ovro.detect_stats(img[bounds[c]:bounds[c + 1]], cell) for c in range(len(nfft))])
+    zp, _, _ = ovro.detect_filter(img, stats, cell, nfft, want_zp=True)
+    return Cube(img, zp, list(nfft), freqs, cell)
+
+
 def label(cands: np.ndarray, tones, nfft: Sequence[int], n_time: int, f_coarse: float = 24000.0,
           pix_tol: int = 1, chan_tol: int = 2) -> np.ndarray:
     """1 where a candidate is an injected sky tone: same coarse channel, within
