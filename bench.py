@@ -663,12 +663,26 @@ def run_scorer_eval(args):
     n_tones = sum(len(t[0].tones) for t in test)
     plain = snr >= 10.0
     fa_plain = int((plain & (yt < 0.5)).sum())
-    neg = np.sort(p[yt < 0.5])[::-1]
-    pstar = neg[fa_plain] if fa_plain < len(neg) else -1.0
-    keep_sc = p > pstar
-    # the scorer as a stage of ovro_detect on one held-out cube, timed against the plain call
+
+    def at_false_alarms(rank, fa):
+        neg = np.sort(rank[yt < 0.5])[::-1]
+        thr = neg[fa] if fa < len(neg) else -np.inf
+        keep = rank > thr
+        return {"tones_found": tones_found(keep), "false_alarms": int((keep & (yt < 0.5)).sum())}
+
+    budgets = {str(fa): {"snr": at_false_alarms(snr, fa), "scorer": at_false_alarms(p, fa)}
+               for fa in (10, 100, 1000, 10000, fa_plain)}
+    # the scorer as a stage of ovro_detect on one held-out cube, its keep
+    # probability set on the training cubes alone (the score above which they
+    # hold as many false alarms per cube as the plain 10-sigma detector)
+    p_train = np.concatenate([SC.score(sc, t[0]) for t in train])
+    y_train = np.concatenate([t[1] for t in train])
+    fa_per_cube = fa_plain / len(test)
+    neg_tr = np.sort(p_train[y_train < 0.5])[::-1]
+    k_tr = int(round(fa_per_cube * len(train)))
+    keep_prob = float(neg_tr[k_tr]) if k_tr < len(neg_tr) else 0.0
     cfg, cb, _, _, _ = test[0]
-    ds = ovro.DetectScorer(sc.w_bf16, trig_sigma, 0.5)
+    ds = ovro.DetectScorer(sc.w_bf16, trig_sigma, keep_prob)
     fixed = ovro.detect_params(mode=ovro.DETECT_FIXED, nsigma=10.0)
 
     def timed(fn):
@@ -680,8 +694,14 @@ def run_scorer_eval(args):
         return out, time.perf_counter() - a
 
     scored, t_det_sc = timed(lambda: ovro.detect(cb.img, cb.cell, cb.nfft, cb.freqs, scorer=ds, max_out=1 << 24))
-    _, t_det_plain = timed(lambda: ovro.detect(cb.img, cb.cell, cb.nfft, cb.freqs, params=fixed))
-    ys = SC.label(scored, cfg.tones, cfg.nfft, cfg.n_time)
+    plain_c, t_det_plain = timed(lambda: ovro.detect(cb.img, cb.cell, cb.nfft, cb.freqs, params=fixed))
+
+    def judged(cands):
+        y = SC.label(cands, cfg.tones, cfg.nfft, cfg.n_time)
+        found = sum(int((SC.label(cands, [tn], cfg.nfft, cfg.n_time) > 0.5).any()) for tn in cfg.tones)
+        return {"candidates": int(len(cands)), "false_alarms": int((y < 0.5).sum()), "tones_found": found,
+                "tones": len(cfg.tones)}
+
     line = {
         "workload": "scorer: 352 antennas, 8 coarse x 8192-pt (K = 29), 256^2, 64 drifting tones (SNR 4-20, "
                     "0-1 Hz/s), 16 horizon carriers, 16 broadband bursts per cube; 3 training + 2 held-out cubes",
@@ -689,9 +709,10 @@ def run_scorer_eval(args):
         "test_triggers": int(len(snr)), "test_positives": int((yt > 0.5).sum()), "tones_held_out": n_tones,
         "auc_snr": SC.roc_auc(snr, yt), "auc_scorer": SC.roc_auc(p, yt),
         "plain_10sigma": {"tones_found": tones_found(plain), "false_alarms": fa_plain},
-        "scorer_same_false_alarms": {"tones_found": tones_found(keep_sc), "false_alarms": int((keep_sc & (yt < 0.5)).sum())},
-        "detect_with_scorer_p0.5_cube0": {"candidates": int(len(scored)), "true": int((ys > 0.5).sum()),
-                                          "s": t_det_sc, "plain_10sigma_s": t_det_plain},
+        "tones_found_at_false_alarm_budgets": budgets,
+        "detect_stage_cube200": {"keep_prob_from_training": keep_prob, "scored": judged(scored),
+                                 "plain_10sigma": judged(plain_c), "scored_s": t_det_sc,
+                                 "plain_s": t_det_plain},
         "train": {"epochs": epochs, "batch": batch, "s": t_train,
                   "cutouts_per_s": epochs * int(x.shape[0]) / t_train, "loss": [round(v, 5) for v in sc.losses]},
         "score_cutouts_per_s": len(snr) / t_score, "cube_pipeline_s": t_cubes,

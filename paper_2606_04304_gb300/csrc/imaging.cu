@@ -195,7 +195,7 @@ __host__ __device__ constexpr int band_pitch(int g) { return (g + g / 16) + ((7 
 // baseline's uv position moves by far less than a cell, so the lanes' centre
 // cells agree (or differ by one) and their table reads hit the same words.
 // No two warps write the same (cell, channel): there are no atomics.
-constexpr int kTileV = 4, kTileU = 8;          // cells per warp tile (rows, columns)
+constexpr int kTileV = 4, kTileU = 4;          // cells per warp tile (rows, columns)
 constexpr int kLanes = 32;                     // channels per warp
 
 // Tiles cover the rows G/2 .. G-1 (v >= 0) of the grid's Hermitian part only
@@ -257,13 +257,19 @@ k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* _
   const float2* gc = (CAL && opt.gains != nullptr) ? opt.gains + chan * opt.n_input : nullptr;
   PrepRec* out = prep + (static_cast<long long>(group) * n_listed) * kLanes + lane;
   int n_kept = 0;
-  // two baselines ahead: their entries and visibility loads are in flight
-  GridEntry en = listed[i0];
-  int2 xx = __ldg(vis2 + static_cast<long long>(en.bl) * 4), yy = __ldg(vis2 + static_cast<long long>(en.bl) * 4 + 3);
-  GridEntry e1 = i0 + 1 < i1 ? listed[i0 + 1] : en;
-  for (int i = i0; i < i1; ++i) {
-    const int2 x1 = __ldg(vis2 + static_cast<long long>(e1.bl) * 4), y1 = __ldg(vis2 + static_cast<long long>(e1.bl) * 4 + 3);
-    const GridEntry e2 = i + 2 < i1 ? listed[i + 2] : e1;
+  // every visibility read of the warp's baselines is issued before any is used
+  int2 xx[kPrepPerWarp], yy[kPrepPerWarp];
+#pragma unroll
+  for (int j = 0; j < kPrepPerWarp; ++j) {
+    const int bl = i0 + j < i1 ? __ldg(&listed[i0 + j].bl) : 0;
+    xx[j] = __ldg(vis2 + static_cast<long long>(bl) * 4);
+    yy[j] = __ldg(vis2 + static_cast<long long>(bl) * 4 + 3);
+  }
+#pragma unroll
+  for (int j = 0; j < kPrepPerWarp; ++j) {
+    const int i = i0 + j;
+    if (i >= i1) break;
+    const GridEntry en = listed[i];
     int pu, pv;
     if (!fast_rint_prod32(en.dxh, en.dxl, s, &pu)) {
       const long long pl = __double2ll_rn(__dmul_rn(base[en.cross].dx, s.s));
@@ -288,15 +294,15 @@ k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* _
     if (keep) {
       float vr, vi;
       if (!CAL || gc == nullptr) {
-        vr = 0.25f * static_cast<float>(xx.x + yy.x);
-        vi = -0.25f * static_cast<float>(xx.y + yy.y);
+        vr = 0.25f * static_cast<float>(xx[j].x + yy[j].x);
+        vi = -0.25f * static_cast<float>(xx[j].y + yy[j].y);
       } else {
         const int a = en.a, b = en.bf & 0xffff;
         float pr = 0.f, pi = 0.f;
 #pragma unroll
         for (int pol = 0; pol < 2; ++pol) {
           const float2 ca = __ldg(gc + 2 * a + pol), cbv = __ldg(gc + 2 * b + pol);
-          const int2 q = pol ? yy : xx;
+          const int2 q = pol ? yy[j] : xx[j];
           const float qr = static_cast<float>(q.x), qi = static_cast<float>(q.y);
           const float gr = ca.x * cbv.x + ca.y * cbv.y, gi = ca.y * cbv.x - ca.x * cbv.y;
           pr += gr * qr - gi * qi;
@@ -310,10 +316,6 @@ k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* _
     }
     reinterpret_cast<int4*>(out)[static_cast<long long>(i) * kLanes] =
         make_int4(r.pu, r.pv, __float_as_int(r.vr), __float_as_int(r.vi));
-    en = e1;
-    e1 = e2;
-    xx = x1;
-    yy = y1;
   }
   if (active && n_kept) atomicAdd(kept + chan, n_kept);
 }
@@ -332,7 +334,7 @@ k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* _
 // its accumulators; list entries are read three records ahead, records two.
 // The tile is written with the (-1)^(row + col) centring sign as two real
 // planes, grid [batch][2][G/2][G] (row j - G/2).
-constexpr int kGridWarps = 16;
+constexpr int kGridWarps = 32;
 constexpr size_t kTileSmem = static_cast<size_t>(kTabXLen) * sizeof(float);
 
 template <int LOG2G>
@@ -719,7 +721,7 @@ struct ImgWs {
 // call.  Over a coarse channel a footprint moves by at most a cell, so a
 // baseline touches 6 tiles of 4 x 8 (a footprint straddling row G/2 up to 6
 // more through its mirror; at most 16 when its centre moves by a few cells).
-constexpr int kEntriesPerBaseline = 16;
+constexpr int kEntriesPerBaseline = 24;
 long long entry_capacity(const ImgPlan& p) { return std::max<long long>(1, p.n_cross * kEntriesPerBaseline); }
 
 ImgWs carve_img(void* ws, size_t bytes, const ImgPlan& p, int n_ant, int n_chan, size_t* need) {
