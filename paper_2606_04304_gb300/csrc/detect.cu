@@ -389,24 +389,28 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restric
 constexpr int kWalkThreads = 64;
 constexpr int kWalkQ = 1;        // 16-byte step words per walk iteration
 
+// Bitset helpers; bit b of a thread's set is word b / 32 at bits[(b / 32) * T]
+// (the words of the threads of a CTA interleave).
+template <int T>
 __device__ __forceinline__ int next_set(const uint32_t* bits, int p, int nwords) {
   int w = p >> 5;
   if (w >= nwords) return -1;
-  uint32_t word = bits[w * kWalkThreads] & (0xffffffffu << (p & 31));
+  uint32_t word = bits[w * T] & (0xffffffffu << (p & 31));
   while (word == 0) {
     if (++w >= nwords) return -1;
-    word = bits[w * kWalkThreads];
+    word = bits[w * T];
   }
   return (w << 5) + __ffs(word) - 1;
 }
 
+template <int T>
 __device__ __forceinline__ int prev_set(const uint32_t* bits, int p) {
   if (p < 0) return -1;
   int w = p >> 5;
-  uint32_t word = bits[w * kWalkThreads] & (0xffffffffu >> (31 - (p & 31)));
+  uint32_t word = bits[w * T] & (0xffffffffu >> (31 - (p & 31)));
   while (word == 0) {
     if (--w < 0) return -1;
-    word = bits[w * kWalkThreads];
+    word = bits[w * T];
   }
   return (w << 5) + 31 - __clz(word);
 }
@@ -427,36 +431,46 @@ __device__ __forceinline__ bool walk_step(uint32_t* bits, int nwords, uint32_t w
     if (rout < cur) {
       --lt;
     } else if (rout == cur) {
-      const int nx = next_set(bits, rout, nwords);
+      const int nx = next_set<kWalkThreads>(bits, rout, nwords);
       if (nx >= 0) cur = nx;
-      else { cur = prev_set(bits, rout); --lt; }
+      else { cur = prev_set<kWalkThreads>(bits, rout); --lt; }
     }
   }
   if (size == 0) { cur = -1; lt = 0; return true; }
   const int target = (size - 1) >> 1;
-  while (lt < target && cur >= 0) { cur = next_set(bits, cur + 1, nwords); ++lt; }
-  while (lt > target && cur >= 0) { cur = prev_set(bits, cur - 1); --lt; }
+  while (lt < target && cur >= 0) { cur = next_set<kWalkThreads>(bits, cur + 1, nwords); ++lt; }
+  while (lt > target && cur >= 0) { cur = prev_set<kWalkThreads>(bits, cur - 1); --lt; }
   return cur >= 0;
 }
 
-// One thread per pixel walks its step stream (written by k_rank) and
-// overwrites each consumed step word with the window's median ranks
-// (lower | upper << 16; equal for odd windows).  The loop touches only the
-// bitset in shared memory and the thread's own stream, read two chunks ahead;
-// k_median_sub then applies the medians with all threads.
+// Median ranks of output channel k of pixel p: lower | upper << 16 (equal for
+// odd windows), in med [pixel][nc].
+__device__ __forceinline__ void put_med(uint32_t* med, int p, int nc, int k, uint32_t v) {
+  med[static_cast<long long>(p) * nc + k] = v;
+}
+
+// One thread per pixel walks its step stream (written by k_rank) over a rank
+// bitset and writes each window's median ranks to med.  The loop touches only
+// the bitset in shared memory and the thread's own stream, read two chunks
+// ahead; k_median_sub then applies the medians with all threads.  With a
+// pixel list (the band walk's failures) thread i walks list[i], i < *n_list.
 __global__ void __launch_bounds__(kWalkThreads)
-k_walk(uint32_t* __restrict__ steps, int n_valid, int nc, int h) {
+k_walk(const uint32_t* __restrict__ steps, int n_valid, int nc, int h, uint32_t* __restrict__ med,
+       const int* __restrict__ list, const int* __restrict__ n_list) {
   extern __shared__ uint32_t bits_all[];
   const int t = threadIdx.x;
-  const int p = blockIdx.x * kWalkThreads + t;
+  int p = blockIdx.x * kWalkThreads + t;
+  if (list) {
+    if (p >= *n_list) return;                            // no barrier follows
+    p = list[p];
+  }
   const int nwords = (nc + 31) >> 5;
   uint32_t* bits = bits_all + t;                         // word w at bits[w * kWalkThreads]
   for (int w = 0; w < nwords; ++w) bits[w * kWalkThreads] = 0u;
   if (p >= n_valid) return;
   const int H = (h + 3) & ~3;
   const int n_total = H + ((nc + 3) & ~3);               // stream words, a multiple of 4
-  uint32_t* st = steps + static_cast<long long>(p) * walk_stride(nc, h);
-  const uint4* st4 = reinterpret_cast<const uint4*>(st);
+  const uint4* st4 = reinterpret_cast<const uint4*>(steps + static_cast<long long>(p) * walk_stride(nc, h));
   int size = 0, cur = -1, lt = 0;
   // the stream is read kWalkQ 16-byte words (4 kWalkQ steps) per iteration,
   // two iterations ahead of the walk
@@ -484,17 +498,15 @@ k_walk(uint32_t* __restrict__ steps, int n_valid, int nc, int h) {
         for (int q = 0; q < 4; ++q)
           if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
       } else {
-        uint32_t r[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          r[q] = 0u;
-          if (i0 - H + q >= nc) continue;
+          const int k = i0 - H + q;
+          if (k >= nc) continue;
           if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
-          const int upper = (size & 1) ? cur : next_set(bits, cur + 1, nwords);
+          const int upper = (size & 1) ? cur : next_set<kWalkThreads>(bits, cur + 1, nwords);
           if (upper < 0) { atomicExch(&g_detect_status, 3); return; }
-          r[q] = static_cast<uint32_t>(cur) | (static_cast<uint32_t>(upper) << 16);
+          put_med(med, p, nc, k, static_cast<uint32_t>(cur) | (static_cast<uint32_t>(upper) << 16));
         }
-        reinterpret_cast<uint4*>(st)[c] = make_uint4(r[0], r[1], r[2], r[3]);
       }
     }
 #pragma unroll
@@ -505,22 +517,108 @@ k_walk(uint32_t* __restrict__ steps, int n_valid, int nc, int h) {
   }
 }
 
-// z' = z - (v[lower] + v[upper]) / 2 for every voxel, v the pixel's sorted
-// values and the ranks those k_walk left in the step stream.
-__global__ void k_median_sub(float* __restrict__ zbuf, const float* __restrict__ sv,
-                             const uint32_t* __restrict__ steps, int n_valid, int nc, int h) {
+// The same walk over a band of kBandWords * 32 ranks starting at r_lo (ranks
+// below and above the band are only counted), for coarse channels longer than
+// the band: a window's median of a standardised spectrum stays near the middle
+// rank, so the band holds it for nearly every pixel and the per-pixel state is
+// a quarter of the full bitset's at 8192 channels (four times the walks per
+// SM).  A pixel whose median leaves the band stops and is listed for the full
+// walk (k_walk with the list), which rewrites all its medians.
+constexpr int kBandWords = 64;
+constexpr int kBandThreads = 128;
+
+__global__ void __launch_bounds__(kBandThreads)
+k_walk_band(const uint32_t* __restrict__ steps, int n_valid, int nc, int h, int r_lo, uint32_t* __restrict__ med,
+            int* __restrict__ fail, int* __restrict__ n_fail) {
+  extern __shared__ uint32_t bits_all[];
+  constexpr int T = kBandThreads, NW = kBandWords, B = NW * 32;
+  const int t = threadIdx.x;
+  const int p = blockIdx.x * T + t;
+  uint32_t* bits = bits_all + t;
+  for (int w = 0; w < NW; ++w) bits[w * T] = 0u;
+  if (p >= n_valid) return;
   const int H = (h + 3) & ~3;
-  const int S = walk_stride(nc, h);                      // a multiple of 4, as is H
+  const int n4 = (H + ((nc + 3) & ~3)) >> 2;
+  const uint4* st4 = reinterpret_cast<const uint4*>(steps + static_cast<long long>(p) * walk_stride(nc, h));
+  int n_below = 0, n_above = 0, n_band = 0, cur = -1, lt = 0;   // lt: band ranks below cur
+  auto give_up = [&]() {
+    const int slot = atomicAdd(n_fail, 1);
+    if (slot < n_valid) fail[slot] = p;
+  };
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  uint4 a = n4 > 0 ? st4[0] : zero4, b = n4 > 1 ? st4[1] : zero4;
+  for (int c = 0; c < n4; ++c) {
+    const uint4 nx = c + 2 < n4 ? st4[c + 2] : zero4;
+    const uint32_t sw[4] = {a.x, a.y, a.z, a.w};
+    const int i0 = c << 2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = i0 - H + q;                            // output channel (< 0: building)
+      if (k >= nc) continue;
+      const int rin = static_cast<int>(sw[q] & 0xffffu), rout = static_cast<int>(sw[q] >> 16);
+      if (rin != 0xffff) {
+        const int r = rin - r_lo;
+        if (r < 0) {
+          ++n_below;
+        } else if (r >= B) {
+          ++n_above;
+        } else {
+          bits[(r >> 5) * T] |= 1u << (r & 31);
+          ++n_band;
+          if (cur < 0) { cur = r; lt = 0; }
+          else if (r < cur) ++lt;
+        }
+      }
+      if (rout != 0xffff) {
+        const int r = rout - r_lo;
+        if (r < 0) {
+          --n_below;
+        } else if (r >= B) {
+          --n_above;
+        } else {
+          bits[(r >> 5) * T] &= ~(1u << (r & 31));
+          --n_band;
+          if (r < cur) {
+            --lt;
+          } else if (r == cur) {
+            const int nxs = next_set<T>(bits, r, NW);
+            if (nxs >= 0) cur = nxs;
+            else { cur = prev_set<T>(bits, r); --lt; }
+          }
+        }
+      }
+      if (n_band == 0) { cur = -1; lt = 0; }
+      if (k < 0) continue;
+      // the lower median is element (size - 1) / 2 of the window; in band
+      // order it is element tb
+      const int size = n_below + n_band + n_above;
+      const int tb = ((size - 1) >> 1) - n_below;
+      const bool even = (size & 1) == 0;
+      if (tb < 0 || tb + (even ? 1 : 0) >= n_band) { give_up(); return; }
+      while (lt < tb) { cur = next_set<T>(bits, cur + 1, NW); ++lt; }
+      while (lt > tb) { cur = prev_set<T>(bits, cur - 1); --lt; }
+      const int upper = even ? next_set<T>(bits, cur + 1, NW) : cur;
+      put_med(med, p, nc, k, static_cast<uint32_t>(cur + r_lo) | (static_cast<uint32_t>(upper + r_lo) << 16));
+    }
+    a = b;
+    b = nx;
+  }
+}
+
+// z' = z - (v[lower] + v[upper]) / 2 for every voxel, v the pixel's sorted
+// values and med the median ranks the walk left.
+__global__ void k_median_sub(float* __restrict__ zbuf, const float* __restrict__ sv,
+                             const uint32_t* __restrict__ med, int n_valid, int nc) {
   if ((nc & 3) == 0) {
     // four channels per thread: 16-byte reads of z and of the rank words
     const int nq = nc >> 2;
     const long long n = static_cast<long long>(n_valid) * nq;
     for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < n;
          v += static_cast<long long>(gridDim.x) * blockDim.x) {
-      const int p = static_cast<int>(v / nq), q = static_cast<int>(v - static_cast<long long>(p) * nq);
-      const uint4 r = __ldg(reinterpret_cast<const uint4*>(steps + static_cast<long long>(p) * S + H) + q);
+      const int p = static_cast<int>(v / nq);
+      const uint4 r = __ldg(reinterpret_cast<const uint4*>(med) + v);
       const float* svp = sv + static_cast<long long>(p) * nc;
-      float4* zq = reinterpret_cast<float4*>(zbuf + static_cast<long long>(p) * nc) + q;
+      float4* zq = reinterpret_cast<float4*>(zbuf) + v;
       float4 x = *zq;
       x.x -= 0.5f * (__ldg(svp + (r.x & 0xffffu)) + __ldg(svp + (r.x >> 16)));
       x.y -= 0.5f * (__ldg(svp + (r.y & 0xffffu)) + __ldg(svp + (r.y >> 16)));
@@ -533,11 +631,11 @@ __global__ void k_median_sub(float* __restrict__ zbuf, const float* __restrict__
   const long long n = static_cast<long long>(n_valid) * nc;
   for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < n;
        v += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int p = static_cast<int>(v / nc), k = static_cast<int>(v - static_cast<long long>(p) * nc);
-    const uint32_t r = __ldg(steps + static_cast<long long>(p) * S + H + k);
+    const int p = static_cast<int>(v / nc);
+    const uint32_t r = __ldg(med + v);
     const float* svp = sv + static_cast<long long>(p) * nc;
-    const float med = 0.5f * (__ldg(svp + (r & 0xffffu)) + __ldg(svp + (r >> 16)));
-    zbuf[v] -= med;
+    const float m = 0.5f * (__ldg(svp + (r & 0xffffu)) + __ldg(svp + (r >> 16)));
+    zbuf[v] -= m;
   }
 }
 
@@ -1031,6 +1129,8 @@ struct DetectWs {
   float* zbuf;
   float* sv;
   uint32_t* steps;
+  uint32_t* med;         // [pixel][channel] median ranks of the current coarse block
+  int* fail;             // pixels whose band walk gave up
   float* snr;
   uint8_t* width;
   unsigned long long* hist;
@@ -1039,7 +1139,7 @@ struct DetectWs {
   int* nfft;
   int* ovf;
   CandRec* recs;
-  int* count;            // [0] gathered values, [1] overflow pairs, [2] candidates
+  int* count;            // [0] gathered values, [1] overflow pairs, [2] candidates, [3] band-walk failures
   uint8_t* want;         // [kMaxBins] bins gathered in one pass
 };
 
@@ -1056,6 +1156,8 @@ DetectWs carve_detect(void* ws, size_t bytes, const DetectPlan& p, size_t* need)
   w.zbuf = c.take<float>(blk);
   w.sv = c.take<float>(blk);
   w.steps = c.take<uint32_t>(static_cast<size_t>(p.n_valid) * p.max_steps);
+  w.med = c.take<uint32_t>(blk);
+  w.fail = c.take<int>(p.n_valid > 0 ? p.n_valid : 1);
   w.snr = c.take<float>(static_cast<size_t>(p.n_vox));
   w.width = c.take<uint8_t>(static_cast<size_t>(p.n_vox));
   w.hist = c.take<unsigned long long>(kMaxBins);
@@ -1137,16 +1239,28 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
     if (int e = rank(per_sm)) return e;
   }
   {
+    // the band walk for coarse channels longer than its band, the full walk
+    // for the pixels it gives up on (or for every pixel of a short channel)
+    const int band = kBandWords * 32;
+    const bool use_band = nc > band;
+    if (use_band) {
+      const size_t sm = static_cast<size_t>(kBandWords) * kBandThreads * 4;
+      OVRO_CUDA_TRY(cudaMemsetAsync(w.count + 3, 0, sizeof(int), st));
+      OVRO_PROF("k_walk", st);
+      k_walk_band<<<(p.n_valid + kBandThreads - 1) / kBandThreads, kBandThreads, sm, st>>>(
+          w.steps, p.n_valid, nc, p.half[c], nc / 2 - band / 2, w.med, w.fail, w.count + 3);
+      OVRO_LAUNCH_CHECK();
+    }
     const size_t sm = static_cast<size_t>((nc + 31) / 32) * kWalkThreads * 4;
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
     {
       OVRO_PROF("k_walk", st);
-      k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(w.steps, p.n_valid, nc,
-                                                                                   p.half[c]);
+      k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(
+          w.steps, p.n_valid, nc, p.half[c], w.med, use_band ? w.fail : nullptr, use_band ? w.count + 3 : nullptr);
       OVRO_LAUNCH_CHECK();
     }
     OVRO_PROF("k_median_sub", st);
-    k_median_sub<<<8 * nsm, 256, 0, st>>>(w.zbuf, w.sv, w.steps, p.n_valid, nc, p.half[c]);
+    k_median_sub<<<8 * nsm, 256, 0, st>>>(w.zbuf, w.sv, w.med, p.n_valid, nc);
     OVRO_LAUNCH_CHECK();
   }
   if (d_zp_out) {

@@ -98,6 +98,23 @@ def test_filter_long_window_c2_shape(lib):
     _filter_vs_oracle(lib, cube, cell, [8192])
 
 
+@pytest.mark.parametrize("n_chan,trend_pixels", [(8192, [(8, 8), (5, 9), (10, 6)]), (8192, "all"), (16384, [(7, 7)])])
+def test_filter_band_walk_and_its_fallback(lib, n_chan, trend_pixels):
+    # channels beyond the band walk's 2048 ranks: most pixels keep their window
+    # medians near the middle rank (band walk); pixels with a steep trend along
+    # frequency sweep their medians across every rank and are walked again in
+    # full; every pixel against the oracle
+    g = np.random.default_rng(n_chan)
+    n, cell = 16, 0.3
+    cube = _cube(g, n_chan, n, tones=[(n_chan // 2, 8, 8, 12.0)])
+    ramp = np.linspace(-40.0, 40.0, n_chan, dtype=np.float32)
+    mask = OI.horizon_mask(n, cell)
+    pix = list(zip(*np.nonzero(mask))) if trend_pixels == "all" else trend_pixels
+    for r, c in pix:
+        cube[:, r, c] += ramp
+    _filter_vs_oracle(lib, cube, cell, [n_chan])
+
+
 def test_detect_bh_and_fixed(lib):
     g = np.random.default_rng(5)
     nfft = [256, 256]
