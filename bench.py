@@ -187,8 +187,9 @@ def roofline_models(cfg, n_kept_vis, peaks):
         "k_stats": ("hbm", cube * 4, "B", cube),
         # standardise + transpose: read the in-horizon pixels, write z
         "k_ztrans": ("hbm", vox * 8, "B", cube),
-        # sort: read z, write sorted values and the step stream
-        "k_rank": ("hbm", vox * 12, "B", cube),
+        # band ranks: read z, write the step stream and the band's sorted
+        # values (2048 of the 8192 channels: 1 B per voxel)
+        "k_rank": ("hbm", vox * 9, "B", cube),
         # walk: read the step stream, write the median ranks over it
         "k_walk": ("hbm", vox * 8, "B", cube),
         # z' = z - median: read ranks and z, write z' (sorted-value gathers hit L1/L2)

@@ -293,320 +293,508 @@ k_ztrans(const float* __restrict__ img, const int* __restrict__ pix, int n_valid
 __host__ __device__ __forceinline__ int walk_stride(int nc, int h) {
   return (nc + ((h + 3) & ~3) + 3) & ~3;
 }
-// Stable LSD radix sort of one pixel spectrum per CTA iteration.
+
+// Stream codes: a rank word of 0xffff is no element; in a band stream
+// (band-relative ranks) 0xfffe is an element below the band and 0xfffd one
+// above it.
+constexpr uint32_t kRankNone = 0xffffu, kRankBelow = 0xfffeu, kRankAbove = 0xfffdu;
+
+// Stable LSD radix sort of m keys with 16-bit payloads in shared memory by the
+// whole CTA: four passes of 8 bits; each warp ranks a contiguous segment
+// (in-warp ranks by an 8-ballot multisplit, per-warp digit histograms at a
+// padded pitch, so an exclusive scan in digit-major order gives every
+// (digit, warp) its stable output offset).  The sorted keys end in ks / is.
+__device__ void lsd_sort(uint32_t* ks, uint16_t* is, uint32_t* kd, uint16_t* id, int m, uint32_t* hist,
+                         uint32_t* tot) {
+  const int W = blockDim.x >> 5;
+  const int HP = W + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = ((m + W - 1) / W + 31) / 32 * 32;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int sh = 8 * pass;
+    for (int i = threadIdx.x; i < 256 * HP; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int i = lane; i < seg; i += 32) {
+      const int k = warp * seg + i;
+      if (k < m) atomicAdd(&hist[((ks[k] >> sh) & 255u) * HP + warp], 1u);
+    }
+    __syncthreads();
+    block_exclusive_scan(hist, 256 * HP, tot);
+    for (int b = 0; b < seg; b += 32) {
+      const int k = warp * seg + b + lane;
+      const bool valid = k < m;
+      const uint32_t key = valid ? ks[k] : 0u;
+      const uint32_t d = (key >> sh) & 255u;
+      // lanes holding the same digit: one ballot per digit bit
+      unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int bit = 0; bit < 8; ++bit) {
+        const bool x = (d >> bit) & 1u;
+        const unsigned bb = __ballot_sync(0xffffffffu, x);
+        peers &= x ? bb : ~bb;
+      }
+      if (valid) {
+        const uint32_t pos = hist[d * HP + warp] + __popc(peers & lt_mask);
+        kd[pos] = key;
+        id[pos] = is[k];
+      }
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) hist[d * HP + warp] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t* t1 = ks; ks = kd; kd = t1;
+    uint16_t* t2 = is; is = id; id = t2;
+  }
+}
+
+// The step stream from per-channel ranks rk (shared memory): step k inserts
+// channel k + h and removes channel k - h - 1, stored at index k + H (H = h
+// rounded up to 4) as (insert rank, remove rank); indices below H hold the
+// insert-only steps that build the first window.  16-byte coalesced stores.
+__device__ void write_stream(const uint16_t* rk, int nc, int h, uint32_t* sp) {
+  const int H = (h + 3) & ~3;
+  const int S = walk_stride(nc, h);
+  for (int q = threadIdx.x; q < S / 4; q += blockDim.x) {
+    uint32_t wv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * q + u;
+      const int cin = i - H + h, cout = i - H - h - 1;
+      const uint32_t rin = (cin >= 0 && cin < nc) ? rk[cin] : kRankNone;
+      const uint32_t rout = (cout >= 0 && i - H < nc) ? rk[cout] : kRankNone;
+      wv[u] = rin | (rout << 16);
+    }
+    reinterpret_cast<uint4*>(sp)[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+  }
+}
+
+// Full ranks of one pixel spectrum per CTA iteration: the sorted values
+// (sv [pixel][nc]) and the step stream of absolute ranks.  With a pixel list
+// (the band walk's failures) iteration i ranks list[i], i < *n_list.
 __global__ void __launch_bounds__(1024)
 k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restrict__ sv,
-       uint32_t* __restrict__ steps) {
+       uint32_t* __restrict__ steps, const int* __restrict__ list, const int* __restrict__ n_list) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = blockDim.x >> 5;
-  const int HP = W + 1;                                          // histogram pitch: digit-major, padded
-  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);           // 256 * HP
-  uint32_t* tot = hist + 256 * HP;                               // 32
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);           // 256 * (W + 1)
+  uint32_t* tot = hist + 256 * (W + 1);                          // 32
   uint32_t* ka = tot + 32;
   uint32_t* kb = ka + nc;
   uint16_t* ia = reinterpret_cast<uint16_t*>(kb + nc);
   uint16_t* ib = ia + nc;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int seg = ((nc + W - 1) / W + 31) / 32 * 32;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  for (int p = blockIdx.x; p < n_valid; p += gridDim.x) {
+  const int n_items = list ? min(*n_list, n_valid) : n_valid;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int p = list ? list[it] : it;
     const float* zp = z + static_cast<long long>(p) * nc;
 #pragma unroll 4
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
       ka[k] = f2key(__ldg(zp + k));
       ia[k] = static_cast<uint16_t>(k);
     }
-    uint32_t* ks = ka; uint32_t* kd = kb;
-    uint16_t* is = ia; uint16_t* id = ib;
     __syncthreads();
-    for (int pass = 0; pass < 4; ++pass) {
-      const int sh = 8 * pass;
-      for (int i = threadIdx.x; i < 256 * HP; i += blockDim.x) hist[i] = 0;
-      __syncthreads();
-      for (int i = lane; i < seg; i += 32) {
-        const int k = warp * seg + i;
-        if (k < nc) atomicAdd(&hist[((ks[k] >> sh) & 255u) * HP + warp], 1u);
-      }
-      __syncthreads();
-      block_exclusive_scan(hist, 256 * HP, tot);
-      for (int b = 0; b < seg; b += 32) {
-        const int k = warp * seg + b + lane;
-        const bool valid = k < nc;
-        const uint32_t key = valid ? ks[k] : 0u;
-        const uint32_t d = (key >> sh) & 255u;
-        // lanes holding the same digit: one ballot per digit bit
-        unsigned peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-        for (int bit = 0; bit < 8; ++bit) {
-          const bool x = (d >> bit) & 1u;
-          const unsigned bb = __ballot_sync(0xffffffffu, x);
-          peers &= x ? bb : ~bb;
-        }
-        if (valid) {
-          const uint32_t pos = hist[d * HP + warp] + __popc(peers & lt_mask);
-          kd[pos] = key;
-          id[pos] = is[k];
-        }
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) hist[d * HP + warp] += __popc(peers);
-        __syncwarp();
-      }
-      __syncthreads();
-      uint32_t* t1 = ks; ks = kd; kd = t1;
-      uint16_t* t2 = is; is = id; id = t2;
-    }
-    // running-median walk stream: step k inserts channel k + h and removes
-    // channel k - h - 1, stored at index k + H (H = h rounded up to 4) as
-    // (insert rank, remove rank), 0xffff = none; indices below H hold the
-    // insert-only steps that build the first window
-    const int H = (h + 3) & ~3;
-    const int S = walk_stride(nc, h);
+    lsd_sort(ka, ia, kb, ib, nc, hist, tot);
     float* svp = sv + static_cast<long long>(p) * nc;
-    uint32_t* sp = steps + static_cast<long long>(p) * S;
-    // four passes leave the sorted keys in ka and their channels in ia; once
-    // the sorted values are out, ka..kb (2 nc >= S words) holds the stream,
-    // built in shared memory and written out with coalesced stores
-    for (int r = threadIdx.x; r < nc; r += blockDim.x) svp[r] = key2f(ks[r]);
-    __syncthreads();
-    uint32_t* stp = ka;
-    for (int k = threadIdx.x; k < S; k += blockDim.x) stp[k] = 0xffffffffu;
-    __syncthreads();
-    uint16_t* st16 = reinterpret_cast<uint16_t*>(stp);
     for (int r = threadIdx.x; r < nc; r += blockDim.x) {
-      const int j = is[r];
-      st16[2 * (j - h + H)] = static_cast<uint16_t>(r);
-      if (j + h + 1 < nc) st16[2 * (j + h + 1 + H) + 1] = static_cast<uint16_t>(r);
+      svp[r] = key2f(ka[r]);
+      ib[ia[r]] = static_cast<uint16_t>(r);                     // channel -> rank
     }
     __syncthreads();
-    // S is a multiple of 4 and every pixel's stream starts 16-byte aligned
-    for (int k = threadIdx.x; k < S / 4; k += blockDim.x)
-      reinterpret_cast<uint4*>(sp)[k] = reinterpret_cast<const uint4*>(stp)[k];
+    write_stream(ib, nc, h, steps + static_cast<long long>(p) * walk_stride(nc, h));
+    __syncthreads();
+  }
+}
+
+// Bin of the 256-bin histogram hg holding element `target` (0-based, in key
+// order) and the count below that bin; run by one warp.
+__device__ __forceinline__ void find_bin(const uint32_t* hg, int target, int* bin, int* below) {
+  const int lane = threadIdx.x & 31;
+  uint32_t c[8], s = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    c[u] = hg[lane * 8 + u];
+    s += c[u];
+  }
+  uint32_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  uint32_t run = incl - s;
+  const uint32_t tg = static_cast<uint32_t>(target);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if (run <= tg && tg < run + c[u]) {
+      *bin = lane * 8 + u;
+      *below = static_cast<int>(run);
+    }
+    run += c[u];
+  }
+}
+
+constexpr int kRankMaxPerThread = 16;   // band ranking: nc <= 16 * 1024
+
+// Band ranks of one pixel spectrum per CTA iteration.  The walk of a long
+// coarse channel needs exact ranks only inside the band [r_lo, r_lo + B) of
+// the middle ranks; below and above it a count suffices.  Two radix-select
+// rounds over the 16 high key bits find the 16-bit buckets holding ranks r_lo
+// and r_lo + B - 1; the keys from the lower bucket's start to the upper
+// bucket's end (the band, its bucket mates and any ties) are compacted in
+// channel order and sorted stably, so the m-th of them has the stable rank
+// c_lo + m (c_lo = keys below the lower bucket), as in the full sort.  Output:
+// the band's sorted values (sv [pixel][0 .. B)) and the stream of band ranks
+// with the below / above codes.
+__global__ void __launch_bounds__(1024)
+k_rank_band(const float* __restrict__ z, int n_valid, int nc, int h, int r_lo, int B, float* __restrict__ sv,
+            uint32_t* __restrict__ steps) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = blockDim.x >> 5;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);           // 256 * (W + 1): sort; 3 * 256 + 512: select
+  uint32_t* tot = hist + 256 * (W + 1);                          // 32
+  uint32_t* ka = tot + 32;
+  uint32_t* kb = ka + nc;
+  uint16_t* ia = reinterpret_cast<uint16_t*>(kb + nc);
+  uint16_t* ib = ia + nc;
+  __shared__ int sel[8];                                         // d_lo, d_hi, c1_lo, c1_hi, e_lo, e_hi, c2_lo, m
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int r_hi = r_lo + B - 1;
+  for (int p = blockIdx.x; p < n_valid; p += gridDim.x) {
+    const float* zp = z + static_cast<long long>(p) * nc;
+    // channel i * blockDim + t in register i: a warp's lanes hold 32 consecutive channels
+    uint32_t key[kRankMaxPerThread];
+#pragma unroll
+    for (int i = 0; i < kRankMaxPerThread; ++i) {
+      const int k = i * blockDim.x + threadIdx.x;
+      key[i] = k < nc ? f2key(__ldg(zp + k)) : 0u;
+    }
+    uint32_t* h1 = hist;
+    uint32_t* h2lo = hist + 256;
+    uint32_t* h2hi = hist + 512;
+    uint32_t* cnt = hist + 768;                                  // per-chunk candidate counts
+    for (int i = threadIdx.x; i < 768; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    // round 1: the top byte; the leader of each group of equal digits adds it
+#pragma unroll
+    for (int i = 0; i < kRankMaxPerThread; ++i) {
+      if (i * static_cast<int>(blockDim.x) >= nc) break;
+      const bool valid = i * blockDim.x + threadIdx.x < nc;
+      const uint32_t d = key[i] >> 24;
+      unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int bit = 0; bit < 8; ++bit) {
+        const bool x = (d >> bit) & 1u;
+        const unsigned bb = __ballot_sync(0xffffffffu, x);
+        peers &= x ? bb : ~bb;
+      }
+      if (valid && lane == __ffs(peers) - 1) atomicAdd(&h1[d], __popc(peers));
+    }
+    __syncthreads();
+    if (warp == 0) {
+      find_bin(h1, r_lo, &sel[0], &sel[2]);
+      find_bin(h1, r_hi, &sel[1], &sel[3]);
+    }
+    __syncthreads();
+    const uint32_t d_lo = sel[0], d_hi = sel[1];
+    // round 2: the second byte among keys of the two boundary top bytes
+#pragma unroll
+    for (int i = 0; i < kRankMaxPerThread; ++i) {
+      if (i * static_cast<int>(blockDim.x) >= nc) break;
+      const bool valid = i * blockDim.x + threadIdx.x < nc;
+      const uint32_t t = key[i] >> 24, d = (key[i] >> 16) & 255u;
+      const bool in_lo = valid && t == d_lo, in_hi = valid && t == d_hi && d_hi != d_lo;
+      unsigned eq = 0xffffffffu;
+#pragma unroll
+      for (int bit = 0; bit < 8; ++bit) {
+        const bool x = (d >> bit) & 1u;
+        const unsigned bb = __ballot_sync(0xffffffffu, x);
+        eq &= x ? bb : ~bb;
+      }
+      const unsigned plo = eq & __ballot_sync(0xffffffffu, in_lo);
+      const unsigned phi = eq & __ballot_sync(0xffffffffu, in_hi);
+      if (in_lo && lane == __ffs(plo) - 1) atomicAdd(&h2lo[d], __popc(plo));
+      if (in_hi && lane == __ffs(phi) - 1) atomicAdd(&h2hi[d], __popc(phi));
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int dummy;
+      find_bin(h2lo, r_lo - sel[2], &sel[4], &sel[6]);
+      find_bin(d_hi == d_lo ? h2lo : h2hi, r_hi - sel[3], &sel[5], &dummy);
+    }
+    __syncthreads();
+    const uint32_t v_lo = (d_lo << 24) | (static_cast<uint32_t>(sel[4]) << 16);
+    const uint32_t v_hi = (d_hi << 24) | (static_cast<uint32_t>(sel[5]) << 16) | 0xffffu;
+    const int c_lo = sel[2] + sel[6];                            // keys below v_lo
+    // compaction of the candidates in channel order: chunk (i, warp) is
+    // channels [i * blockDim + 32 warp, + 32)
+    const int n_chunks = (nc + blockDim.x - 1) / blockDim.x * W;
+#pragma unroll
+    for (int i = 0; i < kRankMaxPerThread; ++i) {
+      if (i * static_cast<int>(blockDim.x) >= nc) break;
+      const bool valid = i * blockDim.x + threadIdx.x < nc;
+      const bool cand = valid && key[i] >= v_lo && key[i] <= v_hi;
+      const unsigned bc = __ballot_sync(0xffffffffu, cand);
+      if (lane == 0) cnt[i * W + warp] = __popc(bc);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // exclusive scan of the n_chunks (<= 512) counts, 16 per lane
+      const int per = (n_chunks + 31) / 32;
+      uint32_t s = 0;
+      for (int u = 0; u < per; ++u) {
+        const int j = lane * per + u;
+        if (j < n_chunks) s += cnt[j];
+      }
+      uint32_t incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      uint32_t run = incl - s;
+      for (int u = 0; u < per; ++u) {
+        const int j = lane * per + u;
+        if (j < n_chunks) {
+          const uint32_t c = cnt[j];
+          cnt[j] = run;
+          run += c;
+        }
+      }
+      if (lane == 31) sel[7] = static_cast<int>(incl);
+    }
+    __syncthreads();
+    const int m = sel[7];
+    uint16_t* rk = ib;                                           // channel -> band rank or code, after the sort
+#pragma unroll
+    for (int i = 0; i < kRankMaxPerThread; ++i) {
+      if (i * static_cast<int>(blockDim.x) >= nc) break;
+      const int k = i * blockDim.x + threadIdx.x;
+      const bool valid = k < nc;
+      const bool cand = valid && key[i] >= v_lo && key[i] <= v_hi;
+      const unsigned bc = __ballot_sync(0xffffffffu, cand);
+      if (cand) {
+        const uint32_t pos = cnt[i * W + warp] + __popc(bc & lt_mask);
+        ka[pos] = key[i];
+        ia[pos] = static_cast<uint16_t>(k);
+      }
+    }
+    __syncthreads();
+    lsd_sort(ka, ia, kb, ib, m, hist, tot);
+    // candidate j has stable rank c_lo + j, band rank j - (r_lo - c_lo)
+    const int off = r_lo - c_lo;
+    float* svp = sv + static_cast<long long>(p) * nc;
+    for (int j = threadIdx.x; j < B; j += blockDim.x) svp[j] = key2f(ka[off + j]);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const int b = j - off;
+      rk[ia[j]] = static_cast<uint16_t>(b < 0 ? kRankBelow : (b >= B ? kRankAbove : static_cast<uint32_t>(b)));
+    }
+#pragma unroll
+    for (int i = 0; i < kRankMaxPerThread; ++i) {
+      const int k = i * blockDim.x + threadIdx.x;
+      if (k < nc && (key[i] < v_lo || key[i] > v_hi))
+        rk[k] = static_cast<uint16_t>(key[i] < v_lo ? kRankBelow : kRankAbove);
+    }
+    __syncthreads();
+    write_stream(rk, nc, h, steps + static_cast<long long>(p) * walk_stride(nc, h));
     __syncthreads();
   }
 }
 
 // --------------------------------------------------------- a9 running median
-constexpr int kWalkThreads = 64;
-constexpr int kWalkQ = 1;        // 16-byte step words per walk iteration
+// The walk keeps, per pixel spectrum, the set of ranks inside the current
+// window as a bitset over B ranks (the full walk: every rank, B >= nc; the
+// band walk: the middle 2048 ranks of the band stream, whose elements below
+// and above the band are only counted).  A cursor word W with lt = the number of
+// set bits in words below W finds any order statistic of the band in a few
+// word steps, since consecutive windows move it by at most one element; an
+// insert or remove below W moves lt by one, so no step needs a search for a
+// removed element.  A pixel's outputs may be split into S segments of
+// consecutive channels, each walked by its own thread from the window before
+// its first output (built from the inserts of the stream), so the chain of
+// dependent steps a thread runs is about nc / S + w instead of nc + w / 2.
 
-// Bitset helpers; bit b of a thread's set is word b / 32 at bits[(b / 32) * T]
-// (the words of the threads of a CTA interleave).
-template <int T>
-__device__ __forceinline__ int next_set(const uint32_t* bits, int p, int nwords) {
-  int w = p >> 5;
-  if (w >= nwords) return -1;
-  uint32_t word = bits[w * T] & (0xffffffffu << (p & 31));
-  while (word == 0) {
-    if (++w >= nwords) return -1;
-    word = bits[w * T];
-  }
-  return (w << 5) + __ffs(word) - 1;
+// Position of the n-th (0-based) set bit of x, n < popc(x): binary search on
+// the population counts of the low halves.
+__device__ __forceinline__ int select_bit(uint32_t x, int n) {
+  int pos = 0;
+  int c = __popc(x & 0xffffu);
+  if (n >= c) { n -= c; pos += 16; x >>= 16; }
+  c = __popc(x & 0xffu);
+  if (n >= c) { n -= c; pos += 8; x >>= 8; }
+  c = __popc(x & 0xfu);
+  if (n >= c) { n -= c; pos += 4; x >>= 4; }
+  c = __popc(x & 0x3u);
+  if (n >= c) { n -= c; pos += 2; x >>= 2; }
+  return pos + (n >= static_cast<int>(x & 1u) ? 1 : 0);
 }
 
-template <int T>
-__device__ __forceinline__ int prev_set(const uint32_t* bits, int p) {
-  if (p < 0) return -1;
-  int w = p >> 5;
-  uint32_t word = bits[w * T] & (0xffffffffu >> (31 - (p & 31)));
-  while (word == 0) {
-    if (--w < 0) return -1;
-    word = bits[w * T];
+struct WalkState {
+  int below, above, band;   // window elements below, above and inside the band
+  int W, lt;                // cursor word; set bits in the words below it
+};
+
+// Insert (sgn = +1) or remove (sgn = -1) band rank r (r < 0: below the band,
+// r >= B: above it).  Ranks are distinct, so both flip one bit.  Bit b of a
+// thread's set is word b / 32 at bits[(b / 32) * T] (the words of the
+// threads of a CTA interleave).
+template <bool BAND, int T>
+__device__ __forceinline__ void walk_update(uint32_t* bits, int r, int B, int sgn, WalkState& s) {
+  const bool inb = !BAND || static_cast<unsigned>(r) < static_cast<unsigned>(B);
+  if (BAND) {
+    s.below += r < 0 ? sgn : 0;
+    s.above += r >= B ? sgn : 0;
   }
-  return (w << 5) + 31 - __clz(word);
+  if (inb) bits[(r >> 5) * T] ^= 1u << (r & 31);
+  s.band += inb ? sgn : 0;
+  s.lt += (inb && (r >> 5) < s.W) ? sgn : 0;
 }
 
-__device__ __forceinline__ bool walk_step(uint32_t* bits, int nwords, uint32_t word, int& size, int& cur,
-                                          int& lt) {
-  const int rin = static_cast<int>(word & 0xffffu);
-  const int rout = static_cast<int>(word >> 16);
-  if (rin != 0xffff) {
-    bits[(rin >> 5) * kWalkThreads] |= 1u << (rin & 31);
-    ++size;
-    if (cur < 0) { cur = rin; lt = 0; }
-    else if (rin < cur) ++lt;
+// Band positions of the window's lower and upper median (equal for an odd
+// window); false if either lies outside the band.
+template <bool BAND, int T>
+__device__ __forceinline__ bool walk_median(const uint32_t* bits, WalkState& s, int& lo, int& hi) {
+  const int below = BAND ? s.below : 0;
+  const int size = below + s.band + (BAND ? s.above : 0);
+  const int tb = ((size - 1) >> 1) - below;
+  const bool even = (size & 1) == 0;
+  if (tb < 0 || tb + (even ? 1 : 0) >= s.band) return false;
+  // lt > tb >= 0 means a set bit below W; lt + popc(word W) <= tb < band means
+  // a set bit above it: the cursor stays inside the set's words
+  while (s.lt > tb) {
+    --s.W;
+    s.lt -= __popc(bits[s.W * T]);
   }
-  if (rout != 0xffff) {
-    bits[(rout >> 5) * kWalkThreads] &= ~(1u << (rout & 31));
-    --size;
-    if (rout < cur) {
-      --lt;
-    } else if (rout == cur) {
-      const int nx = next_set<kWalkThreads>(bits, rout, nwords);
-      if (nx >= 0) cur = nx;
-      else { cur = prev_set<kWalkThreads>(bits, rout); --lt; }
+  uint32_t x = bits[s.W * T];
+  int pc = __popc(x);
+  while (s.lt + pc <= tb) {
+    s.lt += pc;
+    ++s.W;
+    x = bits[s.W * T];
+    pc = __popc(x);
+  }
+  const int b = select_bit(x, tb - s.lt);
+  lo = (s.W << 5) + b;
+  hi = lo;
+  if (even) {
+    // the next set bit: in this word above b, else in a following word
+    const uint32_t rest = b < 31 ? x & (0xfffffffeu << b) : 0u;
+    if (rest) {
+      hi = (s.W << 5) + __ffs(rest) - 1;
+    } else {
+      int w2 = s.W + 1;
+      uint32_t y = bits[w2 * T];
+      while (y == 0u) y = bits[++w2 * T];
+      hi = (w2 << 5) + __ffs(y) - 1;
     }
   }
-  if (size == 0) { cur = -1; lt = 0; return true; }
-  const int target = (size - 1) >> 1;
-  while (lt < target && cur >= 0) { cur = next_set<kWalkThreads>(bits, cur + 1, nwords); ++lt; }
-  while (lt > target && cur >= 0) { cur = prev_set<kWalkThreads>(bits, cur - 1); --lt; }
-  return cur >= 0;
+  return true;
 }
 
-// Median ranks of output channel k of pixel p: lower | upper << 16 (equal for
-// odd windows), in med [pixel][nc].
-__device__ __forceinline__ void put_med(uint32_t* med, int p, int nc, int k, uint32_t v) {
-  med[static_cast<long long>(p) * nc + k] = v;
-}
-
-// One thread per pixel walks its step stream (written by k_rank) over a rank
-// bitset and writes each window's median ranks to med.  The loop touches only
-// the bitset in shared memory and the thread's own stream, read two chunks
-// ahead; k_median_sub then applies the medians with all threads.  With a
-// pixel list (the band walk's failures) thread i walks list[i], i < *n_list.
-__global__ void __launch_bounds__(kWalkThreads)
-k_walk(const uint32_t* __restrict__ steps, int n_valid, int nc, int h, uint32_t* __restrict__ med,
-       const int* __restrict__ list, const int* __restrict__ n_list) {
-  extern __shared__ uint32_t bits_all[];
-  const int t = threadIdx.x;
-  int p = blockIdx.x * kWalkThreads + t;
-  if (list) {
-    if (p >= *n_list) return;                            // no barrier follows
-    p = list[p];
-  }
-  const int nwords = (nc + 31) >> 5;
-  uint32_t* bits = bits_all + t;                         // word w at bits[w * kWalkThreads]
-  for (int w = 0; w < nwords; ++w) bits[w * kWalkThreads] = 0u;
-  if (p >= n_valid) return;
-  const int H = (h + 3) & ~3;
-  const int n_total = H + ((nc + 3) & ~3);               // stream words, a multiple of 4
-  const uint4* st4 = reinterpret_cast<const uint4*>(steps + static_cast<long long>(p) * walk_stride(nc, h));
-  int size = 0, cur = -1, lt = 0;
-  // the stream is read kWalkQ 16-byte words (4 kWalkQ steps) per iteration,
-  // two iterations ahead of the walk
-  const int n4 = n_total >> 2;
+// Applies f(index, word) to words [w0, w1) of a pixel's step stream, read in
+// 16-byte chunks two chunks ahead; stops when f returns false.
+template <class F>
+__device__ __forceinline__ bool for_steps(const uint4* __restrict__ st4, int w0, int w1, F&& f) {
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-  uint4 a[kWalkQ], b[kWalkQ];
-#pragma unroll
-  for (int u = 0; u < kWalkQ; ++u) {
-    a[u] = u < n4 ? st4[u] : zero4;
-    b[u] = kWalkQ + u < n4 ? st4[kWalkQ + u] : zero4;
-  }
-  for (int c0 = 0; c0 < n4; c0 += kWalkQ) {
-    uint4 nx[kWalkQ];
-#pragma unroll
-    for (int u = 0; u < kWalkQ; ++u) nx[u] = c0 + 2 * kWalkQ + u < n4 ? st4[c0 + 2 * kWalkQ + u] : zero4;
-#pragma unroll
-    for (int u = 0; u < kWalkQ; ++u) {
-      const int c = c0 + u;
-      if (c >= n4) break;
-      const uint32_t sw[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
-      const int i0 = c << 2;
-      if (i0 < H) {
-        // steps building the first window (H is a multiple of 4)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int k = i0 - H + q;
-          if (k >= nc) continue;
-          if (!walk_step(bits, nwords, sw[q], size, cur, lt)) { atomicExch(&g_detect_status, 3); return; }
-          const int upper = (size & 1) ? cur : next_set<kWalkThreads>(bits, cur + 1, nwords);
-          if (upper < 0) { atomicExch(&g_detect_status, 3); return; }
-          put_med(med, p, nc, k, static_cast<uint32_t>(cur) | (static_cast<uint32_t>(upper) << 16));
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kWalkQ; ++u) {
-      a[u] = b[u];
-      b[u] = nx[u];
-    }
-  }
-}
-
-// The same walk over a band of kBandWords * 32 ranks starting at r_lo (ranks
-// below and above the band are only counted), for coarse channels longer than
-// the band: a window's median of a standardised spectrum stays near the middle
-// rank, so the band holds it for nearly every pixel and the per-pixel state is
-// a quarter of the full bitset's at 8192 channels (four times the walks per
-// SM).  A pixel whose median leaves the band stops and is listed for the full
-// walk (k_walk with the list), which rewrites all its medians.
-constexpr int kBandWords = 64;
-constexpr int kBandThreads = 128;
-
-__global__ void __launch_bounds__(kBandThreads)
-k_walk_band(const uint32_t* __restrict__ steps, int n_valid, int nc, int h, int r_lo, uint32_t* __restrict__ med,
-            int* __restrict__ fail, int* __restrict__ n_fail) {
-  extern __shared__ uint32_t bits_all[];
-  constexpr int T = kBandThreads, NW = kBandWords, B = NW * 32;
-  const int t = threadIdx.x;
-  const int p = blockIdx.x * T + t;
-  uint32_t* bits = bits_all + t;
-  for (int w = 0; w < NW; ++w) bits[w * T] = 0u;
-  if (p >= n_valid) return;
-  const int H = (h + 3) & ~3;
-  const int n4 = (H + ((nc + 3) & ~3)) >> 2;
-  const uint4* st4 = reinterpret_cast<const uint4*>(steps + static_cast<long long>(p) * walk_stride(nc, h));
-  int n_below = 0, n_above = 0, n_band = 0, cur = -1, lt = 0;   // lt: band ranks below cur
-  auto give_up = [&]() {
-    const int slot = atomicAdd(n_fail, 1);
-    if (slot < n_valid) fail[slot] = p;
-  };
-  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-  uint4 a = n4 > 0 ? st4[0] : zero4, b = n4 > 1 ? st4[1] : zero4;
-  for (int c = 0; c < n4; ++c) {
-    const uint4 nx = c + 2 < n4 ? st4[c + 2] : zero4;
+  const int ce = (w1 + 3) >> 2;
+  int c = w0 >> 2;
+  uint4 a = c < ce ? st4[c] : zero4, b = c + 1 < ce ? st4[c + 1] : zero4;
+  for (; c < ce; ++c) {
+    const uint4 nx = c + 2 < ce ? st4[c + 2] : zero4;
     const uint32_t sw[4] = {a.x, a.y, a.z, a.w};
-    const int i0 = c << 2;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int k = i0 - H + q;                            // output channel (< 0: building)
-      if (k >= nc) continue;
-      const int rin = static_cast<int>(sw[q] & 0xffffu), rout = static_cast<int>(sw[q] >> 16);
-      if (rin != 0xffff) {
-        const int r = rin - r_lo;
-        if (r < 0) {
-          ++n_below;
-        } else if (r >= B) {
-          ++n_above;
-        } else {
-          bits[(r >> 5) * T] |= 1u << (r & 31);
-          ++n_band;
-          if (cur < 0) { cur = r; lt = 0; }
-          else if (r < cur) ++lt;
-        }
-      }
-      if (rout != 0xffff) {
-        const int r = rout - r_lo;
-        if (r < 0) {
-          --n_below;
-        } else if (r >= B) {
-          --n_above;
-        } else {
-          bits[(r >> 5) * T] &= ~(1u << (r & 31));
-          --n_band;
-          if (r < cur) {
-            --lt;
-          } else if (r == cur) {
-            const int nxs = next_set<T>(bits, r, NW);
-            if (nxs >= 0) cur = nxs;
-            else { cur = prev_set<T>(bits, r); --lt; }
-          }
-        }
-      }
-      if (n_band == 0) { cur = -1; lt = 0; }
-      if (k < 0) continue;
-      // the lower median is element (size - 1) / 2 of the window; in band
-      // order it is element tb
-      const int size = n_below + n_band + n_above;
-      const int tb = ((size - 1) >> 1) - n_below;
-      const bool even = (size & 1) == 0;
-      if (tb < 0 || tb + (even ? 1 : 0) >= n_band) { give_up(); return; }
-      while (lt < tb) { cur = next_set<T>(bits, cur + 1, NW); ++lt; }
-      while (lt > tb) { cur = prev_set<T>(bits, cur - 1); --lt; }
-      const int upper = even ? next_set<T>(bits, cur + 1, NW) : cur;
-      put_med(med, p, nc, k, static_cast<uint32_t>(cur + r_lo) | (static_cast<uint32_t>(upper + r_lo) << 16));
+      const int i = (c << 2) + q;
+      if (i >= w0 && i < w1 && !f(i, sw[q])) return false;
     }
     a = b;
     b = nx;
   }
+  return true;
+}
+
+constexpr int kWalkThreads = 64;   // full walk: nc / 32 words per thread
+constexpr int kBandWords = 64;     // band walk: 2048 ranks
+constexpr int kBandThreads = 128;
+
+// One thread per (pixel, segment) walks the segment's outputs over the step
+// stream written by k_rank / k_rank_band and writes each window's median
+// ranks, lower | upper << 16 (equal for an odd window; band ranks for a band
+// stream), to med [pixel][nc]; k_median_sub then applies them with all
+// threads (the gathers of the sorted values would otherwise sit in the walk's
+// chain of dependent steps).
+//   BAND: the band stream (nwords * 32 band ranks); a segment whose median
+//     leaves the band gives up, and its pixel is listed once in fail (k_rank
+//     and the full walk redo it).
+//   !BAND: the full rank set (nwords = nc / 32 rounded up); with a pixel list
+//     (the band walk's failures) item i walks list[i], i < *n_list.
+// seg_len is a multiple of 4, so every segment's steps start on a chunk.
+template <bool BAND, int T>
+__global__ void __launch_bounds__(T)
+k_walk(const uint32_t* __restrict__ steps, int n_valid, int nc, int h, int n_seg, int seg_len, int nwords,
+       uint32_t* __restrict__ med, const int* __restrict__ list, const int* __restrict__ n_list,
+       int* __restrict__ fail, int* __restrict__ n_fail) {
+  extern __shared__ uint32_t bits_all[];
+  const int t = threadIdx.x;
+  const int item = (blockIdx.x * T + t) / n_seg;
+  const int sg = (blockIdx.x * T + t) - item * n_seg;
+  uint32_t* bits = bits_all + t;
+  int p = item;
+  bool live = item < n_valid;
+  if (!BAND && list) {
+    live = item < min(*n_list, n_valid);
+    p = live ? list[item] : 0;
+  }
+  bool gave_up = false;
+  if (live) {
+    for (int w = 0; w < nwords; ++w) bits[w * T] = 0u;
+    const int B = nwords * 32;
+    const int H = (h + 3) & ~3;
+    const int k0 = sg * seg_len, k1 = min(nc, k0 + seg_len);
+    const uint4* st4 = reinterpret_cast<const uint4*>(steps + static_cast<long long>(p) * walk_stride(nc, h));
+    uint32_t* mo = med + static_cast<long long>(p) * nc - H;
+    WalkState s{0, 0, 0, 0, 0};
+    auto rank_of = [&](uint32_t r) {
+      if (!BAND) return static_cast<int>(r);
+      return r == kRankBelow ? -1 : (r == kRankAbove ? B : static_cast<int>(r));
+    };
+    // the window before output k0: channels [k0 - 1 - h, k0 - 1 + h]; channel
+    // j is inserted by word j - h + H (the words below H build the first window)
+    const int wa = max(H - h, H + k0 - 1 - 2 * h), wb = H + k0;
+    bool ok = for_steps(st4, wa, wb, [&](int, uint32_t word) {
+      const uint32_t rin = word & 0xffffu;
+      if (rin != kRankNone) walk_update<BAND, T>(bits, rank_of(rin), B, 1, s);
+      return true;
+    });
+    ok = ok && for_steps(st4, H + k0, H + k1, [&](int i, uint32_t word) {
+      const uint32_t rin = word & 0xffffu, rout = word >> 16;
+      if (rin != kRankNone) walk_update<BAND, T>(bits, rank_of(rin), B, 1, s);
+      if (rout != kRankNone) walk_update<BAND, T>(bits, rank_of(rout), B, -1, s);
+      int lo, hi;
+      if (!walk_median<BAND, T>(bits, s, lo, hi)) return false;
+      mo[i] = static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+      return true;
+    });
+    if (!ok) {
+      if (BAND) gave_up = true;
+      else atomicExch(&g_detect_status, 3);            // the full set always holds the median
+    }
+  }
+  if (BAND) {
+    // a pixel's segments are adjacent threads of one warp (n_seg divides 32)
+    const unsigned any = __ballot_sync(0xffffffffu, gave_up);
+    const int lane = t & 31, first = lane - sg;
+    const unsigned mine = ((n_seg >= 32) ? 0xffffffffu : ((1u << n_seg) - 1u)) << first;
+    if (live && sg == 0 && (any & mine)) {
+      const int slot = atomicAdd(n_fail, 1);
+      if (slot < n_valid) fail[slot] = p;
+    }
+  }
 }
 
 // z' = z - (v[lower] + v[upper]) / 2 for every voxel, v the pixel's sorted
-// values and med the median ranks the walk left.
+// values (the band's for a band stream) and med the median ranks the walk left.
 __global__ void k_median_sub(float* __restrict__ zbuf, const float* __restrict__ sv,
                              const uint32_t* __restrict__ med, int n_valid, int nc) {
   if ((nc & 3) == 0) {
@@ -1221,44 +1409,72 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
     OVRO_LAUNCH_CHECK();
   }
   {
+    // Coarse channels longer than the band: band ranks and the band walk for
+    // every pixel, then full ranks and the full walk for the pixels whose
+    // median left the band.  Shorter ones: full ranks and the full walk.
+    const int band = kBandWords * 32;
+    const bool use_band = nc > band && nc <= kRankMaxPerThread * 1024;
     const int threads = 1024, W = threads / 32;      // one CTA per SM (shared memory): all 32 warps
-    const size_t sm = (256 * (W + 1) + 32) * 4 + static_cast<size_t>(nc) * 12;
-    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    const size_t sm_rank = (256 * (W + 1) + 32) * 4 + static_cast<size_t>(nc) * 12;
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm_rank)));
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank_band, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm_rank)));
     // CTAs per SM (each CTA loops over pixels; the outputs do not depend on it)
     auto rank = [&](int per_sm) -> int {
       const int blocks = std::min(p.n_valid, per_sm * nsm);
       OVRO_PROF("k_rank", st);
-      k_rank<<<blocks, threads, sm, st>>>(w.zbuf, p.n_valid, nc, p.half[c], w.sv, w.steps);
+      if (use_band)
+        k_rank_band<<<blocks, threads, sm_rank, st>>>(w.zbuf, p.n_valid, nc, p.half[c], nc / 2 - band / 2, band,
+                                                      w.sv, w.steps);
+      else
+        k_rank<<<blocks, threads, sm_rank, st>>>(w.zbuf, p.n_valid, nc, p.half[c], w.sv, w.steps, nullptr, nullptr);
       OVRO_LAUNCH_CHECK();
       return OVRO_OK;
     };
-    const std::string key = tune_key("k_rank", {p.n_valid, nc});
-    int per_sm = tuned(key, 16);
+    const std::string rkey = tune_key(use_band ? "k_rank_band" : "k_rank", {p.n_valid, nc});
+    int per_sm = tuned(rkey, 16);
     if (tuning(st))
-      if (int e = tune_pick(key, {1, 2, 4, 16}, rank, st, &per_sm)) return e;
-    if (int e = rank(per_sm)) return e;
-  }
-  {
-    // the band walk for coarse channels longer than its band, the full walk
-    // for the pixels it gives up on (or for every pixel of a short channel)
-    const int band = kBandWords * 32;
-    const bool use_band = nc > band;
-    if (use_band) {
-      const size_t sm = static_cast<size_t>(kBandWords) * kBandThreads * 4;
-      OVRO_CUDA_TRY(cudaMemsetAsync(w.count + 3, 0, sizeof(int), st));
+      if (int e = tune_pick(rkey, {1, 2, 4, 16}, rank, st, &per_sm)) return e;
+
+    // S segments per pixel (S divides 32), tuned per shape; a trial ranks
+    // again, since the fallback rewrites the failed pixels' streams
+    const int nwords = (nc + 31) / 32;
+    const size_t sm_full = static_cast<size_t>(nwords) * kWalkThreads * 4;
+    const size_t sm_band = static_cast<size_t>(kBandWords) * kBandThreads * 4;
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk<false, kWalkThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm_full)));
+    auto rank_walk = [&](int n_seg) -> int {
+      if (int e = rank(per_sm)) return e;
+      const int seg_len = ((nc + n_seg - 1) / n_seg + 3) & ~3;
+      const long long thr = static_cast<long long>(p.n_valid) * n_seg;
+      if (use_band) {
+        OVRO_CUDA_TRY(cudaMemsetAsync(w.count + 3, 0, sizeof(int), st));
+        {
+          OVRO_PROF("k_walk", st);
+          k_walk<true, kBandThreads><<<static_cast<int>((thr + kBandThreads - 1) / kBandThreads), kBandThreads,
+                                       sm_band, st>>>(w.steps, p.n_valid, nc, p.half[c], n_seg, seg_len, kBandWords,
+                                                      w.med, nullptr, nullptr, w.fail, w.count + 3);
+          OVRO_LAUNCH_CHECK();
+        }
+        OVRO_PROF("k_rank", st);
+        k_rank<<<std::min(p.n_valid, nsm), threads, sm_rank, st>>>(w.zbuf, p.n_valid, nc, p.half[c], w.sv, w.steps,
+                                                                   w.fail, w.count + 3);
+        OVRO_LAUNCH_CHECK();
+      }
       OVRO_PROF("k_walk", st);
-      k_walk_band<<<(p.n_valid + kBandThreads - 1) / kBandThreads, kBandThreads, sm, st>>>(
-          w.steps, p.n_valid, nc, p.half[c], nc / 2 - band / 2, w.med, w.fail, w.count + 3);
+      k_walk<false, kWalkThreads><<<static_cast<int>((thr + kWalkThreads - 1) / kWalkThreads), kWalkThreads,
+                                    sm_full, st>>>(w.steps, p.n_valid, nc, p.half[c], n_seg, seg_len, nwords, w.med,
+                                                   use_band ? w.fail : nullptr, use_band ? w.count + 3 : nullptr,
+                                                   nullptr, nullptr);
       OVRO_LAUNCH_CHECK();
-    }
-    const size_t sm = static_cast<size_t>((nc + 31) / 32) * kWalkThreads * 4;
-    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-    {
-      OVRO_PROF("k_walk", st);
-      k_walk<<<(p.n_valid + kWalkThreads - 1) / kWalkThreads, kWalkThreads, sm, st>>>(
-          w.steps, p.n_valid, nc, p.half[c], w.med, use_band ? w.fail : nullptr, use_band ? w.count + 3 : nullptr);
-      OVRO_LAUNCH_CHECK();
-    }
+      return OVRO_OK;
+    };
+    const std::string key = tune_key("k_walk", {p.n_valid, nc});
+    int n_seg = tuned(key, 2);
+    if (tuning(st))
+      if (int e = tune_pick(key, {1, 2, 4}, rank_walk, st, &n_seg)) return e;
+    if (int e = rank_walk(n_seg)) return e;
     OVRO_PROF("k_median_sub", st);
     k_median_sub<<<8 * nsm, 256, 0, st>>>(w.zbuf, w.sv, w.med, p.n_valid, nc);
     OVRO_LAUNCH_CHECK();
@@ -1276,8 +1492,8 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
     auto mf = [&](int per_sm, unsigned long long* hist) -> int {
       const int blocks = std::min(p.n_valid, per_sm * nsm);
       OVRO_PROF("k_mf", st);
-      k_mf<<<blocks, 128, sm, st>>>(w.zbuf, p.n_valid, nc, w.snr + p.vox0[c], w.width + p.vox0[c],
-                                    hist_key0, n_bins, hist);
+      k_mf<<<blocks, 128, sm, st>>>(w.zbuf, p.n_valid, nc, w.snr + p.vox0[c], w.width + p.vox0[c], hist_key0,
+                                    n_bins, hist);
       OVRO_LAUNCH_CHECK();
       return OVRO_OK;
     };

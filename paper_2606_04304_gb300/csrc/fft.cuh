@@ -148,17 +148,16 @@ namespace ovro {
 // stride 16 become conflict-free.
 __device__ __forceinline__ int pad16(int x) { return x + (x >> 4); }
 
-// One Stockham pass in place.  With PLANAR the pass reads its input from two
-// real arrays (re, im: row f, element x at f * pp + x), which may overlap `a`:
-// every read completes before the first write.
-template <int R, bool PLANAR = false>
-__device__ __forceinline__ void inplace_pass(float2* a, int ldp, int G, int Ns,
-                                             const float2* __restrict__ tw,
-                                             const float* pre = nullptr, const float* pim = nullptr,
-                                             int pp = 0) {
+// One Stockham pass in place over rows of G points, the first NS-point
+// transforms already done (G, R and NS are compile-time, so every index split
+// is a shift).  load(f, x) gives element x of row f of the pass's input (the
+// rows themselves, or another source for a first pass; every read completes
+// before the first write, so the source may overlap `a`); tw(i) = omega_G^i.
+template <int R, int NS, int G, class Load, class Tw>
+__device__ __forceinline__ void stockham_pass(float2* a, int ldp, Load&& load, Tw&& tw) {
   // every thread holds exactly 16 values: 16 / R butterflies of radix R
   constexpr int NB = 16 / R;
-  const int per = G / R;
+  constexpr int per = G / R;
   const int T = blockDim.x;
   float2 v[16];
   int fj[NB];
@@ -168,60 +167,47 @@ __device__ __forceinline__ void inplace_pass(float2* a, int ldp, int G, int Ns,
     const int f = gb / per, j = gb - f * per;
     fj[b] = gb;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (PLANAR) {
-        const int x = f * pp + j + r * per;
-        v[b * R + r] = make_float2(pre[x], pim[x]);
-      } else {
-        v[b * R + r] = a[f * ldp + pad16(j + r * per)];
-      }
-    }
+    for (int r = 0; r < R; ++r) v[b * R + r] = load(f, j + r * per);
   }
   __syncthreads();
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int f = fj[b] / per, j = fj[b] - f * per;
-    const int k = j & (Ns - 1);
+    const int k = j & (NS - 1);
     float2 x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = v[b * R + r];
-    if (Ns > 1) {
-      const int base = k * (G / (Ns * R));
+    if (NS > 1) {
+      const int base = k * (G / (NS * R));
 #pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw[r * base]);
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw(r * base));
     }
     dft_reg<R>(x);
-    const int o = (j / Ns) * Ns * R + k;
+    const int o = (j / NS) * NS * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) a[f * ldp + pad16(o + r * Ns)] = x[r];
+    for (int r = 0; r < R; ++r) a[f * ldp + pad16(o + r * NS)] = x[r];
   }
   __syncthreads();
 }
 
 // In-place forward FFTs of the rows of `a` (row f at a[f * ldp], element x at
-// pad16(x)), G = 2^LOG2G >= 32, with blockDim.x * 16 == rows * G.
-// tw: omega_G^k, k < G (shared memory).
-// With `pre` non-null the rows are first read from the planar arrays
-// (pre, pim, row pitch pp floats; see inplace_pass), G >= 16.
-template <int LOG2G>
-__device__ void fft_rows_inplace(float2* a, int ldp, const float2* tw, const float* pre = nullptr,
-                                 const float* pim = nullptr, int pp = 0) {
+// pad16(x)), G = 2^LOG2G with 16 <= G <= 16384, with blockDim.x * 16 == rows * G:
+// radix-16 passes, then one of radix 2, 4 or 8.  The first pass reads its
+// input through load0(f, x); tw(i) = omega_G^i.
+template <int LOG2G, class Load, class Tw>
+__device__ void fft_rows_inplace_f(float2* a, int ldp, Load&& load0, Tw&& tw) {
   constexpr int G = 1 << LOG2G;
   constexpr int n16 = LOG2G / 4;
   constexpr int rem = LOG2G % 4;
-  static_assert(n16 >= 1, "G >= 16");
-  int Ns = 1;
-  if (pre) inplace_pass<16, true>(a, ldp, G, Ns, tw, pre, pim, pp);
-  else inplace_pass<16>(a, ldp, G, Ns, tw);
-  Ns = 16;
-#pragma unroll
-  for (int p = 1; p < n16; ++p) {
-    inplace_pass<16>(a, ldp, G, Ns, tw);
-    Ns *= 16;
-  }
-  if (rem == 1) inplace_pass<2>(a, ldp, G, Ns, tw);
-  if (rem == 2) inplace_pass<4>(a, ldp, G, Ns, tw);
-  if (rem == 3) inplace_pass<8>(a, ldp, G, Ns, tw);
+  constexpr int NSR = 1 << (4 * n16);                 // transforms done before the last radix-2/4/8 pass
+  static_assert(n16 >= 1 && n16 <= 3, "16 <= G <= 16384");
+  auto rows = [&](int f, int x) { return a[f * ldp + pad16(x)]; };
+  stockham_pass<16, 1, G>(a, ldp, load0, tw);
+  if constexpr (n16 >= 2) stockham_pass<16, 16, G>(a, ldp, rows, tw);
+  if constexpr (n16 >= 3) stockham_pass<16, 256, G>(a, ldp, rows, tw);
+  if constexpr (rem == 1) stockham_pass<2, NSR, G>(a, ldp, rows, tw);
+  if constexpr (rem == 2) stockham_pass<4, NSR, G>(a, ldp, rows, tw);
+  if constexpr (rem == 3) stockham_pass<8, NSR, G>(a, ldp, rows, tw);
 }
 
 }  // namespace ovro

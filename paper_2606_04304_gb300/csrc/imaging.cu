@@ -209,8 +209,12 @@ __host__ __device__ constexpr int n_tiles(int g) { return (g / 2 / kTileV) * (g 
 // [-kTabD, kTabD] at stride Q + 1, so (d, off) -> (d + kTabD) (Q + 1) + Q / 2 - off
 // is one-to-one over off in [-Q/2, Q/2] (d = 3 at off = -Q/2 and d = 4 at
 // off = Q/2 land on different entries) and a tile's weights are plain loads at
-// fixed strides from one base, with no range tests.
-constexpr int kTabD = kHalfSup + kTileU - 1;              // 10: offsets a tile column can take
+// fixed strides from one base, with no range tests.  Offsets a tile column
+// can take when the footprint touches the tile lie in [-(3 + kTileU - 1), 3];
+// the kTabMargin rows beyond them (zeros) let a lane whose centre is up to
+// kTabMargin cells from a tile it is listed for read zeros there.
+constexpr int kTabMargin = 4;
+constexpr int kTabD = kHalfSup + kTileU - 1 + kTabMargin;   // 10
 constexpr int kTabStride = kQ + 1;
 constexpr int kTabXLen = (2 * kTabD + 1) * kTabStride;
 
@@ -218,11 +222,23 @@ constexpr int kTabXLen = (2 * kTabD + 1) * kTabStride;
 // by k_grid_prep: its exact rounded position p = rint(u Q), rint(v Q) and its
 // value in the Hermitian part of the grid, conj(Stokes I) / 2, or V = 0 when
 // the visibility is not gridded in that channel.  Layout [group][listed][32].
+// With table bases (a call whose footprints move by less than kTabMargin
+// cells over its channels), pu and pv hold instead the weight-table offsets
+// of the position: column c's weight is tabx[pu + c (Q + 1)], row r's
+// tabx[pv + r (Q + 1)] (r, c grid indices), zero beyond the footprint.
 struct PrepRec {
   int pu, pv;
   float vr, vi;
 };
 constexpr int kMirror = 1 << 31;    // tile list flag: grid the record's mirror (-u, -v, conj V)
+
+// Table offset of a position with centre cell c and offset off (1/Q cells)
+// on an axis of G cells; the mirror position (-c, -off) has offset
+// tab_mirror(G) - tab_base(G, c, off).
+__host__ __device__ constexpr int tab_base(int g, int c, int off) {
+  return (kTabD - g / 2 - c) * kTabStride + kQ / 2 - off;
+}
+__host__ __device__ constexpr int tab_mirror(int g) { return 2 * (kTabD - g / 2) * kTabStride + kQ; }
 constexpr int kPrepPerWarp = 8;     // listed baselines per warp of k_grid_prep
 
 // a5 and the Stokes I of a6 for one channel group: a warp's lanes are the
@@ -235,7 +251,7 @@ constexpr int kPrepPerWarp = 8;     // listed baselines per warp of k_grid_prep
 // conj(Stokes I) = conj(XX + YY) / 4 (the exp(+) transform is a forward FFT of
 // the conjugated grid); calibration corrections c_a conj(c_b) are applied per
 // polarisation in FP32 when given.  Kept visibilities are counted per channel.
-template <int LOG2G, bool CAL>
+template <int LOG2G, bool CAL, bool BASES>
 __global__ void __launch_bounds__(256)
 k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* __restrict__ vis, long long n_bl,
             const Baseline* __restrict__ base, const ChanScale* __restrict__ cs, int ch0, int nb,
@@ -291,6 +307,15 @@ k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* _
       keep = keep && lam >= opt.uv_min && lam < opt.uv_max;
     }
     PrepRec r{lim, lim, 0.0f, 0.0f};
+    if (BASES) {
+      // the position's table offsets, kept or not (a record is only read for
+      // tiles within kTabMargin cells of its footprint)
+      int cu, cv, ou, ov;
+      centre_cell32(pu, cu, ou);
+      centre_cell32(pv, cv, ov);
+      r.pu = tab_base(G, cu, ou);
+      r.pv = tab_base(G, cv, ov);
+    }
     if (keep) {
       float vr, vi;
       if (!CAL || gc == nullptr) {
@@ -311,7 +336,12 @@ k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* _
         vr = 0.25f * pr;
         vi = -0.25f * pi;
       }
-      r = PrepRec{pu, pv, vr, vi};
+      if (!BASES) {
+        r.pu = pu;
+        r.pv = pv;
+      }
+      r.vr = vr;
+      r.vi = vi;
       ++n_kept;
     }
     reinterpret_cast<int4*>(out)[static_cast<long long>(i) * kLanes] =
@@ -326,18 +356,24 @@ k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* _
 // channels, warp tile) pairs, group-major, the tiles of a group taken from the
 // longest list to the shortest; every warp of the persistent grid (one CTA of
 // kGridWarps warps per SM) takes items kGridWarps * gridDim.x apart, so each
-// warp starts on a heavy tile and ends on light ones.  The gap-indexed weight table sits in shared memory,
-// loaded once per CTA.  For every list entry of its tile, a lane reads its
-// channel's prepared record (one 16-byte load, the warp's 32 lanes
-// contiguous), mirrors it if flagged, takes the centre cells and the tile's 4
-// row and 8 column weights of the separable kernel, and adds the products into
-// its accumulators; list entries are read three records ahead, records two.
+// warp starts on a heavy tile and ends on light ones.  The gap-indexed weight
+// table sits in shared memory, loaded once per CTA.  For every list entry of
+// its tile, a lane reads its channel's prepared record (one 16-byte load, the
+// warp's 32 lanes contiguous), mirrors it if flagged, reads the tile's 4 row
+// and 4 column weights of the separable kernel and adds the products into its
+// accumulators; list entries are read three records ahead, records two.
+//   BASES: the record holds the weight-table offsets of its position, so the
+//     weights are 8 loads at fixed strides from (offset + tile origin) and a
+//     lane off the footprint reads the table's zero rows;
+//   otherwise the lane takes the centre cells from the position and adds
+//     zeros when its footprint misses the tile.
 // The tile is written with the (-1)^(row + col) centring sign as two real
 // planes, grid [batch][2][G/2][G] (row j - G/2).
-constexpr int kGridWarps = 32;
+constexpr int kGridWarps = 24;
+constexpr int kRing = 3;           // records in flight per warp
 constexpr size_t kTileSmem = static_cast<size_t>(kTabXLen) * sizeof(float);
 
-template <int LOG2G>
+template <int LOG2G, bool BASES>
 __global__ void __launch_bounds__(kGridWarps * 32, 1)
 k_grid_tiles(const int* __restrict__ tile_idx, const int* __restrict__ tile_off, const int* __restrict__ tile_order,
              const PrepRec* __restrict__ prep, int n_listed, const float* __restrict__ tabx_g, int nb,
@@ -372,52 +408,75 @@ k_grid_tiles(const int* __restrict__ tile_idx, const int* __restrict__ tile_off,
 #pragma unroll
       for (int j = 0; j < kTileU; ++j) acr[i][j] = aci[i][j] = 0.0f;
     auto index = [&](int e) { return e < e1 ? __ldg(tile_idx + e) : 0; };
-    auto record = [&](int ent) {
-      const int4 v = __ldg(reinterpret_cast<const int4*>(pg + static_cast<long long>(ent & ~kMirror) * kLanes));
-      if (ent & kMirror) return PrepRec{-v.x, -v.y, __int_as_float(v.z), -__int_as_float(v.w)};
-      return PrepRec{v.x, v.y, __int_as_float(v.z), __int_as_float(v.w)};
+    auto load_rec = [&](int ent) {
+      return __ldg(reinterpret_cast<const int4*>(pg + static_cast<long long>(ent & ~kMirror) * kLanes));
     };
-    int i2 = index(e0 + 2);
-    PrepRec rc = record(index(e0)), r1 = record(index(e0 + 1));
-#pragma unroll 1
-    for (int e = e0; e < e1; ++e) {
-      // records e + 1 and e + 2 in flight; list entry e + 3 in flight
-      const PrepRec r2 = record(i2);
-      i2 = index(e + 3);
+    auto accumulate = [&](const float* bu, const float* bv, float vr, float vi) {
+      float wv[kTileV], wu[kTileU];
+#pragma unroll
+      for (int i = 0; i < kTileV; ++i) wv[i] = bv[i * kTabStride];
+#pragma unroll
+      for (int j = 0; j < kTileU; ++j) wu[j] = bu[j * kTabStride];
+#pragma unroll
+      for (int i = 0; i < kTileV; ++i) {
+        const float br = wv[i] * vr, bi = wv[i] * vi;
+#pragma unroll
+        for (int j = 0; j < kTileU; ++j) {
+          acr[i][j] = fmaf(br, wu[j], acr[i][j]);
+          aci[i][j] = fmaf(bi, wu[j], aci[i][j]);
+        }
+      }
+    };
+    // one list entry: the record (mirrored if flagged) decoded here, at its use
+    auto grid_one = [&](int4 v, int ent) {
+      const bool m = ent & kMirror;
+      const float vr = __int_as_float(v.z), vi = m ? -__int_as_float(v.w) : __int_as_float(v.w);
+      if (BASES) {
+        // the table's zero rows stand for taps off the footprint
+        const int bu = m ? tab_mirror(G) - v.x : v.x, bv = m ? tab_mirror(G) - v.y : v.y;
+        accumulate(tabx + bu + c0 * kTabStride, tabx + bv + r0 * kTabStride, vr, vi);
+        return;
+      }
       int cu, offu, cv, offv;
-      centre_cell32(rc.pu, cu, offu);
-      centre_cell32(rc.pv, cv, offv);
+      centre_cell32(m ? -v.x : v.x, cu, offu);
+      centre_cell32(m ? -v.y : v.y, cv, offv);
       int dv0 = r0 - (G / 2 + cv), du0 = c0 - (G / 2 + cu);   // offsets of the tile's first row / column
       const bool touch = dv0 <= kHalfSup && dv0 >= -(kHalfSup + kTileV - 1) && du0 <= kHalfSup &&
                          du0 >= -(kHalfSup + kTileU - 1);
       if (__any_sync(full, touch)) {
-        float vr = rc.vr, vi = rc.vi;
+        float wr = vr, wi = vi;
         if (!touch) {
           // a lane whose footprint misses the tile adds zeros; its table
           // reads stay inside the table
-          vr = vi = 0.0f;
+          wr = wi = 0.0f;
           dv0 = du0 = 0;
           offu = offv = 0;
         }
-        const float* bu = tabx + (du0 + kTabD) * kTabStride + kQ / 2 - offu;
-        const float* bv = tabx + (dv0 + kTabD) * kTabStride + kQ / 2 - offv;
-        float wv[kTileV], wu[kTileU];
-#pragma unroll
-        for (int i = 0; i < kTileV; ++i) wv[i] = bv[i * kTabStride];
-#pragma unroll
-        for (int j = 0; j < kTileU; ++j) wu[j] = bu[j * kTabStride];
-#pragma unroll
-        for (int i = 0; i < kTileV; ++i) {
-          const float br = wv[i] * vr, bi = wv[i] * vi;
-#pragma unroll
-          for (int j = 0; j < kTileU; ++j) {
-            acr[i][j] = fmaf(br, wu[j], acr[i][j]);
-            aci[i][j] = fmaf(bi, wu[j], aci[i][j]);
-          }
-        }
+        accumulate(tabx + (du0 + kTabD) * kTabStride + kQ / 2 - offu,
+                   tabx + (dv0 + kTabD) * kTabStride + kQ / 2 - offv, wr, wi);
       }
-      rc = r1;
-      r1 = r2;
+    };
+    // a ring of kRing records in flight, each loaded kRing entries ahead of its
+    // use into its own slot (no register moves wait on a load), and their list
+    // entries, loaded 2 kRing ahead
+    int4 q[kRing];
+    int en[kRing], nx[kRing];
+#pragma unroll
+    for (int d = 0; d < kRing; ++d) en[d] = index(e0 + d);
+#pragma unroll
+    for (int d = 0; d < kRing; ++d) {
+      q[d] = load_rec(en[d]);
+      nx[d] = index(e0 + kRing + d);
+    }
+#pragma unroll 1
+    for (int e = e0; e < e1; e += kRing) {
+#pragma unroll
+      for (int d = 0; d < kRing; ++d) {
+        if (e + d < e1) grid_one(q[d], en[d]);
+        en[d] = nx[d];
+        q[d] = load_rec(en[d]);
+        nx[d] = index(e + d + 2 * kRing);
+      }
     }
     // ---- the tile, with the centring sign (r0 and c0 are even)
     if (cb < nb) {
@@ -524,14 +583,29 @@ k_fft_rows(const float* __restrict__ grid, const float2* __restrict__ tw_g, int 
   const float4* src = reinterpret_cast<const float4*>(grid) + static_cast<long long>(cb) * 2 * plane4 +
                       static_cast<long long>(row0) * (G / 4);
   constexpr int RQ = G / 4;                           // float4 per row
-  for (int i = threadIdx.x; i < 2 * band_h * RQ; i += blockDim.x) {
-    const int pl = i / (band_h * RQ), k = i - pl * band_h * RQ;
+  // 2 band_h G / 4 float4 over band_h G / 16 threads: 8 per thread, all
+  // issued before the first is stored
+  constexpr int PER = 8;
+  const int n1 = band_h * RQ;
+  float4 q[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int i = threadIdx.x + u * blockDim.x;
+    const int pl = i >= n1 ? 1 : 0, k = i - pl * n1;
+    q[u] = __ldg(src + pl * plane4 + k);
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int i = threadIdx.x + u * blockDim.x;
+    const int pl = i >= n1 ? 1 : 0, k = i - pl * n1;
     const int r = k / RQ, c = k - r * RQ;
-    const float4 v = __ldg(src + pl * plane4 + static_cast<long long>(r) * RQ + c);
-    *reinterpret_cast<float4*>((pl ? pim : pre) + r * P + 4 * c) = v;
+    *reinterpret_cast<float4*>((pl ? pim : pre) + r * P + 4 * c) = q[u];
   }
   __syncthreads();
-  fft_rows_inplace<LOG2G>(band, LDP, tw, pre, pim, P);
+  // the first pass reads the planar staging (which the band overlaps)
+  fft_rows_inplace_f<LOG2G>(
+      band, LDP, [&](int f, int x) { return make_float2(pre[f * P + x], pim[f * P + x]); },
+      [&](int i) { return tw[i]; });
   store_band<G, LDP, S>(band, band_h, n_img, static_cast<long long>(cb) * half_rows(G) + row0, h, hs);
 }
 
@@ -580,7 +654,8 @@ k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, 
   constexpr int G = 1 << LOG2G;
   constexpr int LDP = band_pitch(G);
   extern __shared__ __align__(16) unsigned char smem[];
-  const int C = cols_per_cta, CP = C / 2;
+  const int C = cols_per_cta, CP = C / 2;             // powers of two
+  const int cp_shift = __ffs(CP) - 1;
   float2* A = reinterpret_cast<float2*>(smem);        // [C / 2][LDP]: packed column pairs
   float2* tw = A + CP * LDP;
   const int cb = blockIdx.y;
@@ -598,7 +673,7 @@ k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, 
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * blockDim.x;
       if (i < n_items) {
-        const int r = i / CP, p = i - r * CP;
+        const int r = i >> cp_shift, p = i & (CP - 1);
         load_h2<S>(h, hs, hrow0 + r, (hrow0 + r) * n_img + c0 + 2 * p, a[u], e[u]);
       }
     }
@@ -606,7 +681,7 @@ k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, 
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * blockDim.x;
       if (i < n_items) {
-        const int r = i / CP, p = i - r * CP;
+        const int r = i >> cp_shift, p = i & (CP - 1);
         const int j = G / 2 + r, jm = G / 2 - r;      // rows j and G - j
         // d = 2 (c1 + i c2); at G - j the columns are conjugated
         A[p * LDP + pad16(j)] = make_float2(2.0f * (a[u].x - e[u].y), 2.0f * (a[u].y + e[u].x));
@@ -615,7 +690,8 @@ k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, 
     }
   }
   __syncthreads();
-  fft_rows_inplace<LOG2G>(A, LDP, tw);
+  fft_rows_inplace_f<LOG2G>(
+      A, LDP, [&](int f, int x) { return A[f * LDP + pad16(x)]; }, [&](int i) { return tw[i]; });
   const long long chan = ch0 + cb;
   const int k = kept[chan];
   const float norm = k > 0 ? 0.5f / static_cast<float>(k) : 0.0f;
@@ -623,7 +699,7 @@ k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, 
   float* out = img + chan * n_img * n_img;
 #pragma unroll 4
   for (int i = threadIdx.x; i < n_img * C; i += blockDim.x) {
-    const int r = i / C, c = i - r * C;
+    const int r = i >> (cp_shift + 1), c = i & (C - 1);
     const int col = c0 + c;
     float v = 0.0f;
     if (mask[r * n_img + col]) {
@@ -714,13 +790,14 @@ struct ImgWs {
   void* h;           // [batch][G][N] complex in the storage format
   float* hs;         // [batch][G] row scales (FP16 storage)
   int n_listed = 0;
+  bool bases = false;  // records carry weight-table offsets (footprints move < kTabMargin cells)
 };
 
 // Tile list entries: each listed baseline once per warp tile its footprint, or
 // its mirror's, can touch in the gridded half plane in some channel of the
 // call.  Over a coarse channel a footprint moves by at most a cell, so a
-// baseline touches 6 tiles of 4 x 8 (a footprint straddling row G/2 up to 6
-// more through its mirror; at most 16 when its centre moves by a few cells).
+// baseline touches 6 to 9 tiles of 4 x 4 (a footprint straddling row G/2 up to
+// as many more through its mirror).
 constexpr int kEntriesPerBaseline = 24;
 long long entry_capacity(const ImgPlan& p) { return std::max<long long>(1, p.n_cross * kEntriesPerBaseline); }
 
@@ -771,7 +848,7 @@ long long centre_cell_host(long long p) {
 // every channel lie between those at the smallest and the largest scale.
 void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double* freq, int n_chan,
                    double cell, double uv_min, double uv_max, std::vector<GridEntry>& listed,
-                   std::vector<int>& idx, std::vector<int>& off) {
+                   std::vector<int>& idx, std::vector<int>& off, long long* spread) {
   const double du = 1.0 / (static_cast<double>(p.g) * cell);
   double s_lo = HUGE_VAL, s_hi = -HUGE_VAL, fmin = freq[0], fmax = freq[0];
   for (int f = 0; f < n_chan; ++f) {
@@ -786,10 +863,15 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
   const long long cmax = p.g / 2 - kHalfSup - 1;
   const int ntu = n_tiles_u(p.g), nt = n_tiles(p.g);
   std::vector<std::vector<int>> tiles(nt);
+  // the centre cells over the call's channels; *spread: the most any listed
+  // footprint moves across them
+  *spread = 0;
+  long long move = 0;
   auto cells = [&](double d, long long& lo, long long& hi) {
     const long long a = centre_cell_host(std::llrint(d * s_lo)), b = centre_cell_host(std::llrint(d * s_hi));
     lo = std::max(std::min(a, b), -cmax);
     hi = std::min(std::max(a, b), cmax);
+    move = std::max(move, a > b ? a - b : b - a);
     return lo <= hi;
   };
   listed.clear();
@@ -798,6 +880,7 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
     for (int b = a + 1; b < n_ant; ++b, ++cross) {
       const double dx = ant[3 * a] - ant[3 * b], dy = ant[3 * a + 1] - ant[3 * b + 1];
       long long u0, u1, v0, v1;
+      move = 0;
       if (!cells(dx, u0, u1) || !cells(dy, v0, v1)) continue;       // never on the grid
       // uv range: decided here when every channel of the call agrees (with a
       // relative margin), per channel on the device otherwise
@@ -819,6 +902,7 @@ void build_entries(const ImgPlan& p, int n_ant, const double* ant, const double*
       e.dyl = static_cast<float>(dy - static_cast<double>(e.dyh));
       const int li = static_cast<int>(listed.size());
       listed.push_back(e);
+      *spread = std::max(*spread, move);
       // footprint rows / columns over the call (centre +- 3 cells), of the
       // record and of its mirror, within the gridded rows G/2 .. G-1
       auto add = [&](long long vl, long long vh, long long ul, long long uh, int flag) {
@@ -853,20 +937,18 @@ int launch_batch(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int3
     if (w.n_listed > 0) {
       dim3 grid((w.n_listed + 8 * kPrepPerWarp - 1) / (8 * kPrepPerWarp), n_groups);
       OVRO_PROF("k_grid_prep", st);
-      if (cal)
-        k_grid_prep<L, true><<<grid, 256, 0, st>>>(w.listed, w.n_listed, vis, n_bl, w.base, w.cs, ch0, nb, w.kept,
-                                                   w.prep, o);
-      else
-        k_grid_prep<L, false><<<grid, 256, 0, st>>>(w.listed, w.n_listed, vis, n_bl, w.base, w.cs, ch0, nb, w.kept,
-                                                    w.prep, o);
+      auto prep = cal ? (w.bases ? k_grid_prep<L, true, true> : k_grid_prep<L, true, false>)
+                      : (w.bases ? k_grid_prep<L, false, true> : k_grid_prep<L, false, false>);
+      prep<<<grid, 256, 0, st>>>(w.listed, w.n_listed, vis, n_bl, w.base, w.cs, ch0, nb, w.kept, w.prep, o);
       OVRO_LAUNCH_CHECK();
     }
-    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_grid_tiles<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto tiles = w.bases ? k_grid_tiles<L, true> : k_grid_tiles<L, false>;
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kTileSmem)));
     const long long items = static_cast<long long>(n_groups) * n_tiles(G);
     const long long ctas = std::min<long long>(num_sms(), (items + kGridWarps - 1) / kGridWarps);
     OVRO_PROF("k_grid_tiles", st);
-    k_grid_tiles<L><<<static_cast<unsigned>(ctas), kGridWarps * 32, kTileSmem, st>>>(
+    tiles<<<static_cast<unsigned>(ctas), kGridWarps * 32, kTileSmem, st>>>(
         w.tile_idx, w.tile_off, w.tile_order, w.prep, w.n_listed, w.tabx, nb, w.grid);
     OVRO_LAUNCH_CHECK();
   }
@@ -929,9 +1011,12 @@ int upload_common(const ImgPlan& p, ImgWs& w, int n_ant, const double* h_ant,
   for (int i = 0; i < p.n; ++i) inv[i] = static_cast<float>(1.0 / corr[i]);
   std::vector<GridEntry> listed;
   std::vector<int> idx, off;
-  build_entries(p, n_ant, h_ant, h_freq, n_chan, cell, uv_min, uv_max, listed, idx, off);
+  long long spread = 0;
+  build_entries(p, n_ant, h_ant, h_freq, n_chan, cell, uv_min, uv_max, listed, idx, off, &spread);
   if (static_cast<long long>(idx.size()) > entry_capacity(p)) return OVRO_ERR_CAPACITY;
   w.n_listed = static_cast<int>(listed.size());
+  // one cell of slack for a host rounding of u Q that differs from the exact one
+  w.bases = spread + 1 <= kTabMargin;
   std::vector<double> blen(p.n_cross > 0 ? p.n_cross : 1, 0.0);
   {
     long long x = 0;

@@ -5,10 +5,11 @@
 // 8-bit X-engine.  One CTA handles one spectrum (N consecutive samples) of a
 // group of G adjacent inputs: it stages the G-byte-wide rows of packed samples
 // in shared memory, runs F FFTs at a time (Stockham auto-sort, radix-16 passes
-// through a shared exchange buffer, 16 complex values per thread in registers),
-// requantises in the last pass and writes the int8 spectra for all G inputs
-// with row-contiguous stores, so the output for fine channel k' is one
-// 2G-byte run in [k'][spectrum][input] order -- the layout the X-engine reads.
+// through a padded shared exchange buffer, 16 complex values per thread in
+// registers), requantises the bins into a staging tile and writes the int8
+// spectra for all G inputs with row-contiguous stores, so the output for fine
+// channel k' is one 2G-byte run in [k'][spectrum][input] order -- the layout
+// the X-engine reads.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -115,65 +116,102 @@ __global__ void k_twiddle(float2* tw, int n) {
 // --------------------------------------------------------- FFT + requantise
 
 
-// Radix schedule for N = 2^LOG2N: passes of 16, then one of 2^(LOG2N % 4).
+// N = 2, 4, 8: one thread per FFT (the whole transform in registers), 256
+// inputs of the group at a time.
 template <int LOG2N>
-struct Plan {
-  static constexpr int N = 1 << LOG2N;
-  static constexpr int R0 = LOG2N < 4 ? N : 16;                 // radix of the first pass
-  static constexpr int n16 = LOG2N / 4;
-  static constexpr int rem = LOG2N % 4;
-  static constexpr int n_pass = LOG2N < 4 ? 1 : n16 + (rem ? 1 : 0);
-  static constexpr int VPT = R0;                                // values per thread per pass
-  static constexpr int F = (LOG2N >= 13) ? 1 : (LOG2N < 4 ? 256 : (8192 >> LOG2N));  // FFTs in flight
-  static constexpr int THREADS = F * N / VPT;
-};
-
-template <int R, int VPT>
-__device__ __forceinline__ void radix_pass_compute(float2 (&val)[VPT], int N, int Ns, int j0,
-                                                   int jstep, const float2* __restrict__ tw,
-                                                   int tw_stride) {
-  // val holds VPT / R butterflies, butterfly b at val[b*R .. b*R+R)
-#pragma unroll
-  for (int b = 0; b < VPT / R; ++b) {
-    const int j = j0 + b * jstep;
-    const int k = j & (Ns - 1);
-    float2 v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = val[b * R + r];
-    if (Ns > 1) {
-      const int base = k * (N / (Ns * R));
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + static_cast<long long>(r * base) * tw_stride));
+__global__ void __launch_bounds__(256)
+k_upchan(UpchanArgs a) {
+  constexpr int N = 1 << LOG2N;
+  static_assert(N < 16, "short transforms only");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int G = a.group;
+  uint8_t* raw = smem;                                                          // [N][G]
+  int8_t* stg = reinterpret_cast<int8_t*>(raw + static_cast<size_t>(N) * G);    // [N][G][2]
+  float* sc = reinterpret_cast<float*>(
+      stg + ((static_cast<size_t>(N) * G * 2 + 15) & ~static_cast<size_t>(15)));  // [G]
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
+  const int s = blockIdx.y;
+  const int i0 = blockIdx.x * G;
+  const int gv = min(G, a.n_input - i0);
+  const long long row0 = static_cast<long long>(s) * N;
+  {
+    const uint8_t* src = a.volt + row0 * a.n_input + i0;
+    for (int idx = tid; idx < N * G; idx += T) {
+      const int n = idx / G, g = idx - n * G;
+      raw[idx] = g < gv ? src[static_cast<long long>(n) * a.n_input + g] : 0;
     }
-    dft_reg<R>(v);
+    for (int g = tid; g < G; g += T) sc[g] = g < gv ? a.scale[i0 + g] : 0.0f;
+  }
+  __syncthreads();
+  for (int g = tid; g < gv; g += T) {
+    float2 v[N];
 #pragma unroll
-    for (int r = 0; r < R; ++r) val[b * R + r] = v[r];
+    for (int n = 0; n < N; ++n) {
+      const uint32_t byte = raw[n * G + g];
+      v[n].x = static_cast<float>(static_cast<int>(static_cast<int8_t>(byte)) >> 4);
+      v[n].y = static_cast<float>(static_cast<int>(static_cast<int8_t>(byte << 4)) >> 4);
+    }
+    dft_reg<N>(v);
+    const float s_g = sc[g];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int kp = (k + N / 2) & (N - 1);
+      float qr = rintf(__fmul_rn(s_g, v[k].x));
+      float qi = rintf(__fmul_rn(s_g, v[k].y));
+      qr = fminf(fmaxf(qr, -127.f), 127.f);
+      qi = fminf(fmaxf(qi, -127.f), 127.f);
+      char2 q2;
+      q2.x = static_cast<signed char>(qr);
+      q2.y = static_cast<signed char>(qi);
+      reinterpret_cast<char2*>(stg)[kp * G + g] = q2;
+      if (a.out_f) {
+        const long long o = ((static_cast<long long>(kp) * a.n_spec + s) * a.n_input + i0 + g);
+        reinterpret_cast<float2*>(a.out_f)[o] = v[k];
+      }
+    }
+  }
+  __syncthreads();
+  int8_t* dst0 = a.out_q + (static_cast<long long>(s) * a.n_input + i0) * 2;
+  const long long row_stride = static_cast<long long>(a.n_spec) * a.n_input * 2;
+  for (int idx = tid; idx < N * gv; idx += T) {
+    const int kp = idx / gv, g = idx - kp * gv;
+    *reinterpret_cast<char2*>(dst0 + kp * row_stride + 2 * g) = reinterpret_cast<const char2*>(stg)[kp * G + g];
   }
 }
 
+// Radix-16 Stockham kernel for N = 2^LOG2N >= 16 (fft.cuh's row passes): F
+// FFTs of the group in flight (F N = 8192 points, 16 per thread; one FFT of
+// 16384), exchange rows padded by one slot per 16 so the stride-16 writes of
+// a pass hit distinct banks, every index split a shift.  The first pass
+// unpacks the staged 4+4-bit samples; the bins come out in natural order and
+// are requantised, fftshifted, into the staging rows.
 template <int LOG2N>
-__global__ void __launch_bounds__(Plan<LOG2N>::THREADS)
-k_upchan(UpchanArgs a) {
-  using P = Plan<LOG2N>;
-  constexpr int N = P::N;
-  constexpr int VPT = P::VPT;
-  constexpr int F = P::F;
+struct P2Plan {
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int F = N >= 8192 ? 1 : 8192 / N;
+  static constexpr int THREADS = F * N / 16;
+  static constexpr int LDP = N + N / 16;             // pad16(x) < LDP for x < N
+};
+
+template <int LOG2N>
+__global__ void __launch_bounds__(P2Plan<LOG2N>::THREADS, 1024 / P2Plan<LOG2N>::THREADS)
+k_upchan_p2(UpchanArgs a) {
+  using P = P2Plan<LOG2N>;
+  constexpr int N = P::N, F = P::F, LDP = P::LDP;
   extern __shared__ __align__(16) unsigned char smem[];
   const int G = a.group;
-  float2* buf = reinterpret_cast<float2*>(smem);                       // [F][N]
-  uint8_t* raw = smem + static_cast<size_t>(F) * N * sizeof(float2);   // [N][G]
-  int8_t* stg = reinterpret_cast<int8_t*>(raw + static_cast<size_t>(N) * G);  // [N][G][2]
+  float2* buf = reinterpret_cast<float2*>(smem);                                 // [F][LDP]
+  uint8_t* raw = smem + static_cast<size_t>(F) * LDP * sizeof(float2);           // [N][G]
+  int8_t* stg = reinterpret_cast<int8_t*>(raw + static_cast<size_t>(N) * G);     // [N][G][2]
   float* sc = reinterpret_cast<float*>(
       stg + ((static_cast<size_t>(N) * G * 2 + 15) & ~static_cast<size_t>(15)));  // [G]
-
   const int tid = threadIdx.x;
   const int T = blockDim.x;
   const int s = blockIdx.y;
   const int i0 = blockIdx.x * G;
   const int gv = min(G, a.n_input - i0);        // valid inputs in this group
   const long long row0 = static_cast<long long>(s) * N;
-
-  // stage the packed rows
   {
     const uint8_t* src = a.volt + row0 * a.n_input + i0;
     if (gv == G && (G % 4) == 0 && (a.n_input % 4) == 0) {
@@ -192,179 +230,45 @@ k_upchan(UpchanArgs a) {
     for (int g = tid; g < G; g += T) sc[g] = g < gv ? a.scale[i0 + g] : 0.0f;
   }
   __syncthreads();
-
   const int tw_stride = a.tw_n / N;
-  constexpr int BPT = VPT / P::R0;                      // butterflies per thread (first pass)
+  auto tw = [&](int i) { return __ldg(a.tw + static_cast<long long>(i) * tw_stride); };
   for (int f0 = 0; f0 < G; f0 += F) {
-    // ---- pass 0: from the packed samples
-    float2 val[VPT];
-    int Ns = 1;
-    {
-      constexpr int R = P::R0;
-      // thread -> (fft f, butterfly j); F*N/R butterflies, BPT per thread
-      const int per_fft = N / R;
-#pragma unroll
-      for (int b = 0; b < BPT; ++b) {
-        const int gb = tid + b * T;
-        const int f = gb / per_fft, j = gb - f * per_fft;
-        const int g = f0 + f;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          float2 x = make_float2(0.f, 0.f);
-          if (f < F && g < G) {
-            const uint32_t byte = raw[(j + r * per_fft) * G + g];
-            x.x = static_cast<float>(static_cast<int>(static_cast<int8_t>(byte)) >> 4);
-            x.y = static_cast<float>(static_cast<int>(static_cast<int8_t>(byte << 4)) >> 4);
+    fft_rows_inplace_f<LOG2N>(
+        buf, LDP,
+        [&](int f, int x) {
+          // high nibble real, low nibble imaginary (two's complement)
+          float2 v = make_float2(0.f, 0.f);
+          const int g = f0 + f;
+          if (g < G) {
+            const uint32_t byte = raw[x * G + g];
+            v.x = static_cast<float>(static_cast<int>(static_cast<int8_t>(byte)) >> 4);
+            v.y = static_cast<float>(static_cast<int>(static_cast<int8_t>(byte << 4)) >> 4);
           }
-          val[b * R + r] = x;
-        }
-      }
-      // all butterflies in this thread share the same j layout rule
-#pragma unroll
-      for (int b = 0; b < BPT; ++b) {
-        const int gb = tid + b * T;
-        const int j = gb % (N / R);
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = val[b * R + r];
-        dft_reg<R>(v);
-#pragma unroll
-        for (int r = 0; r < R; ++r) val[b * R + r] = v[r];
-        (void)j;
+          return v;
+        },
+        tw);
+    for (int idx = tid; idx < F * N; idx += T) {
+      const int f = idx >> LOG2N, k = idx & (N - 1);
+      const int g = f0 + f;
+      if (g >= gv) continue;
+      const float2 X = buf[f * LDP + pad16(k)];
+      const float s_g = sc[g];
+      const int kp = (k + N / 2) & (N - 1);
+      float qr = rintf(__fmul_rn(s_g, X.x));
+      float qi = rintf(__fmul_rn(s_g, X.y));
+      qr = fminf(fmaxf(qr, -127.f), 127.f);
+      qi = fminf(fmaxf(qi, -127.f), 127.f);
+      char2 q2;
+      q2.x = static_cast<signed char>(qr);
+      q2.y = static_cast<signed char>(qi);
+      reinterpret_cast<char2*>(stg)[kp * G + g] = q2;
+      if (a.out_f) {
+        const long long o = ((static_cast<long long>(kp) * a.n_spec + s) * a.n_input + i0 + g);
+        reinterpret_cast<float2*>(a.out_f)[o] = X;
       }
     }
-
-    // ---- write pass-0 results (or finish if single pass), then middle passes
-    auto store_pass = [&](int R, int Ns_cur) {
-      const int per_fft = N / R;
-      const int nb = VPT / R;
-      for (int b = 0; b < nb; ++b) {
-        const int gb = tid + b * T;
-        const int f = gb / per_fft, j = gb - f * per_fft;
-        if (f >= F) continue;
-        const int k = j & (Ns_cur - 1);
-        const int dst = (j / Ns_cur) * Ns_cur * R + k;
-        for (int r = 0; r < R; ++r) buf[f * N + dst + r * Ns_cur] = val[b * R + r];
-      }
-    };
-    auto load_pass = [&](int R) {
-      const int per_fft = N / R;
-      const int nb = VPT / R;
-      for (int b = 0; b < nb; ++b) {
-        const int gb = tid + b * T;
-        const int f = gb / per_fft, j = gb - f * per_fft;
-        for (int r = 0; r < R; ++r)
-          val[b * R + r] = f < F ? buf[f * N + j + r * per_fft] : make_float2(0.f, 0.f);
-      }
-    };
-
-    // requantise + stage: butterfly outputs at natural bins, fftshifted
-    auto emit = [&](int R, int Ns_cur) {
-      const int per_fft = N / R;
-      const int nb = VPT / R;
-      for (int b = 0; b < nb; ++b) {
-        const int gb = tid + b * T;
-        const int f = gb / per_fft, j = gb - f * per_fft;
-        const int g = f0 + f;
-        if (f >= F || g >= gv) continue;
-        const float s_g = sc[g];
-        const int k = j & (Ns_cur - 1);
-        const int q0 = (j / Ns_cur) * Ns_cur * R + k;
-        for (int r = 0; r < R; ++r) {
-          const int kp = (q0 + r * Ns_cur + N / 2) & (N - 1);
-          const float2 X = val[b * R + r];
-          float qr = rintf(__fmul_rn(s_g, X.x));
-          float qi = rintf(__fmul_rn(s_g, X.y));
-          qr = fminf(fmaxf(qr, -127.f), 127.f);
-          qi = fminf(fmaxf(qi, -127.f), 127.f);
-          char2 q2;
-          q2.x = static_cast<signed char>(qr);
-          q2.y = static_cast<signed char>(qi);
-          reinterpret_cast<char2*>(stg)[kp * G + g] = q2;
-          if (a.out_f) {
-            const long long o = ((static_cast<long long>(kp) * a.n_spec + s) * a.n_input + i0 + g);
-            reinterpret_cast<float2*>(a.out_f)[o] = X;
-          }
-        }
-      }
-    };
-
-    if (P::n_pass == 1) {
-      emit(P::R0, 1);
-    } else {
-      store_pass(P::R0, 1);
-      Ns = P::R0;
-      __syncthreads();
-      for (int p = 1; p < P::n_pass; ++p) {
-        const bool last = (p == P::n_pass - 1);
-        const int R = (p < P::n16) ? 16 : (1 << P::rem);
-        load_pass(R);
-        __syncthreads();
-        const int per_fft = N / R;
-        switch (R) {
-          case 16: {
-            float2 v16[VPT];
-#pragma unroll
-            for (int i = 0; i < VPT; ++i) v16[i] = val[i];
-            const int gb0 = tid;
-            radix_pass_compute<16, VPT>(v16, N, Ns, gb0 % per_fft, T, a.tw, tw_stride);
-#pragma unroll
-            for (int i = 0; i < VPT; ++i) val[i] = v16[i];
-            break;
-          }
-          case 8: {
-            for (int b = 0; b < VPT / 8; ++b) {
-              const int j = (tid + b * T) % per_fft;
-              float2 v[8];
-#pragma unroll
-              for (int r = 0; r < 8; ++r) v[r] = val[b * 8 + r];
-              float2 vv[8];
-#pragma unroll
-              for (int r = 0; r < 8; ++r) vv[r] = v[r];
-              radix_pass_compute<8, 8>(vv, N, Ns, j, 0, a.tw, tw_stride);
-#pragma unroll
-              for (int r = 0; r < 8; ++r) val[b * 8 + r] = vv[r];
-            }
-            break;
-          }
-          case 4: {
-            for (int b = 0; b < VPT / 4; ++b) {
-              const int j = (tid + b * T) % per_fft;
-              float2 vv[4];
-#pragma unroll
-              for (int r = 0; r < 4; ++r) vv[r] = val[b * 4 + r];
-              radix_pass_compute<4, 4>(vv, N, Ns, j, 0, a.tw, tw_stride);
-#pragma unroll
-              for (int r = 0; r < 4; ++r) val[b * 4 + r] = vv[r];
-            }
-            break;
-          }
-          default: {
-            for (int b = 0; b < VPT / 2; ++b) {
-              const int j = (tid + b * T) % per_fft;
-              float2 vv[2];
-              vv[0] = val[b * 2];
-              vv[1] = val[b * 2 + 1];
-              radix_pass_compute<2, 2>(vv, N, Ns, j, 0, a.tw, tw_stride);
-              val[b * 2] = vv[0];
-              val[b * 2 + 1] = vv[1];
-            }
-            break;
-          }
-        }
-        if (last) {
-          emit(R, Ns);
-        } else {
-          store_pass(R, Ns);
-          __syncthreads();
-        }
-        Ns *= R;
-      }
-    }
-    __syncthreads();   // buf reused by the next group of F inputs
+    __syncthreads();   // buf reused by the next F inputs; stg complete
   }
-
-  // ---- write the staged int8 spectra: row k' is 2*gv contiguous bytes
   {
     int8_t* dst0 = a.out_q + (static_cast<long long>(s) * a.n_input + i0) * 2;
     const long long row_stride = static_cast<long long>(a.n_spec) * a.n_input * 2;
@@ -385,14 +289,22 @@ k_upchan(UpchanArgs a) {
   }
 }
 
-int group_for(int log2n, int n_input) {
-  // G inputs per CTA so that raw (G N) + staging (2 G N) + exchange (8 F N) fit.
+size_t smem_p2(int log2n, int G) {
   const int N = 1 << log2n;
+  const int F = N >= 8192 ? 1 : 8192 / N;
+  return static_cast<size_t>(F) * (N + N / 16) * 8 + static_cast<size_t>(N) * G +
+         ((static_cast<size_t>(N) * G * 2 + 15) & ~static_cast<size_t>(15)) + 4 * G + 16;
+}
+
+size_t smem_for(int log2n, int G);
+
+int group_for(int log2n, int n_input) {
+  // G inputs per CTA: the most whose shared memory (raw G N + staging 2 G N +
+  // exchange) leaves room for two CTAs per SM, at least F
   const int F = log2n >= 13 ? 1 : (log2n < 4 ? 256 : (8192 >> log2n));
-  const size_t budget = 200 * 1024;
-  const size_t xbuf = static_cast<size_t>(F) * N * 8;
+  const size_t budget = log2n < 4 ? 200 * 1024 : 110 * 1024;
   int G = 1;
-  while (G < 64 && (xbuf + 3ull * (2 * G) * N + 4 * 2 * G) <= budget) G *= 2;
+  while (G < 64 && smem_for(log2n, 2 * G) <= budget) G *= 2;
   if (G < F) G = F;
   int np2 = 1;
   while (np2 < n_input) np2 *= 2;
@@ -401,22 +313,27 @@ int group_for(int log2n, int n_input) {
 }
 
 size_t smem_for(int log2n, int G) {
+  if (log2n >= 4) return smem_p2(log2n, G);
   const int N = 1 << log2n;
-  const int F = log2n >= 13 ? 1 : (log2n < 4 ? 256 : (8192 >> log2n));
-  return static_cast<size_t>(F) * N * 8 + static_cast<size_t>(N) * G +
-         ((static_cast<size_t>(N) * G * 2 + 15) & ~static_cast<size_t>(15)) + 4 * G + 16;
+  return static_cast<size_t>(N) * G + ((static_cast<size_t>(N) * G * 2 + 15) & ~static_cast<size_t>(15)) + 4 * G +
+         16;
 }
 
 template <int L>
 int launch_upchan_t(const UpchanArgs& a, cudaStream_t st) {
-  using P = Plan<L>;
   const size_t sm = smem_for(L, a.group);
-  auto kern = k_upchan<L>;
-  OVRO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(sm)));
   dim3 grid((a.n_input + a.group - 1) / a.group, a.n_spec);
-  OVRO_PROF("k_upchan", st);
-  kern<<<grid, P::THREADS, sm, st>>>(a);
+  if constexpr (L >= 4) {
+    auto kern = k_upchan_p2<L>;
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    OVRO_PROF("k_upchan", st);
+    kern<<<grid, P2Plan<L>::THREADS, sm, st>>>(a);
+  } else {
+    auto kern = k_upchan<L>;
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    OVRO_PROF("k_upchan", st);
+    kern<<<grid, 256, sm, st>>>(a);
+  }
   OVRO_LAUNCH_CHECK();
   return OVRO_OK;
 }
