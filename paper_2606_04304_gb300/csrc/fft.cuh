@@ -178,9 +178,22 @@ __device__ __forceinline__ void stockham_pass(float2* a, int ldp, Load&& load, T
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = v[b * R + r];
     if (NS > 1) {
+      // twiddles w^r, w = omega_G^base: w^(2^m) read, the others products of
+      // those (at most three roundings deep), so a pass reads log2 R of them
       const int base = k * (G / (NS * R));
+      float2 t[R];
+      t[1] = tw(base);
+      if (R >= 4) t[2] = tw(2 * base);
+      if (R >= 8) t[4] = tw(4 * base);
+      if (R >= 16) t[8] = tw(8 * base);
 #pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], tw(r * base));
+      for (int r = 3; r < R; ++r) {
+        if ((r & (r - 1)) == 0) continue;
+        const int hb = 1 << (31 - __clz(r));            // highest power of two in r (compile-time)
+        t[r] = cmul(t[hb], t[r - hb]);
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], t[r]);
     }
     dft_reg<R>(x);
     const int o = (j / NS) * NS * R + k;

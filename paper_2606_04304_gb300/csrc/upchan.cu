@@ -300,9 +300,10 @@ size_t smem_for(int log2n, int G);
 
 int group_for(int log2n, int n_input) {
   // G inputs per CTA: the most whose shared memory (raw G N + staging 2 G N +
-  // exchange) leaves room for two CTAs per SM, at least F
+  // exchange) fits one CTA per SM, at least F (wider groups coalesce the
+  // G-byte row reads and 2G-byte row writes)
   const int F = log2n >= 13 ? 1 : (log2n < 4 ? 256 : (8192 >> log2n));
-  const size_t budget = log2n < 4 ? 200 * 1024 : 110 * 1024;
+  const size_t budget = 200 * 1024;
   int G = 1;
   while (G < 64 && smem_for(log2n, 2 * G) <= budget) G *= 2;
   if (G < F) G = F;
