@@ -112,9 +112,11 @@ def write_traffic_table(case, csv_path, command):
     """Adds the kernels of one profiler case's ncu capture (dram__bytes_read.sum,
     dram__bytes_write.sum over every launch of the case) to
     profiles/dram_traffic.json as DRAM bytes per unit of work."""
-    # the traced name of a kernel where ncu sees another (the X-engine at K <= 32
-    # runs its channel-major variant under the traced name k_xeng_tc)
-    alias = {"k_xeng_tc2": "k_xeng_tc"}
+    # the traced name of a kernel where ncu sees another (the X-engine variants,
+    # the upchannelizer's radix-16 kernel and the band ranks are traced under
+    # the stage's kernel name)
+    alias = {"k_xeng_tc2": "k_xeng_tc", "k_xeng_tc3": "k_xeng_tc", "k_upchan_p2": "k_upchan",
+             "k_rank_band": "k_rank"}
     rows = [(lid, alias.get(k, k), m, v) for lid, k, m, v in _ncu_rows(csv_path)]
     if not rows:
         raise SystemExit(f"no kernel metrics in {csv_path}")

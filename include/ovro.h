@@ -177,7 +177,9 @@ int ovro_upchan_noalloc(const uint8_t* d_volt, int n_input, int n_coarse, int64_
  *           bound).  Both are bit-exact integer results.
  * Errors:   OVRO_ERR_OVERFLOW if 2 * 128^2 * n_spec >= 2^24 (n_spec > 511):
  *           the bound holds for any int8 input, -128 included,
- *           OVRO_ERR_UNSUPPORTED if n_ant > 4096.
+ *           OVRO_ERR_UNSUPPORTED if n_ant > 4096,
+ *           OVRO_ERR_INVALID_ARG if d_fine_q is not 4-byte aligned or d_vis
+ *           not 16-byte aligned.
  * ------------------------------------------------------------------------- */
 enum { OVRO_XENG_TC = 0, OVRO_XENG_FP32 = 1 };
 int ovro_correlate(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec, int mode,

@@ -7,20 +7,21 @@
 //  * k_xeng_simt: plain FP32 SIMT accumulation, 2x2 antennas x 2x2 pols per
 //    thread (exact: every partial sum is an integer below 2^24).
 //
-//  * k_xeng_tc: 5th-generation tensor cores.  sm_103a has no integer MMA
-//    (tcgen05 .kind::i8 is rejected by ptxas for this target), so the int8
-//    values are carried exactly in FP16 operands and accumulated in FP32 in
-//    tensor memory; every int8 value has |q| <= 128, so each spectrum adds at
-//    most 2 * 128^2 = 2^15 to a sum and every partial sum stays an integer
-//    below 2^24 for K <= 511: the result is exact.  The Hermitian product becomes
-//    one real GEMM: A row i = X_i = (re_i(s), im_i(s))_s, B rows 2j, 2j+1 =
-//    X_j and Z_j = (-im_j(s), re_j(s))_s, so D[i][2j] = Re V_ij and
-//    D[i][2j+1] = Im V_ij land as adjacent TMEM columns.  One CTA per SM pair
-//    slot runs persistently over (channel, 128x128-input tile) work items of
-//    the upper triangle; one thread issues tcgen05.mma (M=128, N=256, K=16
-//    steps) from no-swizzle K-major shared-memory operands, the MMA completion
-//    is signalled through an mbarrier by tcgen05.commit, and all four warps
-//    drain their TMEM lane quarter with tcgen05.ld and store int32 records.
+//  * tensor cores (5th generation).  sm_103a has no integer MMA (tcgen05
+//    .kind::i8 is rejected by ptxas for this target), so the int8 values are
+//    carried exactly in FP16 operands and accumulated in FP32 in tensor
+//    memory; every int8 value has |q| <= 128, so each spectrum adds at most
+//    2 * 128^2 = 2^15 to a sum and every partial sum stays an integer below
+//    2^24 for K <= 511: the result is exact.  The Hermitian product becomes one
+//    real GEMM: A row i = X_i = (re_i(s), im_i(s))_s, B rows j and 128 + j of
+//    a 128-input tile = X_j and Z_j = (-im_j(s), re_j(s))_s, so D[i][j] =
+//    Re V_ij and D[i][128 + j] = Im V_ij.  One thread issues tcgen05.mma
+//    (M = 128, N = 256, K = 16 steps) from no-swizzle K-major shared-memory
+//    operands, completions are signalled through mbarriers by tcgen05.commit,
+//    and warps drain TMEM lane quarters with tcgen05.ld into int32 records.
+//    k_xeng_tc2 (K <= 32, up to 768 inputs) converts a channel's spectra once
+//    and runs all its tile pairs; k_xeng_tc3 streams the spectra of each tile
+//    pair through shared memory with warp-specialised roles.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -120,8 +121,6 @@ constexpr int kTcInputsN = 128;           // column inputs per tile -> N = 256
 constexpr int kTcN = 2 * kTcInputsN;
 constexpr int kTcKc = 64;                 // FP16 K elements per chunk (32 spectra)
 constexpr int kTcSpecPerChunk = kTcKc / 2;
-constexpr int kTmemCols = 256;
-constexpr int kTcThreads = 128;
 constexpr uint32_t kLBO = 128;            // bytes between K-adjacent core matrices
 constexpr uint32_t kSBO = (kTcKc / 8) * 128;  // bytes between 8-row groups
 constexpr int kTcASmem = kTcM * kTcKc * 2;    // 16 KB
@@ -169,29 +168,89 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   }
 }
 
-__global__ void __launch_bounds__(kTcThreads)
-k_xeng_tc(const int8_t* __restrict__ q, int n_ant, int n_spec, int n_tiles, int n_pairs,
-          long long n_items, int32_t* __restrict__ vis) {
+// ------------------------------------------- tcgen05 path, streamed spectra
+// For more than 32 spectra (or larger arrays) the operands of a tile pair are
+// streamed through shared memory in chunks of 32 spectra, with the roles of a
+// CTA's warps split so that the tensor pipe never waits on the SIMT work:
+//   warps 0-7 (converters): thread t owns operand rows 2 (t % 64) and
+//     2 (t % 64) + 1 of the pair and quarter t / 64 of a chunk's spectra; it
+//     reads its inputs' int8 spectra four chunks ahead into registers (4-byte
+//     loads, 128 contiguous bytes per warp and spectrum) while converting a
+//     chunk into FP16 A and [X; Z] B rows of a free stage (exactly: the byte
+//     with its sign bit flipped is the low byte of the FP16 number
+//     1024 + 128 + q, and one packed subtraction of 1152 leaves q; 16-byte
+//     shared stores), then arrives on that stage's full barrier;
+//   warp 12 lane 0 (MMA): per chunk waits for a full stage, issues the four
+//     K = 16 MMAs into the item's accumulator and commits them to the stage's
+//     empty barrier (and, after the item's last chunk, to the accumulator's
+//     ready barrier);
+//   warps 8-11 (epilogue): drain an item's accumulator (TMEM lane quarter
+//     warp % 4) into int32 records and arrive on its free barrier.
+// Three operand stages (48 KB each) and two 256-column accumulators, so the
+// epilogue of item i runs under the MMAs of item i + 1.  Every wait is bounded
+// (1 s); a timeout sets the status word and a shared abort flag that every
+// role polls, and the kernel waits (bounded) for its MMAs before freeing TMEM.
+constexpr int kT3Stages = 3;
+constexpr int kT3StageBytes = kTcASmem + 2 * kTcASmem;     // A 16 KB + B 32 KB
+constexpr int kT3ConvThreads = 256;                        // warps 0-7
+constexpr int kT3Threads = 416;                            // 13 warps
+constexpr int kT3MmaWarp = 12;
+constexpr int kT3SpecPerThread = kTcSpecPerChunk / 4;      // a converter's quarter of a chunk
+constexpr uint32_t kT3TmemCols = 512;
+
+__device__ __forceinline__ bool mbar_wait_abort(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    // the thread may be suspended up to 20 us inside try_wait (woken when the
+    // phase completes), so waiting roles take few issue slots
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(mbar), "r"(parity), "r"(20000u) : "memory");
+    if (done) return true;
+    if (*abort_flag) return false;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      atomicExch(&g_xeng_status, 1);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+
+__global__ void __launch_bounds__(kT3Threads, 1)
+k_xeng_tc3(const int8_t* __restrict__ q, int n_ant, int n_spec, int n_tiles, int n_pairs, long long n_items,
+           int32_t* __restrict__ vis) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem;                       // 16 KB
-  unsigned char* sB = smem + kTcASmem;            // 32 KB
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t full_b[kT3Stages], empty_b[kT3Stages], accf_b[2], acce_b[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
-
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int n_input = 2 * n_ant;
   const long long n_bl = static_cast<long long>(n_ant) * (n_ant + 1) / 2;
-  const uint32_t mbar_a = smem_u32(&mbar);
+  const int n_chunks = (n_spec + kTcSpecPerChunk - 1) / kTcSpecPerChunk;
+  volatile int* abort_flag = &abort_sh;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base_sh)), "r"(kTmemCols) : "memory");
+                 :: "r"(smem_u32(&tmem_base_sh)), "r"(kT3TmemCols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar_a) : "memory");
+    for (int s = 0; s < kT3Stages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full_b[s])), "r"(kT3ConvThreads)
+                   : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty_b[s])) : "memory");
+    }
+    for (int a = 0; a < 2; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&accf_b[a])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&acce_b[a])), "r"(kTcM) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_sh = 0;
   }
@@ -199,118 +258,245 @@ k_xeng_tc(const int8_t* __restrict__ q, int n_ant, int n_spec, int n_tiles, int 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
-  uint32_t phase = 0;
 
-  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int ch = static_cast<int>(item / n_pairs);
-    int p = static_cast<int>(item - static_cast<long long>(ch) * n_pairs), I = 0;
+  auto pair_of = [&](long long item, int& ch, int& I, int& J) {
+    ch = static_cast<int>(item / n_pairs);
+    int p = static_cast<int>(item - static_cast<long long>(ch) * n_pairs);
+    I = 0;
     while (p >= n_tiles - I) { p -= n_tiles - I; ++I; }
-    const int J = I + p;
-    const int8_t* qc = q + static_cast<long long>(ch) * n_spec * n_input * 2;
+    J = I + p;
+  };
 
-    // ---- operands: A row t = X_{I*128+t}; B rows 2t, 2t+1 = X_j, Z_j, j = J*128+t.
-    // A chunk's 2 x 32 int8 pairs per thread are read with one round trip, and
-    // the next chunk's reads are issued while this chunk's MMAs run.
-    const int ia = I * kTcM + tid;
-    const int ib = J * kTcInputsN + tid;
-    uint32_t va[kTcSpecPerChunk], vb[kTcSpecPerChunk];   // (re, im) int8 pairs, 16 bits used
-    auto read_chunk = [&](int s0) {
+  if (warp < kT3ConvThreads / 32) {
+    // ---------------------------------------------------------- converters
+    const int pr = tid & 63;                           // operand rows 2 pr, 2 pr + 1
+    const int qq = tid >> 6;                           // spectra 8 qq .. 8 qq + 7 of a chunk
+    // this CTA's chunks in order (chunk gg is chunk gg % n_chunks of its item
+    // gg / n_chunks); the reads run four chunks ahead of the conversion
+    // (register sets 0-3), from a read cursor that moves to the next item's
+    // rows once per item
+    const int my_items = static_cast<int>((n_items - blockIdx.x + gridDim.x - 1) / gridDim.x);
+    const int total = my_items * n_chunks;
+    const int stride = n_input / 2;                    // 4-byte words per spectrum row
+    int rd_it = 0, rd_c = 0;                           // read cursor: item, chunk
+    const uint32_t* rd_a = nullptr;                    // word of inputs ia, ia + 1 in spectrum 8 qq of the item
+    const uint32_t* rd_b = nullptr;
+    bool rd_oka = false, rd_okb = false;
+    auto rd_item = [&]() {
+      rd_oka = rd_okb = false;
+      if (rd_it >= my_items) return;
+      int ch, I, J;
+      pair_of(blockIdx.x + static_cast<long long>(rd_it) * gridDim.x, ch, I, J);
+      const int ia = I * kTcM + 2 * pr, ib = J * kTcInputsN + 2 * pr;
+      const uint32_t* base = reinterpret_cast<const uint32_t*>(q + static_cast<long long>(ch) * n_spec * n_input * 2) +
+                             static_cast<long long>(qq * kT3SpecPerThread) * stride;
+      rd_a = base + ia / 2;
+      rd_b = base + ib / 2;
+      rd_oka = ia < n_input;
+      rd_okb = ib < n_input;
+    };
+    rd_item();
+    uint32_t va0[kT3SpecPerThread], vb0[kT3SpecPerThread], va1[kT3SpecPerThread], vb1[kT3SpecPerThread];
+    uint32_t va2[kT3SpecPerThread], vb2[kT3SpecPerThread], va3[kT3SpecPerThread], vb3[kT3SpecPerThread];
+    auto read_next = [&](uint32_t (&va)[kT3SpecPerThread], uint32_t (&vb)[kT3SpecPerThread]) {
+      // spectra valid in this thread's eighth of the chunk (0 past the last item)
+      const int nv = rd_it < my_items ? n_spec - (rd_c * kTcSpecPerChunk + qq * kT3SpecPerThread) : 0;
+      const uint32_t* pa = rd_a + static_cast<long long>(rd_c * kTcSpecPerChunk) * stride;
+      const uint32_t* pb = rd_b + static_cast<long long>(rd_c * kTcSpecPerChunk) * stride;
 #pragma unroll
-      for (int ss = 0; ss < kTcSpecPerChunk; ++ss) {
-        const int s = s0 + ss;
-        const uint16_t* row = reinterpret_cast<const uint16_t*>(qc + static_cast<long long>(s) * n_input * 2);
-        va[ss] = (s < n_spec && ia < n_input) ? __ldg(row + ia) : 0u;
-        vb[ss] = (s < n_spec && ib < n_input) ? __ldg(row + ib) : 0u;
+      for (int ss = 0; ss < kT3SpecPerThread; ++ss) {
+        va[ss] = (ss < nv && rd_oka) ? __ldg(pa) : 0u;
+        vb[ss] = (ss < nv && rd_okb) ? __ldg(pb) : 0u;
+        pa += stride;
+        pb += stride;
+      }
+      if (++rd_c == n_chunks) {
+        rd_c = 0;
+        ++rd_it;
+        rd_item();
       }
     };
-    read_chunk(0);
-    for (int s0 = 0; s0 < n_spec; s0 += kTcSpecPerChunk) {
+    // (re, im) int8 pairs -> FP16 pairs, exact: with the sign bits flipped
+    // each byte is the low byte of the FP16 number 1024 + 128 + q (high byte
+    // 0x64), and one packed subtraction of 1152 leaves q
+    const __half2 k1152 = __float2half2_rn(1152.0f);
+    auto to_h2 = [&](uint32_t x, uint32_t sel) {
+      const uint32_t w = __byte_perm(x, 0x64646464u, sel);
+      const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&w), k1152);
+      return *reinterpret_cast<const uint32_t*>(&h);
+    };
+    // this thread's operand rows: byte offsets within a stage at K = 0
+    const uint32_t oa0 = op_offset(2 * pr, 0), oa1 = op_offset(2 * pr + 1, 0);
+    // B rows 0..127 hold X, rows 128..255 Z (so a quarter-warp's stores fall
+    // on two rows of each 8-row core matrix group: 2-way bank conflicts)
+    const uint32_t ob0 = kTcASmem + op_offset(2 * pr, 0), ob1 = kTcASmem + op_offset(kTcInputsN + 2 * pr, 0);
+    const uint32_t ob2 = kTcASmem + op_offset(2 * pr + 1, 0), ob3 = kTcASmem + op_offset(kTcInputsN + 2 * pr + 1, 0);
+    // convert chunk gg into its stage once the stage is free
+    auto convert = [&](int gg, const uint32_t (&va)[kT3SpecPerThread], const uint32_t (&vb)[kT3SpecPerThread]) {
+      const int s = gg % kT3Stages;
+      const uint32_t use = static_cast<uint32_t>(gg / kT3Stages);
+      if (!mbar_wait_abort(smem_u32(&empty_b[s]), (use & 1u) ^ 1u, abort_flag)) return false;
+      unsigned char* st = smem + s * kT3StageBytes;
 #pragma unroll
-      for (int ss = 0; ss < kTcSpecPerChunk; ++ss) {
-        const short ar = static_cast<signed char>(va[ss] & 0xffu), ai = static_cast<signed char>(va[ss] >> 8);
-        const short br = static_cast<signed char>(vb[ss] & 0xffu), bi = static_cast<signed char>(vb[ss] >> 8);
-        const __half2 ha = __halves2half2(__short2half_rn(ar), __short2half_rn(ai));
-        const __half2 hx = __halves2half2(__short2half_rn(br), __short2half_rn(bi));
-        const __half2 hz = __halves2half2(__short2half_rn(static_cast<short>(-bi)), __short2half_rn(br));
-        *reinterpret_cast<__half2*>(sA + op_offset(tid, 2 * ss)) = ha;
-        *reinterpret_cast<__half2*>(sB + op_offset(2 * tid, 2 * ss)) = hx;
-        *reinterpret_cast<__half2*>(sB + op_offset(2 * tid + 1, 2 * ss)) = hz;
+      for (int h2 = 0; h2 < kT3SpecPerThread / 4; ++h2) {
+        // spectra 4 k .. 4 k + 3 of the chunk are K elements 8 k .. 8 k + 7:
+        // one 16-byte core-matrix row per operand row
+        uint32_t a0[4], a1[4], x0[4], x1[4], z0[4], z1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int ss = 4 * h2 + u;
+          const uint32_t xa = va[ss] ^ 0x80808080u, xb = vb[ss] ^ 0x80808080u;
+          a0[u] = to_h2(xa, 0x5140u);
+          a1[u] = to_h2(xa, 0x5342u);
+          x0[u] = to_h2(xb, 0x5140u);
+          x1[u] = to_h2(xb, 0x5342u);
+          // Z = (-im, re): the halves swapped, the new low one negated
+          z0[u] = __byte_perm(x0[u], 0u, 0x1032u) ^ 0x00008000u;
+          z1[u] = __byte_perm(x1[u], 0u, 0x1032u) ^ 0x00008000u;
+        }
+        unsigned char* sk = st + (qq * (kT3SpecPerThread / 4) + h2) * kLBO;
+        *reinterpret_cast<uint4*>(sk + oa0) = make_uint4(a0[0], a0[1], a0[2], a0[3]);
+        *reinterpret_cast<uint4*>(sk + oa1) = make_uint4(a1[0], a1[1], a1[2], a1[3]);
+        *reinterpret_cast<uint4*>(sk + ob0) = make_uint4(x0[0], x0[1], x0[2], x0[3]);
+        *reinterpret_cast<uint4*>(sk + ob1) = make_uint4(z0[0], z0[1], z0[2], z0[3]);
+        *reinterpret_cast<uint4*>(sk + ob2) = make_uint4(x1[0], x1[1], x1[2], x1[3]);
+        *reinterpret_cast<uint4*>(sk + ob3) = make_uint4(z1[0], z1[1], z1[2], z1[3]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (s0 + kTcSpecPerChunk < n_spec) read_chunk(s0 + kTcSpecPerChunk);
-      if (tid == 0) {
+      mbar_arrive(smem_u32(&full_b[s]));
+      return true;
+    };
+    read_next(va0, vb0);
+    read_next(va1, vb1);
+    read_next(va2, vb2);
+    read_next(va3, vb3);
+    for (int gg = 0; gg < total; gg += 4) {
+      // each set is refilled four chunks ahead as soon as it is converted
+      if (!convert(gg, va0, vb0)) break;
+      read_next(va0, vb0);
+      if (gg + 1 >= total) break;
+      if (!convert(gg + 1, va1, vb1)) break;
+      read_next(va1, vb1);
+      if (gg + 2 >= total) break;
+      if (!convert(gg + 2, va2, vb2)) break;
+      read_next(va2, vb2);
+      if (gg + 3 >= total) break;
+      if (!convert(gg + 3, va3, vb3)) break;
+      read_next(va3, vb3);
+    }
+  } else if (warp == kT3MmaWarp) {
+    // ------------------------------------------------------------------ MMA
+    if (lane == 0) {
+      long long g = 0;
+      int li = 0;                                      // items of this CTA so far
+      for (long long item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++li) {
+        const int a = li & 1;
+        const uint32_t ause = static_cast<uint32_t>(li >> 1);
+        if (!mbar_wait_abort(smem_u32(&acce_b[a]), (ause & 1u) ^ 1u, abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        const uint32_t d = tmem + static_cast<uint32_t>(a * 256);
+        bool ok = true;
+        for (int c = 0; c < n_chunks; ++c, ++g) {
+          const int s = static_cast<int>(g % kT3Stages);
+          const uint32_t use = static_cast<uint32_t>(g / kT3Stages);
+          if (!mbar_wait_abort(smem_u32(&full_b[s]), use & 1u, abort_flag)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(smem + s * kT3StageBytes), b0 = a0 + kTcASmem;
 #pragma unroll
-        for (int kk = 0; kk < kTcKc / 16; ++kk) {
-          const uint64_t ad = make_sdesc(a0 + kk * 2 * kLBO);
-          const uint64_t bd = make_sdesc(b0 + kk * 2 * kLBO);
-          const uint32_t acc = (s0 > 0 || kk > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-              :: "r"(tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc) : "memory");
+          for (int kk = 0; kk < kTcKc / 16; ++kk) {
+            const uint64_t ad = make_sdesc(a0 + kk * 2 * kLBO);
+            const uint64_t bd = make_sdesc(b0 + kk * 2 * kLBO);
+            const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                :: "r"(d), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc) : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       :: "r"(smem_u32(&empty_b[s])) : "memory");
         }
+        if (!ok) break;
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(mbar_a) : "memory");
+                     :: "r"(smem_u32(&accf_b[a])) : "memory");
       }
-      // all threads wait for the MMAs (operand smem is rewritten next chunk)
-      if (!mbar_wait(mbar_a, phase)) {
-        atomicExch(&g_xeng_status, 1);
-        abort_sh = 1;
+      // before TMEM is released, the MMAs this thread issued complete: the
+      // commit of its last chunk arrives (a bounded wait that ignores the
+      // abort flag, so an aborted run still drains its MMAs)
+      if (g > 0) {
+        const long long gl = g - 1;
+        (void)mbar_wait(smem_u32(&empty_b[gl % kT3Stages]), static_cast<uint32_t>(gl / kT3Stages) & 1u);
       }
-      phase ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      __syncthreads();
-      if (abort_sh) break;
     }
-    if (abort_sh) break;
-
-    // ---- epilogue: warp w drains TMEM lanes 32w..32w+31 (rows = inputs)
-    const int gi = I * kTcM + warp * 32 + lane;
-    const int a = gi >> 1, pa = gi & 1;
-    int4* out = reinterpret_cast<int4*>(vis + static_cast<long long>(ch) * n_bl * 8);
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q4 = warp & 3;
+    int li = 0;
+    for (long long item = blockIdx.x; item < n_items; item += gridDim.x, ++li) {
+      if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;    // warp-uniform
+      int ch, I, J;
+      pair_of(item, ch, I, J);
+      const int a = li & 1;
+      const uint32_t ause = static_cast<uint32_t>(li >> 1);
+      // one lane waits, the warp follows its verdict: tcgen05.ld needs the
+      // whole warp converged
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait_abort(smem_u32(&accf_b[a]), ause & 1u, abort_flag);
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int gi = I * kTcM + q4 * 32 + lane;
+      const int an = gi >> 1, pa = gi & 1;
+      int4* out = reinterpret_cast<int4*>(vis + static_cast<long long>(ch) * n_bl * 8);
+      const uint32_t tl0 = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>(a * 256);
 #pragma unroll 1
-    for (int c0 = 0; c0 < kTcN; c0 += 32) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-          "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-            "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-            "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-            "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (a < n_ant) {
-        // columns c0 .. c0+31 = column inputs j0 .. j0+15, (re, im) each
-        const int j0 = J * kTcInputsN + c0 / 2;
+      for (int cin0 = 0; cin0 < kTcInputsN; cin0 += 32) {
+        // TMEM columns cin0 .. cin0 + 31: Re of column inputs J 128 + cin0 ..;
+        // the same + 128: their Im
+        uint32_t re[32], im[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+            "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]),
+              "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]),
+              "=r"(re[14]), "=r"(re[15]), "=r"(re[16]), "=r"(re[17]), "=r"(re[18]), "=r"(re[19]),
+              "=r"(re[20]), "=r"(re[21]), "=r"(re[22]), "=r"(re[23]), "=r"(re[24]), "=r"(re[25]),
+              "=r"(re[26]), "=r"(re[27]), "=r"(re[28]), "=r"(re[29]), "=r"(re[30]), "=r"(re[31])
+            : "r"(tl0 + cin0));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+            "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]),
+              "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]),
+              "=r"(im[14]), "=r"(im[15]), "=r"(im[16]), "=r"(im[17]), "=r"(im[18]), "=r"(im[19]),
+              "=r"(im[20]), "=r"(im[21]), "=r"(im[22]), "=r"(im[23]), "=r"(im[24]), "=r"(im[25]),
+              "=r"(im[26]), "=r"(im[27]), "=r"(im[28]), "=r"(im[29]), "=r"(im[30]), "=r"(im[31])
+            : "r"(tl0 + cin0 + 128u));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (an < n_ant) {
+          const int b0 = (J * kTcInputsN + cin0) >> 1;
 #pragma unroll
-        for (int bb = 0; bb < 8; ++bb) {
-          const int b = (j0 >> 1) + bb;
-          if (b >= n_ant || b < a) continue;
-          int4 v;
-          v.x = __float2int_rn(__uint_as_float(r[4 * bb + 0]));
-          v.y = __float2int_rn(__uint_as_float(r[4 * bb + 1]));
-          v.z = __float2int_rn(__uint_as_float(r[4 * bb + 2]));
-          v.w = __float2int_rn(__uint_as_float(r[4 * bb + 3]));
-          __stcs(out + bl_index(a, b, n_ant) * 2 + pa, v);
+          for (int bb = 0; bb < 16; ++bb) {
+            const int b = b0 + bb;
+            if (b >= n_ant || b < an) continue;
+            int4 v;
+            v.x = __float2int_rn(__uint_as_float(re[2 * bb]));
+            v.y = __float2int_rn(__uint_as_float(im[2 * bb]));
+            v.z = __float2int_rn(__uint_as_float(re[2 * bb + 1]));
+            v.w = __float2int_rn(__uint_as_float(im[2 * bb + 1]));
+            __stcs(out + bl_index(an, b, n_ant) * 2 + pa, v);
+          }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&acce_b[a]));
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
   }
-
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                 :: "r"(tmem), "r"(kTmemCols) : "memory");
+                 :: "r"(tmem), "r"(kT3TmemCols) : "memory");
   }
 }
 
@@ -532,7 +718,7 @@ int correlate_enqueue(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec,
   if (n_ant > 4096) return OVRO_ERR_UNSUPPORTED;
   // any int8 input (-128 included): partial sums below 2 * 128^2 * K < 2^24
   if (2LL * 128 * 128 * n_spec >= (1LL << 24)) return OVRO_ERR_OVERFLOW;
-  if (reinterpret_cast<uintptr_t>(d_vis) % 16 != 0 || reinterpret_cast<uintptr_t>(d_fine_q) % 2 != 0)
+  if (reinterpret_cast<uintptr_t>(d_vis) % 16 != 0 || reinterpret_cast<uintptr_t>(d_fine_q) % 4 != 0)
     return OVRO_ERR_INVALID_ARG;
   const int n_input = 2 * n_ant;
   if (mode == OVRO_XENG_FP32) {
@@ -561,24 +747,15 @@ int correlate_enqueue(const int8_t* d_fine_q, int n_ant, int n_chan, int n_spec,
   }
   const int n_pairs = n_tiles * (n_tiles + 1) / 2;
   const long long n_items = static_cast<long long>(n_pairs) * n_chan;
-  // 96 KB of dynamic shared memory keeps at most two CTAs (2 x 256 TMEM columns) per SM
-  const int smem = 96 * 1024;
-  OVRO_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  // persistent CTAs per SM (one or two fit: 256 TMEM columns each)
-  auto run = [&](int per_sm) -> int {
-    long long grid = static_cast<long long>(per_sm) * num_sms();
-    if (grid > n_items) grid = n_items;
-    OVRO_PROF("k_xeng_tc", st);
-    k_xeng_tc<<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(d_fine_q, n_ant, n_spec, n_tiles,
-                                                                    n_pairs, n_items, d_vis);
-    OVRO_LAUNCH_CHECK();
-    return OVRO_OK;
-  };
-  const std::string key = tune_key("k_xeng_tc", {n_ant, n_chan, n_spec});
-  int per_sm = tuned(key, 2);
-  if (tuning(st))
-    if (int e = tune_pick(key, {1, 2}, run, st, &per_sm)) return e;
-  return run(per_sm);
+  // three 48 KB operand stages: one CTA (and one 512-column TMEM allocation) per SM
+  const int smem = kT3Stages * kT3StageBytes;
+  OVRO_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const long long grid = std::min<long long>(num_sms(), n_items);
+  OVRO_PROF("k_xeng_tc", st);
+  k_xeng_tc3<<<static_cast<unsigned>(grid), kT3Threads, smem, st>>>(d_fine_q, n_ant, n_spec, n_tiles, n_pairs,
+                                                                    n_items, d_vis);
+  OVRO_LAUNCH_CHECK();
+  return OVRO_OK;
 }
 
 }  // namespace ovro
