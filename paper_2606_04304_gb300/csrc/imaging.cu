@@ -239,115 +239,144 @@ __host__ __device__ constexpr int tab_base(int g, int c, int off) {
   return (kTabD - g / 2 - c) * kTabStride + kQ / 2 - off;
 }
 __host__ __device__ constexpr int tab_mirror(int g) { return 2 * (kTabD - g / 2) * kTabStride + kQ; }
-constexpr int kPrepPerWarp = 8;     // listed baselines per warp of k_grid_prep
 
-// a5 and the Stokes I of a6 for one channel group: a warp's lanes are the
-// group's 32 channels; for each of its listed baselines a lane decides the
-// exact rounded position (float-float, FP64 when that cannot decide), the keep
-// test (centre cell inside the grid's margin; the uv range when it must be
-// decided per channel), reads XX and YY and stores the record -- the image is
-// the real part of the transform, i.e. the transform of the grid's Hermitian
-// part H = (G + conj G(-u, -v)) / 2, so the record carries half of
+// a5 and the Stokes I of a6 for one channel group and kPrepBl listed
+// baselines per CTA: for each (channel, baseline) a thread decides the exact
+// rounded position (float-float, FP64 when that cannot decide), the keep test
+// (centre cell inside the grid's margin; the uv range when it must be decided
+// per channel), reads XX and YY and forms the record -- the image is the real
+// part of the transform, i.e. the transform of the grid's Hermitian part
+// H = (G + conj G(-u, -v)) / 2, so the record carries half of
 // conj(Stokes I) = conj(XX + YY) / 4 (the exp(+) transform is a forward FFT of
 // the conjugated grid); calibration corrections c_a conj(c_b) are applied per
-// polarisation in FP32 when given.  Kept visibilities are counted per channel.
+// polarisation in FP32 when given.  Lanes are baselines while the
+// visibilities are read (a warp reads consecutive baselines of one channel:
+// nearly sequential 32-byte records), and the records are turned around in
+// shared memory so each baseline's 32 channel records are stored as one
+// 512-byte run ([group][listed][lane]).  Kept visibilities are counted per
+// channel.
+constexpr int kPrepBl = 64;          // listed baselines per CTA of k_grid_prep
+constexpr int kPrepCh = kLanes / 8;  // channels per warp (8 warps)
+
 template <int LOG2G, bool CAL, bool BASES>
 __global__ void __launch_bounds__(256)
 k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* __restrict__ vis, long long n_bl,
             const Baseline* __restrict__ base, const ChanScale* __restrict__ cs, int ch0, int nb,
             int* __restrict__ kept, PrepRec* __restrict__ prep, GridOpts opt) {
   constexpr int G = 1 << LOG2G;
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  // [baseline][channel] records, rows padded by one record so that the lanes'
+  // 16-byte stores (lanes = baselines) fall in distinct banks
+  __shared__ int4 tile[kPrepBl][kLanes + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int group = blockIdx.y;
-  const int i0 = gw * kPrepPerWarp;
-  if (i0 >= n_listed) return;
-  const int i1 = min(n_listed, i0 + kPrepPerWarp);
-  const int cb = group * kLanes + lane;
-  const bool active = cb < nb;
-  const long long chan = ch0 + (active ? cb : nb - 1);
-  const ChanScale s = cs[chan];
+  const int i0 = blockIdx.x * kPrepBl;
+  const int nbl = min(kPrepBl, n_listed - i0);
   const int cmax = G / 2 - kHalfSup - 1;
   const int lim = (cmax + 1) * kQ;                     // < 2^21
-  const int2* vis2 = reinterpret_cast<const int2*>(vis) + chan * n_bl * 4;
-  const float2* gc = (CAL && opt.gains != nullptr) ? opt.gains + chan * opt.n_input : nullptr;
-  PrepRec* out = prep + (static_cast<long long>(group) * n_listed) * kLanes + lane;
-  int n_kept = 0;
-  // every visibility read of the warp's baselines is issued before any is used
-  int2 xx[kPrepPerWarp], yy[kPrepPerWarp];
+  // this lane's two baselines (i0 + lane, i0 + lane + 32)
+  GridEntry en[2];
+  bool has[2];
 #pragma unroll
-  for (int j = 0; j < kPrepPerWarp; ++j) {
-    const int bl = i0 + j < i1 ? __ldg(&listed[i0 + j].bl) : 0;
-    xx[j] = __ldg(vis2 + static_cast<long long>(bl) * 4);
-    yy[j] = __ldg(vis2 + static_cast<long long>(bl) * 4 + 3);
+  for (int h = 0; h < 2; ++h) {
+    const int bi = lane + 32 * h;
+    has[h] = bi < nbl;
+    en[h] = listed[i0 + (has[h] ? bi : 0)];
+  }
+  // every visibility read of the thread (kPrepCh channels x 2 baselines) is
+  // issued before any is used
+  int2 xx[kPrepCh][2], yy[kPrepCh][2];
+#pragma unroll
+  for (int cc = 0; cc < kPrepCh; ++cc) {
+    const int cb = group * kLanes + warp * kPrepCh + cc;
+    const long long chan = ch0 + (cb < nb ? cb : nb - 1);
+    const int2* vis2 = reinterpret_cast<const int2*>(vis) + chan * n_bl * 4;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      xx[cc][h] = __ldg(vis2 + static_cast<long long>(en[h].bl) * 4);
+      yy[cc][h] = __ldg(vis2 + static_cast<long long>(en[h].bl) * 4 + 3);
+    }
   }
 #pragma unroll
-  for (int j = 0; j < kPrepPerWarp; ++j) {
-    const int i = i0 + j;
-    if (i >= i1) break;
-    const GridEntry en = listed[i];
-    int pu, pv;
-    if (!fast_rint_prod32(en.dxh, en.dxl, s, &pu)) {
-      const long long pl = __double2ll_rn(__dmul_rn(base[en.cross].dx, s.s));
-      pu = static_cast<int>(pl > lim ? lim : (pl < -lim ? -lim : pl));
-    }
-    if (!fast_rint_prod32(en.dyh, en.dyl, s, &pv)) {
-      const long long pl = __double2ll_rn(__dmul_rn(base[en.cross].dy, s.s));
-      pv = static_cast<int>(pl > lim ? lim : (pl < -lim ? -lim : pl));
-    }
-    bool keep = pu > -lim && pu < lim && pv > -lim && pv < lim;
-    if (keep) {
-      int cu, cv, o;
-      centre_cell32(pu, cu, o);
-      centre_cell32(pv, cv, o);
-      keep = cu <= cmax && cu >= -cmax && cv <= cmax && cv >= -cmax;
-    }
-    if (CAL && (en.bf & kCheckUv)) {
-      const double lam = __dmul_rn(opt.blen[en.cross], s.nu_c);
-      keep = keep && lam >= opt.uv_min && lam < opt.uv_max;
-    }
-    PrepRec r{lim, lim, 0.0f, 0.0f};
-    if (BASES) {
-      // the position's table offsets, kept or not (a record is only read for
-      // tiles within kTabMargin cells of its footprint)
-      int cu, cv, ou, ov;
-      centre_cell32(pu, cu, ou);
-      centre_cell32(pv, cv, ov);
-      r.pu = tab_base(G, cu, ou);
-      r.pv = tab_base(G, cv, ov);
-    }
-    if (keep) {
-      float vr, vi;
-      if (!CAL || gc == nullptr) {
-        vr = 0.25f * static_cast<float>(xx[j].x + yy[j].x);
-        vi = -0.25f * static_cast<float>(xx[j].y + yy[j].y);
-      } else {
-        const int a = en.a, b = en.bf & 0xffff;
-        float pr = 0.f, pi = 0.f;
+  for (int cc = 0; cc < kPrepCh; ++cc) {
+    const int cl = warp * kPrepCh + cc;              // channel within the group
+    const int cb = group * kLanes + cl;
+    const bool active = cb < nb;
+    const long long chan = ch0 + (active ? cb : nb - 1);
+    const ChanScale sc = cs[chan];
+    const float2* gc = (CAL && opt.gains != nullptr) ? opt.gains + chan * opt.n_input : nullptr;
+    int n_kept = 0;
 #pragma unroll
-        for (int pol = 0; pol < 2; ++pol) {
-          const float2 ca = __ldg(gc + 2 * a + pol), cbv = __ldg(gc + 2 * b + pol);
-          const int2 q = pol ? yy[j] : xx[j];
-          const float qr = static_cast<float>(q.x), qi = static_cast<float>(q.y);
-          const float gr = ca.x * cbv.x + ca.y * cbv.y, gi = ca.y * cbv.x - ca.x * cbv.y;
-          pr += gr * qr - gi * qi;
-          pi += gr * qi + gi * qr;
+    for (int h = 0; h < 2; ++h) {
+      const GridEntry& e = en[h];
+      int pu, pv;
+      if (!fast_rint_prod32(e.dxh, e.dxl, sc, &pu)) {
+        const long long pl = __double2ll_rn(__dmul_rn(base[e.cross].dx, sc.s));
+        pu = static_cast<int>(pl > lim ? lim : (pl < -lim ? -lim : pl));
+      }
+      if (!fast_rint_prod32(e.dyh, e.dyl, sc, &pv)) {
+        const long long pl = __double2ll_rn(__dmul_rn(base[e.cross].dy, sc.s));
+        pv = static_cast<int>(pl > lim ? lim : (pl < -lim ? -lim : pl));
+      }
+      bool keep = pu > -lim && pu < lim && pv > -lim && pv < lim;
+      if (keep) {
+        int cu, cv, o;
+        centre_cell32(pu, cu, o);
+        centre_cell32(pv, cv, o);
+        keep = cu <= cmax && cu >= -cmax && cv <= cmax && cv >= -cmax;
+      }
+      if (CAL && (e.bf & kCheckUv)) {
+        const double lam = __dmul_rn(opt.blen[e.cross], sc.nu_c);
+        keep = keep && lam >= opt.uv_min && lam < opt.uv_max;
+      }
+      PrepRec r{lim, lim, 0.0f, 0.0f};
+      if (BASES) {
+        // the position's table offsets, kept or not (a record is only read for
+        // tiles within kTabMargin cells of its footprint)
+        int cu, cv, ou, ov;
+        centre_cell32(pu, cu, ou);
+        centre_cell32(pv, cv, ov);
+        r.pu = tab_base(G, cu, ou);
+        r.pv = tab_base(G, cv, ov);
+      }
+      if (keep) {
+        float vr, vi;
+        if (!CAL || gc == nullptr) {
+          vr = 0.25f * static_cast<float>(xx[cc][h].x + yy[cc][h].x);
+          vi = -0.25f * static_cast<float>(xx[cc][h].y + yy[cc][h].y);
+        } else {
+          const int a = e.a, b = e.bf & 0xffff;
+          float pr = 0.f, pi = 0.f;
+#pragma unroll
+          for (int pol = 0; pol < 2; ++pol) {
+            const float2 ca = __ldg(gc + 2 * a + pol), cbv = __ldg(gc + 2 * b + pol);
+            const int2 q = pol ? yy[cc][h] : xx[cc][h];
+            const float qr = static_cast<float>(q.x), qi = static_cast<float>(q.y);
+            const float gr = ca.x * cbv.x + ca.y * cbv.y, gi = ca.y * cbv.x - ca.x * cbv.y;
+            pr += gr * qr - gi * qi;
+            pi += gr * qi + gi * qr;
+          }
+          vr = 0.25f * pr;
+          vi = -0.25f * pi;
         }
-        vr = 0.25f * pr;
-        vi = -0.25f * pi;
+        if (!BASES) {
+          r.pu = pu;
+          r.pv = pv;
+        }
+        r.vr = vr;
+        r.vi = vi;
+        if (has[h]) ++n_kept;
       }
-      if (!BASES) {
-        r.pu = pu;
-        r.pv = pv;
-      }
-      r.vr = vr;
-      r.vi = vi;
-      ++n_kept;
+      tile[lane + 32 * h][cl] = make_int4(r.pu, r.pv, __float_as_int(r.vr), __float_as_int(r.vi));
     }
-    reinterpret_cast<int4*>(out)[static_cast<long long>(i) * kLanes] =
-        make_int4(r.pu, r.pv, __float_as_int(r.vr), __float_as_int(r.vi));
+    // the channel's kept visibilities over the warp's 64 baselines
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n_kept += __shfl_xor_sync(0xffffffffu, n_kept, o);
+    if (lane == 0 && active && n_kept) atomicAdd(kept + chan, n_kept);
   }
-  if (active && n_kept) atomicAdd(kept + chan, n_kept);
+  __syncthreads();
+  // one baseline's 32 channel records per warp store: 512 contiguous bytes
+  int4* out = reinterpret_cast<int4*>(prep) + (static_cast<long long>(group) * n_listed + i0) * kLanes;
+  for (int bi = warp; bi < nbl; bi += 8) out[static_cast<long long>(bi) * kLanes + lane] = tile[bi][lane];
 }
 
 // Gridding of one channel batch into the Hermitian part of the grid, rows
@@ -935,7 +964,7 @@ int launch_batch(const ImgPlan& p, const ImgWs& w, const GridOpts& o, const int3
     const bool cal = o.gains != nullptr || o.uv_min > 0.0 || std::isfinite(o.uv_max);
     const int n_groups = (nb + kLanes - 1) / kLanes;
     if (w.n_listed > 0) {
-      dim3 grid((w.n_listed + 8 * kPrepPerWarp - 1) / (8 * kPrepPerWarp), n_groups);
+      dim3 grid((w.n_listed + kPrepBl - 1) / kPrepBl, n_groups);
       OVRO_PROF("k_grid_prep", st);
       auto prep = cal ? (w.bases ? k_grid_prep<L, true, true> : k_grid_prep<L, true, false>)
                       : (w.bases ? k_grid_prep<L, false, true> : k_grid_prep<L, false, false>);
