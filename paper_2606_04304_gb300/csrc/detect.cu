@@ -446,6 +446,7 @@ constexpr int kRankMaxPerThread = 16;   // band ranking: nc <= 16 * 1024
 // c_lo + m (c_lo = keys below the lower bucket), as in the full sort.  Output:
 // the band's sorted values (sv [pixel][0 .. B)) and the stream of band ranks
 // with the below / above codes.
+template <int KPT>   // keys per thread: nc <= KPT * 1024
 __global__ void __launch_bounds__(1024)
 k_rank_band(const float* __restrict__ z, int n_valid, int nc, int h, int r_lo, int B, float* __restrict__ sv,
             uint32_t* __restrict__ steps) {
@@ -464,9 +465,9 @@ k_rank_band(const float* __restrict__ z, int n_valid, int nc, int h, int r_lo, i
   for (int p = blockIdx.x; p < n_valid; p += gridDim.x) {
     const float* zp = z + static_cast<long long>(p) * nc;
     // channel i * blockDim + t in register i: a warp's lanes hold 32 consecutive channels
-    uint32_t key[kRankMaxPerThread];
+    uint32_t key[KPT];
 #pragma unroll
-    for (int i = 0; i < kRankMaxPerThread; ++i) {
+    for (int i = 0; i < KPT; ++i) {
       const int k = i * blockDim.x + threadIdx.x;
       key[i] = k < nc ? f2key(__ldg(zp + k)) : 0u;
     }
@@ -476,20 +477,12 @@ k_rank_band(const float* __restrict__ z, int n_valid, int nc, int h, int r_lo, i
     uint32_t* cnt = hist + 768;                                  // per-chunk candidate counts
     for (int i = threadIdx.x; i < 768; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    // round 1: the top byte; the leader of each group of equal digits adds it
+    // round 1: the top byte (shared atomics; equal digits within a warp are
+    // serialised by the shared-memory pipe, not by issued instructions)
 #pragma unroll
-    for (int i = 0; i < kRankMaxPerThread; ++i) {
+    for (int i = 0; i < KPT; ++i) {
       if (i * static_cast<int>(blockDim.x) >= nc) break;
-      const bool valid = i * blockDim.x + threadIdx.x < nc;
-      const uint32_t d = key[i] >> 24;
-      unsigned peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-      for (int bit = 0; bit < 8; ++bit) {
-        const bool x = (d >> bit) & 1u;
-        const unsigned bb = __ballot_sync(0xffffffffu, x);
-        peers &= x ? bb : ~bb;
-      }
-      if (valid && lane == __ffs(peers) - 1) atomicAdd(&h1[d], __popc(peers));
+      if (i * blockDim.x + threadIdx.x < nc) atomicAdd(&h1[key[i] >> 24], 1u);
     }
     __syncthreads();
     if (warp == 0) {
@@ -500,22 +493,12 @@ k_rank_band(const float* __restrict__ z, int n_valid, int nc, int h, int r_lo, i
     const uint32_t d_lo = sel[0], d_hi = sel[1];
     // round 2: the second byte among keys of the two boundary top bytes
 #pragma unroll
-    for (int i = 0; i < kRankMaxPerThread; ++i) {
+    for (int i = 0; i < KPT; ++i) {
       if (i * static_cast<int>(blockDim.x) >= nc) break;
       const bool valid = i * blockDim.x + threadIdx.x < nc;
       const uint32_t t = key[i] >> 24, d = (key[i] >> 16) & 255u;
-      const bool in_lo = valid && t == d_lo, in_hi = valid && t == d_hi && d_hi != d_lo;
-      unsigned eq = 0xffffffffu;
-#pragma unroll
-      for (int bit = 0; bit < 8; ++bit) {
-        const bool x = (d >> bit) & 1u;
-        const unsigned bb = __ballot_sync(0xffffffffu, x);
-        eq &= x ? bb : ~bb;
-      }
-      const unsigned plo = eq & __ballot_sync(0xffffffffu, in_lo);
-      const unsigned phi = eq & __ballot_sync(0xffffffffu, in_hi);
-      if (in_lo && lane == __ffs(plo) - 1) atomicAdd(&h2lo[d], __popc(plo));
-      if (in_hi && lane == __ffs(phi) - 1) atomicAdd(&h2hi[d], __popc(phi));
+      if (valid && t == d_lo) atomicAdd(&h2lo[d], 1u);
+      else if (valid && t == d_hi) atomicAdd(&h2hi[d], 1u);
     }
     __syncthreads();
     if (warp == 0) {
@@ -531,7 +514,7 @@ k_rank_band(const float* __restrict__ z, int n_valid, int nc, int h, int r_lo, i
     // channels [i * blockDim + 32 warp, + 32)
     const int n_chunks = (nc + blockDim.x - 1) / blockDim.x * W;
 #pragma unroll
-    for (int i = 0; i < kRankMaxPerThread; ++i) {
+    for (int i = 0; i < KPT; ++i) {
       if (i * static_cast<int>(blockDim.x) >= nc) break;
       const bool valid = i * blockDim.x + threadIdx.x < nc;
       const bool cand = valid && key[i] >= v_lo && key[i] <= v_hi;
@@ -568,7 +551,7 @@ k_rank_band(const float* __restrict__ z, int n_valid, int nc, int h, int r_lo, i
     const int m = sel[7];
     uint16_t* rk = ib;                                           // channel -> band rank or code, after the sort
 #pragma unroll
-    for (int i = 0; i < kRankMaxPerThread; ++i) {
+    for (int i = 0; i < KPT; ++i) {
       if (i * static_cast<int>(blockDim.x) >= nc) break;
       const int k = i * blockDim.x + threadIdx.x;
       const bool valid = k < nc;
@@ -591,7 +574,7 @@ k_rank_band(const float* __restrict__ z, int n_valid, int nc, int h, int r_lo, i
       rk[ia[j]] = static_cast<uint16_t>(b < 0 ? kRankBelow : (b >= B ? kRankAbove : static_cast<uint32_t>(b)));
     }
 #pragma unroll
-    for (int i = 0; i < kRankMaxPerThread; ++i) {
+    for (int i = 0; i < KPT; ++i) {
       const int k = i * blockDim.x + threadIdx.x;
       if (k < nc && (key[i] < v_lo || key[i] > v_hi))
         rk[k] = static_cast<uint16_t>(key[i] < v_lo ? kRankBelow : kRankAbove);
@@ -1418,15 +1401,20 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
     const size_t sm_rank = (256 * (W + 1) + 32) * 4 + static_cast<size_t>(nc) * 12;
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm_rank)));
-    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank_band, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank_band<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm_rank)));
+    OVRO_CUDA_TRY(cudaFuncSetAttribute(k_rank_band<kRankMaxPerThread>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm_rank)));
     // CTAs per SM (each CTA loops over pixels; the outputs do not depend on it)
     auto rank = [&](int per_sm) -> int {
       const int blocks = std::min(p.n_valid, per_sm * nsm);
       OVRO_PROF("k_rank", st);
-      if (use_band)
-        k_rank_band<<<blocks, threads, sm_rank, st>>>(w.zbuf, p.n_valid, nc, p.half[c], nc / 2 - band / 2, band,
-                                                      w.sv, w.steps);
+      if (use_band && nc <= 8 * 1024)
+        k_rank_band<8><<<blocks, threads, sm_rank, st>>>(w.zbuf, p.n_valid, nc, p.half[c], nc / 2 - band / 2, band,
+                                                         w.sv, w.steps);
+      else if (use_band)
+        k_rank_band<kRankMaxPerThread><<<blocks, threads, sm_rank, st>>>(w.zbuf, p.n_valid, nc, p.half[c],
+                                                                         nc / 2 - band / 2, band, w.sv, w.steps);
       else
         k_rank<<<blocks, threads, sm_rank, st>>>(w.zbuf, p.n_valid, nc, p.half[c], w.sv, w.steps, nullptr, nullptr);
       OVRO_LAUNCH_CHECK();
