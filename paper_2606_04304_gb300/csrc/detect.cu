@@ -304,12 +304,15 @@ constexpr uint32_t kRankNone = 0xffffu, kRankBelow = 0xfffeu, kRankAbove = 0xfff
 // (in-warp ranks by an 8-ballot multisplit, per-warp digit histograms at a
 // padded pitch, so an exclusive scan in digit-major order gives every
 // (digit, warp) its stable output offset).  The sorted keys end in ks / is.
+//   sw: the warps that rank segments (<= blockDim / 32).  All 32 for the band
+//   too: with 8 (a scan over a quarter of the digit counters) the idle warps
+//   waited at the barriers and the sort took longer.
 __device__ void lsd_sort(uint32_t* ks, uint16_t* is, uint32_t* kd, uint16_t* id, int m, uint32_t* hist,
-                         uint32_t* tot) {
-  const int W = blockDim.x >> 5;
+                         uint32_t* tot, int sw) {
+  const int W = sw;
   const int HP = W + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int seg = ((m + W - 1) / W + 31) / 32 * 32;
+  const int seg = warp < W ? ((m + W - 1) / W + 31) / 32 * 32 : 0;   // idle warps rank nothing
   const unsigned lt_mask = (1u << lane) - 1u;
   for (int pass = 0; pass < 4; ++pass) {
     const int sh = 8 * pass;
@@ -394,7 +397,7 @@ k_rank(const float* __restrict__ z, int n_valid, int nc, int h, float* __restric
       ia[k] = static_cast<uint16_t>(k);
     }
     __syncthreads();
-    lsd_sort(ka, ia, kb, ib, nc, hist, tot);
+    lsd_sort(ka, ia, kb, ib, nc, hist, tot, W);
     float* svp = sv + static_cast<long long>(p) * nc;
     for (int r = threadIdx.x; r < nc; r += blockDim.x) {
       svp[r] = key2f(ka[r]);
@@ -564,7 +567,7 @@ k_rank_band(const float* __restrict__ z, int n_valid, int nc, int h, int r_lo, i
       }
     }
     __syncthreads();
-    lsd_sort(ka, ia, kb, ib, m, hist, tot);
+    lsd_sort(ka, ia, kb, ib, m, hist, tot, W);
     // candidate j has stable rank c_lo + j, band rank j - (r_lo - c_lo)
     const int off = r_lo - c_lo;
     float* svp = sv + static_cast<long long>(p) * nc;
