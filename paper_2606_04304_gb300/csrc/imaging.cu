@@ -390,7 +390,8 @@ k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* _
 // its tile, a lane reads its channel's prepared record (one 16-byte load, the
 // warp's 32 lanes contiguous), mirrors it if flagged, reads the tile's 4 row
 // and 4 column weights of the separable kernel and adds the products into its
-// accumulators; list entries are read three records ahead, records two.
+// accumulators; kRing records are in flight per warp and their list entries
+// are read 2 kRing ahead.
 //   BASES: the record holds the weight-table offsets of its position, so the
 //     weights are 8 loads at fixed strides from (offset + tile origin) and a
 //     lane off the footprint reads the table's zero rows;
@@ -398,8 +399,8 @@ k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* _
 //     zeros when its footprint misses the tile.
 // The tile is written with the (-1)^(row + col) centring sign as two real
 // planes, grid [batch][2][G/2][G] (row j - G/2).
-constexpr int kGridWarps = 24;
-constexpr int kRing = 3;           // records in flight per warp
+constexpr int kGridWarps = 20;
+constexpr int kRing = 4;           // records in flight per warp
 constexpr size_t kTileSmem = static_cast<size_t>(kTabXLen) * sizeof(float);
 
 template <int LOG2G, bool BASES>
