@@ -694,7 +694,7 @@ k_fft_cols(const void* __restrict__ h, const float* __restrict__ hs, int n_img, 
   for (int i = threadIdx.x; i < G; i += blockDim.x) tw[i] = tw_g[i];
   // U items per thread in flight: the reads come from L2 and would otherwise
   // wait one round trip each
-  constexpr int U = 4;
+  constexpr int U = 8;
   const int n_items = half_rows(G) * CP;
   for (int p = threadIdx.x; p < CP; p += blockDim.x) A[p * LDP] = make_float2(0.0f, 0.0f);   // row 0: empty
   for (int i0 = threadIdx.x; i0 < n_items; i0 += U * blockDim.x) {
