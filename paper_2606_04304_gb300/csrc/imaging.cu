@@ -259,7 +259,7 @@ constexpr int kPrepBl = 64;          // listed baselines per CTA of k_grid_prep
 constexpr int kPrepCh = kLanes / 8;  // channels per warp (8 warps)
 
 template <int LOG2G, bool CAL, bool BASES>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, CAL ? 1 : 4)
 k_grid_prep(const GridEntry* __restrict__ listed, int n_listed, const int32_t* __restrict__ vis, long long n_bl,
             const Baseline* __restrict__ base, const ChanScale* __restrict__ cs, int ch0, int nb,
             int* __restrict__ kept, PrepRec* __restrict__ prep, GridOpts opt) {
