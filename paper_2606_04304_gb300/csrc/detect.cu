@@ -701,7 +701,7 @@ __device__ __forceinline__ bool for_steps(const uint4* __restrict__ st4, int w0,
 }
 
 constexpr int kWalkThreads = 64;   // full walk: nc / 32 words per thread
-constexpr int kBandWords = 64;     // band walk: 2048 ranks
+constexpr int kBandWordsMax = 64;  // band walk: up to 2048 ranks
 constexpr int kBandThreads = 128;
 
 // One thread per (pixel, segment) walks the segment's outputs over the step
@@ -1398,7 +1398,13 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
     // Coarse channels longer than the band: band ranks and the band walk for
     // every pixel, then full ranks and the full walk for the pixels whose
     // median left the band.  Shorter ones: full ranks and the full walk.
-    const int band = kBandWords * 32;
+    // the band: the middle 2048 ranks (a window median's rank wanders about
+    // nc / (2 sqrt(W)) from the middle for a stationary spectrum: 99 ranks at
+    // 8192 channels, W = 1707; on the skewed noise images of the full workload
+    // a band of 1024 sent enough pixels to the full walk to cost more than the
+    // smaller sort saved: 13.7 against 12.6 ms per step for ranks and walk)
+    const int band_words = kBandWordsMax;
+    const int band = band_words * 32;
     const bool use_band = nc > band && nc <= kRankMaxPerThread * 1024;
     const int threads = 1024, W = threads / 32;      // one CTA per SM (shared memory): all 32 warps
     const size_t sm_rank = (256 * (W + 1) + 32) * 4 + static_cast<size_t>(nc) * 12;
@@ -1432,7 +1438,7 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
     // again, since the fallback rewrites the failed pixels' streams
     const int nwords = (nc + 31) / 32;
     const size_t sm_full = static_cast<size_t>(nwords) * kWalkThreads * 4;
-    const size_t sm_band = static_cast<size_t>(kBandWords) * kBandThreads * 4;
+    const size_t sm_band = static_cast<size_t>(band_words) * kBandThreads * 4;
     OVRO_CUDA_TRY(cudaFuncSetAttribute(k_walk<false, kWalkThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm_full)));
     auto rank_walk = [&](int n_seg) -> int {
@@ -1444,7 +1450,7 @@ int run_filter_coarse(int c, const float* img_block, const DetectPlan& p, const 
         {
           OVRO_PROF("k_walk", st);
           k_walk<true, kBandThreads><<<static_cast<int>((thr + kBandThreads - 1) / kBandThreads), kBandThreads,
-                                       sm_band, st>>>(w.steps, p.n_valid, nc, p.half[c], n_seg, seg_len, kBandWords,
+                                       sm_band, st>>>(w.steps, p.n_valid, nc, p.half[c], n_seg, seg_len, band_words,
                                                       w.med, nullptr, nullptr, w.fail, w.count + 3);
           OVRO_LAUNCH_CHECK();
         }
