@@ -172,19 +172,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 // For more than 32 spectra (or larger arrays) the operands of a tile pair are
 // streamed through shared memory in chunks of 32 spectra, with the roles of a
 // CTA's warps split so that the tensor pipe never waits on the SIMT work:
-//   warps 0-7 (converters): thread t owns operand rows 2 (t % 64) and
-//     2 (t % 64) + 1 of the pair and quarter t / 64 of a chunk's spectra; it
+//   warps 0-15 (converters): thread t owns operand rows 2 (t % 64) and
+//     2 (t % 64) + 1 of the pair and eighth t / 64 of a chunk's spectra; it
 //     reads its inputs' int8 spectra four chunks ahead into registers (4-byte
 //     loads, 128 contiguous bytes per warp and spectrum) while converting a
 //     chunk into FP16 A and [X; Z] B rows of a free stage (exactly: the byte
 //     with its sign bit flipped is the low byte of the FP16 number
 //     1024 + 128 + q, and one packed subtraction of 1152 leaves q; 16-byte
 //     shared stores), then arrives on that stage's full barrier;
-//   warp 12 lane 0 (MMA): per chunk waits for a full stage, issues the four
+//   warp 20 lane 0 (MMA): per chunk waits for a full stage, issues the four
 //     K = 16 MMAs into the item's accumulator and commits them to the stage's
 //     empty barrier (and, after the item's last chunk, to the accumulator's
 //     ready barrier);
-//   warps 8-11 (epilogue): drain an item's accumulator (TMEM lane quarter
+//   warps 16-19 (epilogue): drain an item's accumulator (TMEM lane quarter
 //     warp % 4) into int32 records and arrive on its free barrier.
 // Three operand stages (48 KB each) and two 256-column accumulators, so the
 // epilogue of item i runs under the MMAs of item i + 1.  Every wait is bounded
@@ -192,10 +192,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 // role polls, and the kernel waits (bounded) for its MMAs before freeing TMEM.
 constexpr int kT3Stages = 3;
 constexpr int kT3StageBytes = kTcASmem + 2 * kTcASmem;     // A 16 KB + B 32 KB
-constexpr int kT3ConvThreads = 256;                        // warps 0-7
-constexpr int kT3Threads = 416;                            // 13 warps
-constexpr int kT3MmaWarp = 12;
-constexpr int kT3SpecPerThread = kTcSpecPerChunk / 4;      // a converter's quarter of a chunk
+constexpr int kT3ConvThreads = 512;                        // warps 0-15
+constexpr int kT3Threads = 672;                            // 21 warps
+constexpr int kT3MmaWarp = 20;
+constexpr int kT3SpecPerThread = kTcSpecPerChunk / (kT3ConvThreads / 64);   // a converter's eighth of a chunk
 constexpr uint32_t kT3TmemCols = 512;
 
 __device__ __forceinline__ bool mbar_wait_abort(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
@@ -270,7 +270,7 @@ k_xeng_tc3(const int8_t* __restrict__ q, int n_ant, int n_spec, int n_tiles, int
   if (warp < kT3ConvThreads / 32) {
     // ---------------------------------------------------------- converters
     const int pr = tid & 63;                           // operand rows 2 pr, 2 pr + 1
-    const int qq = tid >> 6;                           // spectra 8 qq .. 8 qq + 7 of a chunk
+    const int qq = tid >> 6;                           // spectra qq kT3SpecPerThread .. of a chunk
     // this CTA's chunks in order (chunk gg is chunk gg % n_chunks of its item
     // gg / n_chunks); the reads run four chunks ahead of the conversion
     // (register sets 0-3), from a read cursor that moves to the next item's
@@ -449,33 +449,28 @@ k_xeng_tc3(const int8_t* __restrict__ q, int n_ant, int n_spec, int n_tiles, int
       int4* out = reinterpret_cast<int4*>(vis + static_cast<long long>(ch) * n_bl * 8);
       const uint32_t tl0 = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>(a * 256);
 #pragma unroll 1
-      for (int cin0 = 0; cin0 < kTcInputsN; cin0 += 32) {
-        // TMEM columns cin0 .. cin0 + 31: Re of column inputs J 128 + cin0 ..;
-        // the same + 128: their Im
-        uint32_t re[32], im[32];
+      for (int cin0 = 0; cin0 < kTcInputsN; cin0 += 16) {
+        // TMEM columns cin0 .. cin0 + 15: Re of column inputs J 128 + cin0 ..;
+        // the same + 128: their Im (16 columns at a time keep the epilogue's
+        // registers within the 21-warp CTA's budget)
+        uint32_t re[16], im[16];
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-            "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]),
               "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]),
-              "=r"(re[14]), "=r"(re[15]), "=r"(re[16]), "=r"(re[17]), "=r"(re[18]), "=r"(re[19]),
-              "=r"(re[20]), "=r"(re[21]), "=r"(re[22]), "=r"(re[23]), "=r"(re[24]), "=r"(re[25]),
-              "=r"(re[26]), "=r"(re[27]), "=r"(re[28]), "=r"(re[29]), "=r"(re[30]), "=r"(re[31])
+              "=r"(re[14]), "=r"(re[15])
             : "r"(tl0 + cin0));
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-            "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]),
               "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]),
-              "=r"(im[14]), "=r"(im[15]), "=r"(im[16]), "=r"(im[17]), "=r"(im[18]), "=r"(im[19]),
-              "=r"(im[20]), "=r"(im[21]), "=r"(im[22]), "=r"(im[23]), "=r"(im[24]), "=r"(im[25]),
-              "=r"(im[26]), "=r"(im[27]), "=r"(im[28]), "=r"(im[29]), "=r"(im[30]), "=r"(im[31])
+              "=r"(im[14]), "=r"(im[15])
             : "r"(tl0 + cin0 + 128u));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (an < n_ant) {
           const int b0 = (J * kTcInputsN + cin0) >> 1;
 #pragma unroll
-          for (int bb = 0; bb < 16; ++bb) {
+          for (int bb = 0; bb < 8; ++bb) {
             const int b = b0 + bb;
             if (b >= n_ant || b < an) continue;
             int4 v;
